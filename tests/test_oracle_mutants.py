@@ -1,0 +1,107 @@
+"""Planted mistakes: each test copies the oracle's C source, plants one plausible
+slip (a wrong sign, a dropped term, a wrong index, an off-by-one coefficient, a
+skipped rotation, a wrong normalisation), builds it, and checks that the pins
+reject the mutant.  Everything runs on the CPU."""
+import ctypes
+import math
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import cpaa_inputs as ci
+from oracle import oracle as O
+from oracle import build as B
+
+MUTANTS = {
+    "recurrence_sign": ("s = 2.0 * s - j->T[u];", "s = 2.0 * s + j->T[u];"),
+    "recurrence_factor": ("s = 2.0 * s - j->T[u];", "s = s - j->T[u];"),
+    "first_round_degree_index": (
+        "s = s + j->T[v] / (double)(rp[v + 1] - rp[v]);\n            }\n            j->Tpp[u] = s;\n            j->pibar[u] = j->pibar[u] + j->ck * s;\n        } else if",
+        "s = s + j->T[v] / (double)(rp[u + 1] - rp[u]);\n            }\n            j->Tpp[u] = s;\n            j->pibar[u] = j->pibar[u] + j->ck * s;\n        } else if"),
+    "later_round_degree_index": ("s = s + j->Tp[v] / (double)(rp[v + 1] - rp[v]);",
+                                 "s = s + j->Tp[v] / (double)(rp[u + 1] - rp[u]);"),
+    "gather_wrong_operand": ("s = s + j->Tp[v] / (double)(rp[v + 1] - rp[v]);",
+                             "s = s + j->T[v] / (double)(rp[v + 1] - rp[v]);"),
+    "c0_not_halved": ("pibar[i] = ck[0] / 2.0 * T[i];", "pibar[i] = ck[0] * T[i];"),
+    "coeff_off_by_one": ("job.pibar = pibar; job.ck = ck[k];", "job.pibar = pibar; job.ck = ck[k - 1];"),
+    "ratio_transposed": ("double ratio = c / (1.0 - s);", "double ratio = (1.0 - s) / c;"),
+    "rotation_skipped": ("if (k >= 2) { /* rotate", "if (k >= 3) { /* rotate"),
+    "scale_normalisation": ("pi[i] = (1.0 - c) * pibar[i];", "pi[i] = c * pibar[i];"),
+    "err_bound_exponent": ("2.0 * pow(b, (double)(M + 1)) / (1.0 + b)", "2.0 * pow(b, (double)M) / (1.0 + b)"),
+    "kappa_degree": ("q += p[i] * p[i] / d;", "q += p[i] * p[i] * d;"),
+    "dense_wrong_degree": ("a[i * n + j] -= c / (double)(row_ptr[j + 1] - row_ptr[j]);",
+                           "a[i * n + j] -= c / (double)(row_ptr[i + 1] - row_ptr[i]);"),
+    "power_restart": ("job.T = x; job.Tpp = y; job.c = c; job.p = p;",
+                      "job.T = p; job.Tpp = y; job.c = c; job.p = p;"),
+}
+
+
+def _pins():
+    """Run the core pins against whatever library O._lib holds; return the
+    names of the pins that failed."""
+    failed = []
+    c = 0.85
+    ck = O.cheb_coeffs(c, 12)
+    if np.abs(ck - O.quadrature_coeffs(c, 12)).max() > 1e-12:
+        failed.append("coeffs")
+    S = 1.0 / (1.0 - c)
+    for M in (1, 5, 12):
+        SM = ck[0] / 2 + ck[1:M + 1].sum()
+        if abs(O.err_bound(c, M) - (1.0 - SM / S)) > 1e-13:
+            failed.append("err_bound")
+            break
+    for g in (ci.random_small(30, 70, seed=1), ci.star(5), ci.chung_lu(200, 900, seed=3)):
+        rp, cx = g.numpy()
+        n = g.n
+        p = (np.arange(n) % 4 + 1.0)
+        p /= p.sum()
+        ref = O.lapack_pagerank(rp, cx, p, c)
+        for M in (1, 2, 5):
+            for norm in (0, 1):
+                if np.abs(O.cpaa(rp, cx, p, c, M, norm) - O.eig_truncation(rp, cx, p, c, M, norm)).sum() > 1e-12:
+                    failed.append("eig_truncation")
+        for norm in (0, 1):
+            M = O.rounds_needed(c, 1e-12, O.kappa(rp, p), norm)
+            if M < 0 or np.abs(O.cpaa(rp, cx, p, c, M, norm) - ref).sum() > 1e-12:
+                failed.append("converged")
+        # the stopping bound must hold and must not be loose by more than kappa
+        k = O.kappa(rp, p)
+        if not (1.0 <= k <= math.sqrt(rp[-1]) * np.sqrt((p * p).sum()) * (1 + 1e-12) + 1e-12):
+            failed.append("kappa_range")
+        d = np.diff(rp).astype(float)
+        if abs(k - math.sqrt(d.sum()) * math.sqrt((p * p / d).sum())) > 1e-12 * k:
+            failed.append("kappa_def")
+        if np.abs(O.dense_pagerank(rp, cx, p, c) - ref).sum() > 1e-12:
+            failed.append("dense")
+        try:
+            x, _ = O.power(rp, cx, p, c, tol=1e-13, max_iter=5000)
+            if np.abs(x - ref).sum() > 1e-12:
+                failed.append("power")
+        except RuntimeError:
+            failed.append("power")
+    return failed
+
+
+def test_unmutated_oracle_passes_core_pins():
+    assert _pins() == []
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(B.SRC).read()
+    assert src.count(old) == 1, "mutation anchor not unique: " + name
+    path = tmp_path / "mutant.c"
+    path.write_text(src.replace(old, new))
+    so = tmp_path / "libmutant.so"
+    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off",
+                    "-o", str(so), str(path), "-lm", "-lpthread"], check=True)
+    saved = O._lib
+    try:
+        O._lib = O.configure(ctypes.CDLL(str(so)))
+        failed = _pins()
+    finally:
+        O._lib = saved
+    assert failed, "planted mistake %r passed every pin" % name
