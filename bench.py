@@ -1,0 +1,410 @@
+#!/usr/bin/env python3
+"""CPAA PageRank benchmark on one GB300 per rank.
+
+Workload (default): Chung-Lu power-law undirected graph, n = 2^24 vertices,
+2.56e8 endpoint-pair draws (exponent 2.1, seed 0) plus a Hamiltonian ring,
+symmetric int32 CSR; damping c = 0.85; uniform p = 1/n; stop when the
+rigorous L1 bound is below 1e-6.  One step = one full cpaa_solve (prep,
+kappa, M fused recurrence rounds, finalisation) on inputs already resident in
+HBM.  The CSR (about 2 GB of column indices) is far larger than the 126 MB
+L2, so no extra L2 flush is needed between steps.
+
+Printed: one JSON line (rank 0).  ``value`` is GTEPS = nnz x rounds / s over
+all ranks; ``e2e`` is the same through the C ABI with host buffers (H2D of p
+and D2H of pi inside the timed region); ``roofline`` is for the step kernel,
+timed live with CUDA events on the solve's stream; ``cpu_baseline`` is the
+FP64 oracle on the host cores on a bounded sample of the same graph.
+
+``--impl reference`` times the FP64 CPU oracle alone (this method has no
+other reference implementation) on the same workload and prints its line.
+Multi-GPU runs (torchrun) are independent replicas: the method's rounds need
+the whole graph, and one graph fits one GPU.
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CPAA GTEPS (% HBM roofline); time to 1e-6 L1 vs plain FP64 on same GB300"
+
+WORKLOADS = {
+    "chung_lu_16M": dict(n=1 << 24, edges=256_000_000, gamma=2.1, seed=0, c=0.85, tol=1e-6,
+                         desc="Chung-Lu n=2^24, 2.56e8 pair draws, gamma=2.1, seed 0, + ring; "
+                              "c=0.85, uniform p, tol 1e-6 L1"),
+    "chung_lu_10k": dict(n=10_000, edges=100_000, gamma=2.1, seed=0, c=0.85, tol=1e-10,
+                         desc="Chung-Lu n=10000, 1e5 pair draws, gamma=2.1, seed 0, + ring; "
+                              "c=0.85, uniform p, tol 1e-10"),
+    "chung_lu_4M": dict(n=1 << 22, edges=64_000_000, gamma=2.1, seed=0, c=0.85, tol=1e-6,
+                        desc="Chung-Lu n=2^22, 6.4e7 pair draws, gamma=2.1, seed 0, + ring; "
+                             "c=0.85, uniform p, tol 1e-6 L1"),
+    "chung_lu_1M": dict(n=1 << 20, edges=16_000_000, gamma=2.1, seed=0, c=0.85, tol=1e-6,
+                        desc="Chung-Lu n=2^20, 1.6e7 pair draws, gamma=2.1, seed 0, + ring; "
+                             "c=0.85, uniform p, tol 1e-6 L1"),
+}
+
+PREC = {"f64": 0, "f32": 1, "bf16": 2}
+VB = {"f64": 8, "f32": 4, "bf16": 2}
+
+
+def alg_bytes_per_round(n, nnz, prec):
+    """Algorithmic bytes one round must move: column indices 4 nnz, row
+    pointers 4 (n+1), one degree word 4 n, the gathered vector once (vb n),
+    the old iterate read and the new one written (2 vb n), the accumulator
+    read-modify-write (2 vr n) and, for the FP32/BF16 forms, the Kahan
+    compensation read-modify-write (8 n)."""
+    vb = VB[prec]
+    vr = 8 if prec == "f64" else 4
+    kahan = 0 if prec == "f64" else 8
+    return 4 * nnz + 4 * (n + 1) + 4 * n + 3 * vb * n + 2 * vr * n + kahan * n
+
+
+# -- distributed plumbing (replicas) --------------------------------------------
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
+        int(os.environ.get("LOCAL_RANK", 0))
+
+
+def dist_init(world, use_cuda):
+    if world > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group("nccl" if use_cuda else "gloo")
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(x, world, device="cpu"):
+    """Max of a float over all ranks (identity when world == 1)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x, world, device="cpu"):
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# -- clocks ----------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# -- inputs -----------------------------------------------------------------------
+
+def make_graph(wl, device):
+    import cpaa_inputs as ci
+    w = WORKLOADS[wl]
+    t = time.time()
+    g = ci.chung_lu(w["n"], w["edges"], gamma=w["gamma"], seed=w["seed"], device=device)
+    return g, time.time() - t
+
+
+def measured_peak_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def step_kernel_hash():
+    src = os.path.join(ROOT, "paper_2112_01743_gb300", "csrc", "step.cu")
+    with open(src, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def profiled_traffic(prec, wl):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    or None when there is none or the kernel source changed since."""
+    path = os.path.join(ROOT, "profiles", "cheb_step_%s_%s.md" % (prec, wl))
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    h = re.search(r"step_cu_sha256_16:\s*([0-9a-f]+)", txt)
+    if not m or not h or h.group(1) != step_kernel_hash():
+        return None
+    return float(m.group(1))
+
+
+# -- CPU oracle leg ------------------------------------------------------------------
+
+def oracle_sample(rp, cx, rounds, threads):
+    """Time the FP64 oracle for ``rounds`` rounds on the full graph."""
+    from oracle import oracle as O
+    n = len(rp) - 1
+    p = np.full(n, 1.0 / n)
+    O.lib()
+    t = time.perf_counter()
+    O.cpaa(rp, cx, p, 0.85, rounds, nthreads=threads)
+    dt = time.perf_counter() - t
+    return dt
+
+
+# -- main arms ----------------------------------------------------------------------
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    if dev == "cuda":
+        torch.cuda.set_device(local)
+    g, _ = make_graph(args.workload, dev)
+    rp, cx = g.numpy()
+    n, nnz = g.n, g.nnz
+    del g
+    threads = os.cpu_count() or 1
+    rounds = args.ref_rounds
+    for _ in range(args.warmup):
+        oracle_sample(rp, cx, rounds, threads)
+    times = [oracle_sample(rp, cx, rounds, threads) for _ in range(args.steps)]
+    tot = sum(times)
+    value = nnz * rounds * len(times) / tot / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload]["desc"], "n": n, "nnz": nnz,
+                   "rounds_per_step": rounds},
+        "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": threads, "kind": "oracle",
+                         "sample": "%d round(s) of the FP64 oracle recurrence on the full graph "
+                                   "per step" % rounds},
+        "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (no CPU fallback)")
+    torch.cuda.set_device(local)
+    dist_init(world, True)
+    import paper_2112_01743_gb300 as pkg
+    wl = WORKLOADS[args.workload]
+    prec = args.precision
+
+    g, gen_s = make_graph(args.workload, "cuda")
+    n, nnz = g.n, g.nnz
+    t = time.time()
+    G = pkg.Graph(g.row_ptr, g.col_idx, n=n, validate=True)
+    create_s = time.time() - t
+    cpu_graph = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_graph = g.numpy()
+    del g
+    torch.cuda.empty_cache()
+
+    p = torch.full((n,), 1.0 / n, dtype=torch.float64, device="cuda")
+    pi = torch.empty_like(p)
+    stream = torch.cuda.current_stream()
+
+    def solve(precision, time_rounds=True):
+        return G.solve(p, wl["c"], wl["tol"], pi, precision=PREC[precision],
+                       time_rounds=time_rounds)
+
+    # ---- main timed region (device-resident inputs)
+    for _ in range(max(args.warmup, 3)):
+        solve(prec)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = [solve(prec) for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    local_ms = e0.elapsed_time(e1)
+    ms_total = reduce_max(local_ms, world, "cuda")
+    rounds = infos[0].rounds
+    units = reduce_sum(sum(nnz * i.rounds for i in infos), world, "cuda")
+    value = units / (ms_total * 1e-3) / 1e9
+    pi_main = pi.clone()
+    round_ms = sum(i.rounds_ms for i in infos) / sum(i.rounds for i in infos)
+    ab = alg_bytes_per_round(n, nnz, prec)
+    peak, peak_kind = measured_peak_gbs()
+    achieved = ab / (round_ms * 1e-3) / 1e9
+
+    # ---- plain FP64 single-vector form on the same GPU (time to the same tol)
+    f64 = None
+    if prec != "f64" and not args.skip_f64:
+        for _ in range(3):
+            solve("f64")
+        torch.cuda.synchronize()
+        e0.record(stream)
+        inf64 = [solve("f64") for _ in range(args.steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / args.steps
+        r64 = sum(i.rounds_ms for i in inf64) / sum(i.rounds for i in inf64)
+        ab64 = alg_bytes_per_round(n, nnz, "f64")
+        l1 = float((pi_main - pi).abs().sum().item())
+        f64 = {"ms_per_solve": ms64, "gteps": nnz * inf64[0].rounds / (ms64 * 1e-3) / 1e9,
+               "rounds": inf64[0].rounds, "round_ms": r64,
+               "hbm_frac_of_measured": ab64 / (r64 * 1e-3) / 1e9 / peak,
+               "fp64_adds_per_round": nnz,
+               "speedup_of_%s" % prec: ms64 / (ms_total / args.steps),
+               "l1_%s_vs_f64" % prec: l1}
+
+    # ---- end to end through the C ABI with host buffers (pinned)
+    hp = torch.full((n,), 1.0 / n, dtype=torch.float64).pin_memory()
+    hpi = torch.empty((n,), dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        G.solve(hp, wl["c"], wl["tol"], hpi, precision=PREC[prec])
+    barrier(world)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    e2e_units = 0
+    for _ in range(args.steps):
+        ii = G.solve(hp, wl["c"], wl["tol"], hpi, precision=PREC[prec])
+        e2e_units += nnz * ii.rounds
+    e2e_s = reduce_max(time.perf_counter() - t, world, "cuda")
+    e2e_units = reduce_sum(e2e_units, world, "cuda")
+    e2e = {"value": e2e_units / e2e_s / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": 8 * n,
+           "d2h_bytes_per_step": 8 * n}
+
+    # ---- CPU oracle baseline on a bounded sample
+    cpu = None
+    if cpu_graph is not None:
+        rp, cx = cpu_graph
+        threads = os.cpu_count() or 1
+        dt = oracle_sample(rp, cx, args.ref_rounds, threads)
+        cpu = {"value": nnz * args.ref_rounds / dt / 1e9, "unit": "GTEPS", "cores": threads,
+               "kind": "oracle",
+               "sample": "%d round(s) of the FP64 oracle recurrence on the full graph (%.1f s)"
+                         % (args.ref_rounds, dt)}
+
+    G.close()
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": prec,
+        "data": "synthetic",
+        "config": {"workload": wl["desc"], "n": n, "nnz": nnz, "rounds": rounds,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (col_idx %.2f GB), no flush" % (4 * nnz / 1e9),
+                   "graph_gen_s": round(gen_s, 2), "graph_create_s": round(create_s, 2)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": profiled_traffic(prec, args.workload),
+                     "kernel": "cheb_step_kernel<%s>" % prec, "alg_bytes_per_launch": ab,
+                     "avg_launch_ms": round_ms, "peak_kind": peak_kind},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clk,
+        "gpu_launches": sum(i.rounds + 5 for i in infos),
+        "f64": f64,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="chung_lu_16M")
+    ap.add_argument("--precision", choices=sorted(PREC), default="f32")
+    ap.add_argument("--ref-rounds", type=int, default=2,
+                    help="oracle rounds per CPU sample (bounded CPU work)")
+    ap.add_argument("--skip-f64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

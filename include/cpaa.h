@@ -1,0 +1,172 @@
+/*
+ * cpaa.h -- C ABI of the GB300 (sm_103a) CPAA PageRank library.
+ *
+ * CPAA (Zhang, Tang, Yao, Zhang, "A Parallel PageRank Algorithm For
+ * Undirected Graph") computes the PageRank vector of an undirected graph,
+ *
+ *     pi* = (1 - c) (I - c P)^-1 p,   P = A D^-1            (Sec. 2.1)
+ *
+ * by the Chebyshev expansion of f(x) = 1/(1 - c x) applied to P (Eq. 31):
+ *
+ *     pi_M = c_0/2 p + sum_{k=1..M} c_k T_k(P) p,           (Sec. 4.1)
+ *     T_0 p = p,  T_1 p = P p,  T_{k+1} p = 2 P T_k p - T_{k-1} p,
+ *
+ * followed by a normalisation (Algorithm 1).  The number of rounds M is the
+ * smallest one whose rigorous L1 bound is below the caller's tolerance: the
+ * tail of the series is ERR_M (Eq. 41) times kappa = sqrt(sum_i d_i) *
+ * ||D^-1/2 p||_2, which bounds ||T_k(P) p||_1 for every k.
+ *
+ * Conventions for every entry point:
+ *  - Plain C types only; no exception or C++ type crosses this boundary.
+ *  - Every call returns a cpaa_status; nothing aborts the process.
+ *    cpaa_last_error() gives a one-line message for the calling thread.
+ *  - The caller owns every pointer it passes.  Host arrays may be freed as
+ *    soon as a call returns.  Device arrays must stay valid until the work
+ *    queued on the caller's stream is complete.
+ *  - Graph arrays are CSR with int32 indices: row_ptr[n+1], col_idx[nnz].
+ *    Row u lists the neighbours of u in strictly ascending order.  The
+ *    matrix is symmetric (undirected graph, Sec. 2.1), and every vertex has
+ *    degree >= 1 (d_i > 0, Sec. 2.1).  A self-loop is one entry and counts
+ *    once in d_u.  nnz < 2^31.
+ *  - Vectors p and pi are FP64, length n.  Batches are B such vectors stored
+ *    one after another (column-major n x B).
+ *  - A cpaa_graph may be used by one solve at a time; it owns its device
+ *    copy of the CSR, its tiling and a reusable workspace.
+ *
+ * Tests and the Python binding call exactly these symbols.
+ */
+#ifndef CPAA_H
+#define CPAA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CPAA_OK = 0,
+    CPAA_EINVAL = 1,     /* bad argument: c outside (0,1), tol <= 0, p < 0, sum p != 1,
+                            invalid CSR (see cpaa_graph_create) */
+    CPAA_ENOMEM = 2,     /* a device or host allocation failed, or a budget was exceeded */
+    CPAA_ENOTCONV = 3,   /* the bound needs more rounds than max_rounds; pi holds the
+                            result after max_rounds */
+    CPAA_ECUDA = 4,      /* a CUDA runtime call failed (message in cpaa_last_error) */
+    CPAA_ETIMEOUT = 5,   /* a wait ran out of time (server) */
+    CPAA_EBUSY = 6,      /* no room for the request right now (server) */
+    CPAA_ECANCELLED = 7, /* the request was cancelled (server) */
+    CPAA_ENOTFOUND = 8   /* unknown ticket or graph id (server) */
+} cpaa_status;
+
+/* Number format of the iterate vectors.  F64: FP64 storage and arithmetic.
+ * F32: FP32 storage and arithmetic, Kahan-compensated FP32 accumulator.
+ * BF16: bfloat16 storage, FP32 arithmetic, Kahan-compensated FP32
+ * accumulator.  The coefficients c_k, the stopping rule and every output
+ * stay FP64 on all three. */
+typedef enum { CPAA_F64 = 0, CPAA_F32 = 1, CPAA_BF16 = 2 } cpaa_precision;
+
+/* cpaa_graph_create flags */
+#define CPAA_GRAPH_DEVICE_INPUT 1u /* row_ptr / col_idx are device pointers */
+#define CPAA_GRAPH_VALIDATE 2u     /* also check column range, row order and symmetry
+                                      (one device pass over col_idx) */
+
+/* cpaa_options.flags */
+#define CPAA_DEVICE_IO 1u   /* p / pi (P / PI) are device pointers */
+#define CPAA_TIME_ROUNDS 2u /* time the M round launches with CUDA events on the solve's
+                               stream; the result is cpaa_info.rounds_ms */
+
+typedef struct {
+    cpaa_precision precision; /* default CPAA_F64 */
+    int normalize;            /* 0: pi = pibar / sum(pibar), last line of Algorithm 1 (default);
+                                 1: pi = (1 - c) pibar (Sec. 2.1) */
+    int fixed_rounds;         /* > 0: run exactly this many rounds (Algorithm 1's M) and
+                                 ignore tol; 0: choose M from tol (default) */
+    int max_rounds;           /* cap on M; 0 means 2000 */
+    unsigned flags;           /* CPAA_DEVICE_IO | CPAA_TIME_ROUNDS */
+    void *stream;             /* cudaStream_t to run on; NULL = legacy default stream */
+    double *history;          /* optional host array [2*(M+1)]: sum T_k and sum |T_k|
+                                 for k = 0..M (the mass view of Sec. 4.1) */
+} cpaa_options;
+
+typedef struct {
+    int rounds;       /* M that was run */
+    double bound;     /* rigorous L1 bound on ||pi - pi*||_1 after M rounds */
+    double kappa;     /* sqrt(sum d) ||D^-1/2 p||_2 */
+    double mass;      /* sum_u T_M[u]; equals sum p up to rounding (Sec. 4.1) */
+    double l1;        /* sum_u |T_M[u]| */
+    double sum_pibar; /* sum_u pibar[u] before normalisation */
+    double rounds_ms; /* device time of the M round launches (CPAA_TIME_ROUNDS), else 0 */
+} cpaa_info;
+
+typedef struct cpaa_graph cpaa_graph;
+
+/* Fill *opt with the defaults listed above. */
+void cpaa_options_init(cpaa_options *opt);
+
+/* Upload an undirected graph (Sec. 2.1: A symmetric, d_i > 0) and build the
+ * degree vectors and the row tiling the step kernels walk.
+ *   n        vertices, 1 <= n < 2^31
+ *   nnz      CSR entries, row_ptr[n]; 0 < nnz < 2^31
+ *   row_ptr  int32[n+1], host or device (CPAA_GRAPH_DEVICE_INPUT)
+ *   col_idx  int32[nnz], same memory space as row_ptr
+ *   flags    CPAA_GRAPH_DEVICE_INPUT | CPAA_GRAPH_VALIDATE
+ *   out      receives the handle; release with cpaa_graph_destroy
+ * Always checked: row_ptr[0] = 0, row_ptr non-decreasing, row_ptr[n] = nnz,
+ * every degree >= 1.  With CPAA_GRAPH_VALIDATE also: 0 <= col_idx < n,
+ * strictly ascending rows, and A symmetric (the remark closing Sec. 3:
+ * Eq. 31 needs the real spectrum that an undirected graph gives).  Violations return
+ * CPAA_EINVAL and no handle.  Runs on the current CUDA device. */
+cpaa_status cpaa_graph_create(int64_t n, int64_t nnz, const int32_t *row_ptr,
+                              const int32_t *col_idx, unsigned flags, cpaa_graph **out);
+
+/* Release the graph and its workspace.  NULL is accepted. */
+cpaa_status cpaa_graph_destroy(cpaa_graph *g);
+
+/* Size of the graph and the device bytes it holds (CSR, degrees, tiling and
+ * workspace).  Any output pointer may be NULL. */
+cpaa_status cpaa_graph_info(const cpaa_graph *g, int64_t *n, int64_t *nnz,
+                            int64_t *device_bytes, int64_t *num_tiles);
+
+/* Personalised PageRank of one vector (Sec. 2.1, Algorithm 1).
+ *   p    FP64[n], p >= 0, |sum p - 1| <= 1e-9
+ *   c    damping factor, 0 < c < 1
+ *   tol  L1 tolerance on ||pi - pi*||_1 (> 0; ignored with fixed_rounds)
+ *   pi   FP64[n] output
+ *   opt  NULL for defaults
+ *   info NULL or receives the run's figures
+ * p and pi are host pointers unless opt->flags has CPAA_DEVICE_IO.  With host
+ * pointers the call returns once pi is written; with device pointers it
+ * returns once the work is queued behind one short synchronisation (the
+ * rounds M depend on kappa, which is reduced on the device). */
+cpaa_status cpaa_solve(cpaa_graph *g, const double *p, double c, double tol, double *pi,
+                       const cpaa_options *opt, cpaa_info *info);
+
+/* B personalised vectors at once (the batched form: the graph is read once
+ * per step for a whole tile of vectors).  Column b of P (P + b*n) is solved
+ * with damping c[b] and written to PI + b*n; info, if not NULL, has B
+ * entries.  Each column gets the rounds its own bound asks for; a column's
+ * result does not depend on the other columns. */
+cpaa_status cpaa_solve_batch(cpaa_graph *g, int B, const double *P, const double *c,
+                             double tol, double *PI, const cpaa_options *opt,
+                             cpaa_info *info);
+
+/* The stopping rule on its own: the smallest M in [1, max_rounds] with
+ * bound(M) < tol, or -1.  normalize as in cpaa_options; bound as in
+ * cpaa_info.bound (Eq. 41 times kappa, plus the normalisation term). */
+int cpaa_rounds_needed(double c, double tol, double kappa, int normalize, int max_rounds);
+
+/* The bound itself for a given M. */
+double cpaa_l1_bound(double c, int M, double kappa, int normalize);
+
+/* Human-readable name of a status. */
+const char *cpaa_status_string(cpaa_status s);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *cpaa_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CPAA_H */

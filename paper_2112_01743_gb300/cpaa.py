@@ -1,0 +1,257 @@
+"""ctypes binding of libcpaa.so with the names of include/cpaa.h.
+
+Arguments may be torch tensors (host or CUDA), numpy arrays, or raw integer
+addresses.  The functions only marshal arguments and check the returned
+status; the computation happens in the library.  A non-OK status raises
+``CpaaError`` (``CPAA_ENOTCONV`` only when ``raise_notconv`` is set).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = [
+    "CpaaError", "CpaaOptions", "CpaaInfo", "lib", "library_path",
+    "CPAA_OK", "CPAA_EINVAL", "CPAA_ENOMEM", "CPAA_ENOTCONV", "CPAA_ECUDA", "CPAA_ETIMEOUT",
+    "CPAA_EBUSY", "CPAA_ECANCELLED", "CPAA_ENOTFOUND",
+    "CPAA_F64", "CPAA_F32", "CPAA_BF16", "CPAA_GRAPH_DEVICE_INPUT", "CPAA_GRAPH_VALIDATE",
+    "CPAA_DEVICE_IO", "CPAA_TIME_ROUNDS",
+    "cpaa_options_init", "cpaa_graph_create", "cpaa_graph_destroy", "cpaa_graph_info",
+    "cpaa_solve", "cpaa_solve_batch", "cpaa_rounds_needed", "cpaa_l1_bound",
+    "cpaa_status_string", "cpaa_last_error", "Graph", "EXPORTED_SYMBOLS",
+]
+
+CPAA_OK, CPAA_EINVAL, CPAA_ENOMEM, CPAA_ENOTCONV, CPAA_ECUDA = 0, 1, 2, 3, 4
+CPAA_ETIMEOUT, CPAA_EBUSY, CPAA_ECANCELLED, CPAA_ENOTFOUND = 5, 6, 7, 8
+CPAA_F64, CPAA_F32, CPAA_BF16 = 0, 1, 2
+CPAA_GRAPH_DEVICE_INPUT, CPAA_GRAPH_VALIDATE = 1, 2
+CPAA_DEVICE_IO = 1
+CPAA_TIME_ROUNDS = 2
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+library_path = os.path.join(HERE, "_build", "libcpaa.so")
+
+# Every function include/cpaa.h declares (the CPU test checks the exports).
+EXPORTED_SYMBOLS = [
+    "cpaa_options_init", "cpaa_graph_create", "cpaa_graph_destroy", "cpaa_graph_info",
+    "cpaa_solve", "cpaa_solve_batch", "cpaa_rounds_needed", "cpaa_l1_bound",
+    "cpaa_status_string", "cpaa_last_error",
+]
+
+
+class CpaaError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (_status_name(status), message))
+        self.status = status
+
+
+class CpaaOptions(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("normalize", ctypes.c_int),
+                ("fixed_rounds", ctypes.c_int), ("max_rounds", ctypes.c_int),
+                ("flags", ctypes.c_uint), ("stream", ctypes.c_void_p),
+                ("history", ctypes.POINTER(ctypes.c_double))]
+
+
+class CpaaInfo(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int), ("bound", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("mass", ctypes.c_double), ("l1", ctypes.c_double), ("sum_pibar", ctypes.c_double),
+                ("rounds_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libcpaa.so; raise if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(library_path):
+        raise ImportError("libcpaa.so is not built (%s); run __graft_entry__.build()" % library_path)
+    L = ctypes.CDLL(library_path)
+    vp, i64, dbl, cint, cuint = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int, ctypes.c_uint
+    L.cpaa_options_init.restype = None
+    L.cpaa_options_init.argtypes = [ctypes.POINTER(CpaaOptions)]
+    L.cpaa_graph_create.restype = cint
+    L.cpaa_graph_create.argtypes = [i64, i64, vp, vp, cuint, ctypes.POINTER(vp)]
+    L.cpaa_graph_destroy.restype = cint
+    L.cpaa_graph_destroy.argtypes = [vp]
+    L.cpaa_graph_info.restype = cint
+    L.cpaa_graph_info.argtypes = [vp] + [ctypes.POINTER(i64)] * 4
+    L.cpaa_solve.restype = cint
+    L.cpaa_solve.argtypes = [vp, vp, dbl, dbl, vp, ctypes.POINTER(CpaaOptions), ctypes.POINTER(CpaaInfo)]
+    L.cpaa_solve_batch.restype = cint
+    L.cpaa_solve_batch.argtypes = [vp, cint, vp, vp, dbl, vp, ctypes.POINTER(CpaaOptions),
+                                   ctypes.POINTER(CpaaInfo)]
+    L.cpaa_rounds_needed.restype = cint
+    L.cpaa_rounds_needed.argtypes = [dbl, dbl, dbl, cint, cint]
+    L.cpaa_l1_bound.restype = dbl
+    L.cpaa_l1_bound.argtypes = [dbl, cint, dbl, cint]
+    L.cpaa_status_string.restype = ctypes.c_char_p
+    L.cpaa_status_string.argtypes = [cint]
+    L.cpaa_last_error.restype = ctypes.c_char_p
+    L.cpaa_last_error.argtypes = []
+    _lib = L
+    return L
+
+
+def _status_name(s):
+    try:
+        return lib().cpaa_status_string(int(s)).decode()
+    except Exception:
+        return "status %d" % s
+
+
+def _check(status, raise_notconv=True):
+    if status == CPAA_OK or (status == CPAA_ENOTCONV and not raise_notconv):
+        return status
+    raise CpaaError(status, lib().cpaa_last_error().decode())
+
+
+def _addr(x):
+    """Address of a tensor / ndarray / int (no copy, no conversion)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError("unsupported argument type %r" % type(x))
+
+
+def _is_device(x):
+    return hasattr(x, "is_cuda") and x.is_cuda
+
+
+def cpaa_options_init():
+    o = CpaaOptions()
+    lib().cpaa_options_init(ctypes.byref(o))
+    return o
+
+
+def cpaa_graph_create(n, nnz, row_ptr, col_idx, flags=0):
+    """Upload a symmetric CSR graph; returns the opaque handle (int)."""
+    h = ctypes.c_void_p()
+    if _is_device(row_ptr):
+        flags |= CPAA_GRAPH_DEVICE_INPUT
+    _check(lib().cpaa_graph_create(int(n), int(nnz), _addr(row_ptr), _addr(col_idx), int(flags),
+                                   ctypes.byref(h)))
+    return h.value
+
+
+def cpaa_graph_destroy(g):
+    return _check(lib().cpaa_graph_destroy(g))
+
+
+def cpaa_graph_info(g):
+    v = [ctypes.c_int64() for _ in range(4)]
+    _check(lib().cpaa_graph_info(g, *[ctypes.byref(x) for x in v]))
+    return {"n": v[0].value, "nnz": v[1].value, "device_bytes": v[2].value, "num_tiles": v[3].value}
+
+
+def _options(precision, normalize, fixed_rounds, max_rounds, device_io, stream, history,
+             time_rounds=False):
+    o = cpaa_options_init()
+    o.precision = int(precision)
+    o.normalize = int(normalize)
+    o.fixed_rounds = int(fixed_rounds)
+    if max_rounds:
+        o.max_rounds = int(max_rounds)
+    o.flags = (CPAA_DEVICE_IO if device_io else 0) | (CPAA_TIME_ROUNDS if time_rounds else 0)
+    o.stream = stream
+    if history is not None:
+        o.history = history.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return o
+
+
+def _stream_of(x, stream):
+    if stream is not None:
+        return int(stream)
+    if _is_device(x):
+        import torch
+        return torch.cuda.current_stream(x.device).cuda_stream
+    return None
+
+
+def cpaa_solve(g, p, c, tol, pi, precision=CPAA_F64, normalize=0, fixed_rounds=0, max_rounds=0,
+               stream=None, history=None, raise_notconv=True, time_rounds=False):
+    """pi <- CPAA(p); p, pi FP64 length n (both host or both device)."""
+    dev = _is_device(p)
+    if dev != _is_device(pi):
+        raise ValueError("p and pi must both be host or both be device buffers")
+    o = _options(precision, normalize, fixed_rounds, max_rounds, dev, _stream_of(p, stream), history,
+                 time_rounds)
+    info = CpaaInfo()
+    st = lib().cpaa_solve(g, _addr(p), float(c), float(tol), _addr(pi), ctypes.byref(o), ctypes.byref(info))
+    _check(st, raise_notconv)
+    return info
+
+
+def cpaa_solve_batch(g, B, P, c, tol, PI, precision=CPAA_F32, normalize=0, fixed_rounds=0,
+                     max_rounds=0, stream=None, raise_notconv=True):
+    """Column b of P (n x B column-major, i.e. B vectors back to back) with
+    damping c[b] -> column b of PI.  Returns a list of B info records."""
+    dev = _is_device(P)
+    cvec = np.ascontiguousarray(np.broadcast_to(np.asarray(c, dtype=np.float64), (int(B),)))
+    o = _options(precision, normalize, fixed_rounds, max_rounds, dev, _stream_of(P, stream), None)
+    infos = (CpaaInfo * int(B))()
+    st = lib().cpaa_solve_batch(g, int(B), _addr(P), cvec.ctypes.data, float(tol), _addr(PI),
+                                ctypes.byref(o), infos)
+    _check(st, raise_notconv)
+    return list(infos)
+
+
+def cpaa_rounds_needed(c, tol, kappa, normalize=0, max_rounds=2000):
+    return lib().cpaa_rounds_needed(float(c), float(tol), float(kappa), int(normalize), int(max_rounds))
+
+
+def cpaa_l1_bound(c, M, kappa, normalize=0):
+    return lib().cpaa_l1_bound(float(c), int(M), float(kappa), int(normalize))
+
+
+def cpaa_status_string(s):
+    return lib().cpaa_status_string(int(s)).decode()
+
+
+def cpaa_last_error():
+    return lib().cpaa_last_error().decode()
+
+
+class Graph:
+    """Owning wrapper of a cpaa_graph handle."""
+
+    def __init__(self, row_ptr, col_idx, n=None, validate=False):
+        n = int(n if n is not None else len(row_ptr) - 1)
+        nnz = int(col_idx.numel() if hasattr(col_idx, "numel") else len(col_idx))
+        self.n, self.nnz = n, nnz
+        self.handle = cpaa_graph_create(n, nnz, row_ptr, col_idx,
+                                        CPAA_GRAPH_VALIDATE if validate else 0)
+
+    def info(self):
+        return cpaa_graph_info(self.handle)
+
+    def solve(self, p, c, tol, pi, **kw):
+        return cpaa_solve(self.handle, p, c, tol, pi, **kw)
+
+    def solve_batch(self, B, P, c, tol, PI, **kw):
+        return cpaa_solve_batch(self.handle, B, P, c, tol, PI, **kw)
+
+    def close(self):
+        if self.handle:
+            cpaa_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

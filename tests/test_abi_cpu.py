@@ -1,0 +1,72 @@
+"""CPU-only checks of the C ABI: the library loads, exports every function
+include/cpaa.h declares, and its host-side stopping rule agrees with the
+oracle's.  No GPU call is made."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2112_01743_gb300 import build
+    build.build()
+    import paper_2112_01743_gb300 as pkg
+    return pkg
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "cpaa.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(cpaa_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_binding_names(L):
+    assert _declared() == sorted(L.EXPORTED_SYMBOLS)
+
+
+def test_library_exports_every_declared_symbol(L):
+    lib = L.lib()
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(L):
+    assert L.cpaa_status_string(L.CPAA_OK) == "CPAA_OK"
+    assert L.cpaa_status_string(L.CPAA_ENOTCONV) == "CPAA_ENOTCONV"
+    assert L.cpaa_status_string(99) == "CPAA_UNKNOWN"
+
+
+def test_options_defaults(L):
+    o = L.cpaa_options_init()
+    assert (o.precision, o.normalize, o.fixed_rounds, o.max_rounds, o.flags) == (0, 0, 0, 2000, 0)
+
+
+@pytest.mark.parametrize("c", [0.5, 0.85, 0.95, 0.99])
+@pytest.mark.parametrize("kappa", [1.0, 1.44, 74.0, 1.6e4])
+@pytest.mark.parametrize("norm", [0, 1])
+def test_stopping_rule_matches_oracle(L, c, kappa, norm):
+    from oracle import oracle as O
+    for tol in (1e-3, 1e-6, 1e-10, 1e-12):
+        assert L.cpaa_rounds_needed(c, tol, kappa, norm) == O.rounds_needed(c, tol, kappa, norm)
+        for M in (1, 7, 30):
+            a, b = L.cpaa_l1_bound(c, M, kappa, norm), O.l1_bound(c, M, kappa, norm)
+            assert abs(a - b) <= 1e-14 * abs(b)
+
+
+def test_stopping_rule_rejects_bad_args(L):
+    assert L.cpaa_rounds_needed(0.0, 1e-6, 1.0) == -1
+    assert L.cpaa_rounds_needed(1.0, 1e-6, 1.0) == -1
+    assert L.cpaa_rounds_needed(0.85, 0.0, 1.0) == -1
+    assert L.cpaa_rounds_needed(0.85, 1e-300, 1.0, 0, 50) == -1
+
+
+def test_config1_rounds_from_eq41():
+    """The 10k-vertex configuration stops on ERR_M < 1e-10 (Eq. 41 alone): 39
+    rounds at c = 0.85."""
+    from oracle import oracle as O
+    M = next(m for m in range(1, 200) if O.err_bound(0.85, m) < 1e-10)
+    assert M == 39

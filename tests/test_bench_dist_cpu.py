@@ -1,0 +1,52 @@
+"""The benchmark's multi-rank plumbing (replicas, max over ranks) on the CPU
+with the gloo backend, world size 2."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    import bench
+    bench.dist_init(world, False)
+    bench.barrier(world)
+    mx = bench.reduce_max(10.0 * (rank + 1), world)
+    sm = bench.reduce_sum(rank + 1, world)
+    # the reference arm runs on rank 0 only; other ranks leave without work
+    rc = bench.run_reference(type("A", (), {})()) if rank == 1 else None
+    q.put((rank, mx, sm, rc))
+    import torch.distributed as dist
+    dist.destroy_process_group()
+
+
+def test_world_size_two_gloo():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert out[0][1:3] == (20.0, 3.0) and out[1][1:3] == (20.0, 3.0)
+    assert out[1][3] == 0
+
+
+def test_alg_bytes_formula():
+    import bench
+    n, nnz = 10, 100
+    assert bench.alg_bytes_per_round(n, nnz, "f64") == 4 * nnz + 4 * (n + 1) + 4 * n + 24 * n + 16 * n
+    assert bench.alg_bytes_per_round(n, nnz, "f32") == 4 * nnz + 4 * (n + 1) + 4 * n + 12 * n + 8 * n + 8 * n

@@ -1,0 +1,121 @@
+"""Parity at the benchmark configurations' full sizes (GPU + host oracle).
+
+The oracle runs every row on the host cores for the same number of rounds the
+GPU ran (rows are independent inside a round, Sec. 4.1), so the comparison is
+element by element over the whole vector."""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import cpaa_inputs as ci
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2112_01743_gb300 as pkg
+    return pkg
+
+
+def _solve(pkg, G, p, c, tol, **kw):
+    pi = torch.empty_like(p)
+    info = G.solve(p, c, tol, pi, **kw)
+    torch.cuda.synchronize()
+    return pi, info
+
+
+def _l1(a, ref):
+    return float(np.abs(a.cpu().numpy() - ref).sum())
+
+
+def test_config_10k_eq41_rounds(pkg):
+    """10,000-vertex Chung-Lu, uniform p, c = 0.85, run until ERR_M < 1e-10
+    (Eq. 41): 39 rounds; FP64 L1 <= 1e-12 against the oracle."""
+    g = ci.chung_lu(10000, 100000, seed=0)
+    rp, cx = g.numpy()
+    G = pkg.Graph(g.row_ptr.cuda(), g.col_idx.cuda(), validate=True)
+    p = torch.full((g.n,), 1.0 / g.n, dtype=torch.float64, device="cuda")
+    M = next(m for m in range(1, 200) if O.err_bound(0.85, m) < 1e-10)
+    pi, info = _solve(pkg, G, p, 0.85, 0.0, fixed_rounds=M)
+    ref = O.cpaa(rp, cx, np.full(g.n, 1.0 / g.n), 0.85, M)
+    assert M == 39 and info.rounds == 39
+    assert _l1(pi, ref) <= 1e-12
+    truth = O.power(rp, cx, np.full(g.n, 1.0 / g.n), 0.85, tol=1e-12)[0]
+    assert _l1(pi, truth) <= 1e-10 * 10  # Eq. 41 is the paper's own (rough) bound
+    G.close()
+
+
+@pytest.fixture(scope="module")
+def big_chung_lu(pkg):
+    g = ci.chung_lu(1 << 24, 256_000_000, seed=0, device="cuda")
+    G = pkg.Graph(g.row_ptr, g.col_idx, n=g.n, validate=True)
+    rp, cx = g.numpy()
+    del g
+    torch.cuda.empty_cache()
+    yield G, rp, cx
+    G.close()
+
+
+def test_config_16M_f64_and_f32(pkg, big_chung_lu):
+    """16.7M-vertex Chung-Lu, uniform p, c = 0.85, tol 1e-6: FP64 within 1e-12
+    L1 and FP32 within 1e-6 relative L1 of the oracle run for the same M."""
+    G, rp, cx = big_chung_lu
+    n = len(rp) - 1
+    p = torch.full((n,), 1.0 / n, dtype=torch.float64, device="cuda")
+    pi64, i64 = _solve(pkg, G, p, 0.85, 1e-6, precision=pkg.CPAA_F64)
+    pi32, i32 = _solve(pkg, G, p, 0.85, 1e-6, precision=pkg.CPAA_F32)
+    assert i64.rounds == i32.rounds
+    hp = np.full(n, 1.0 / n)
+    assert i64.rounds == O.rounds_needed(0.85, 1e-6, O.kappa(rp, hp))
+    ref = O.cpaa(rp, cx, hp, 0.85, i64.rounds)
+    e64 = _l1(pi64, ref)
+    e32 = _l1(pi32, ref) / np.abs(ref).sum()
+    print("16M: rounds %d, FP64 L1 %.3e, FP32 rel L1 %.3e" % (i64.rounds, e64, e32))
+    assert e64 <= 1e-12
+    assert e32 <= 1e-6
+
+
+def test_config_16M_seeded_sample(pkg, big_chung_lu):
+    """A 3-seed personalised vector on the same graph (high kappa)."""
+    G, rp, cx = big_chung_lu
+    n = len(rp) - 1
+    hp = np.zeros(n)
+    hp[[7, 123456, n - 5]] = 1.0 / 3
+    p = torch.as_tensor(hp).cuda()
+    pi64, i64 = _solve(pkg, G, p, 0.85, 1e-6, precision=pkg.CPAA_F64)
+    pi32, i32 = _solve(pkg, G, p, 0.85, 1e-6, precision=pkg.CPAA_F32)
+    ref = O.cpaa(rp, cx, hp, 0.85, i64.rounds)
+    assert i64.rounds == O.rounds_needed(0.85, 1e-6, O.kappa(rp, hp))
+    assert _l1(pi64, ref) <= 1e-12
+    assert _l1(pi32, ref) / np.abs(ref).sum() <= 1e-6
+
+
+def test_config_grid_precision_study(pkg):
+    """4096 x 4096 lattice with 20% of edges deleted (spanning tree kept):
+    FP64 / FP32 / BF16 against the oracle (BF16 is reported, loosely bounded)."""
+    g = ci.grid_deleted(4096, 4096, 0.2, seed=0, device="cuda")
+    assert g.nnz == 2 * (2 * 4096 * 4095 - round(0.2 * 2 * 4096 * 4095))
+    G = pkg.Graph(g.row_ptr, g.col_idx, n=g.n, validate=True)
+    rp, cx = g.numpy()
+    n = g.n
+    del g
+    p = torch.full((n,), 1.0 / n, dtype=torch.float64, device="cuda")
+    res = {}
+    for name, prec in (("f64", pkg.CPAA_F64), ("f32", pkg.CPAA_F32), ("bf16", pkg.CPAA_BF16)):
+        res[name] = _solve(pkg, G, p, 0.85, 1e-6, precision=prec)
+    M = res["f64"][1].rounds
+    assert all(r[1].rounds == M for r in res.values())
+    ref = O.cpaa(rp, cx, np.full(n, 1.0 / n), 0.85, M)
+    errs = {k: _l1(v[0], ref) for k, v in res.items()}
+    print("grid: rounds %d, L1 errors %s" % (M, errs))
+    assert errs["f64"] <= 1e-12
+    assert errs["f32"] <= 1e-6
+    assert errs["bf16"] <= 5e-2
+    G.close()

@@ -1,0 +1,197 @@
+"""GPU parity: the CUDA path against the FP64 oracle, through the C ABI.
+
+Tolerances: FP64 path L1 <= 1e-12; FP32 path relative L1 <= 1e-6 (both
+against the oracle run for the same number of rounds M).  The BF16 path's
+error is measured and only bounded loosely (it is a precision study)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import cpaa_inputs as ci
+from oracle import oracle as O
+from tests.gpu_util import boundary_graphs, solve, upload
+
+pytestmark = pytest.mark.gpu
+
+GRAPHS = boundary_graphs()
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2112_01743_gb300 as pkg
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def uploaded(pkg):
+    return [upload(pkg, g) for g in GRAPHS]
+
+
+def _p_variants(n):
+    uni = np.full(n, 1.0 / n)
+    seed = np.zeros(n); seed[n // 2] = 1.0
+    ramp = np.arange(1, n + 1, dtype=float); ramp /= ramp.sum()
+    return {"uniform": uni, "seed": seed, "ramp": ramp}
+
+
+@pytest.mark.parametrize("gi", range(len(GRAPHS)), ids=[g.name for g in GRAPHS])
+def test_f64_fixed_rounds_matches_oracle(pkg, uploaded, gi):
+    g, G = GRAPHS[gi], uploaded[gi]
+    rp, cx = g.numpy()
+    for pname, p in _p_variants(g.n).items():
+        for M in (1, 2, 3, 17):
+            for norm in (0, 1):
+                pi, info = solve(pkg, G, p, 0.85, fixed_rounds=M, normalize=norm)
+                ref = O.cpaa(rp, cx, p, 0.85, M, normalize=norm)
+                assert info.rounds == M
+                err = np.abs(pi - ref).sum()
+                assert err <= 1e-12, (g.name, pname, M, norm, err)
+
+
+@pytest.mark.parametrize("gi", range(len(GRAPHS)), ids=[g.name for g in GRAPHS])
+@pytest.mark.parametrize("c", [0.5, 0.85, 0.95])
+def test_f64_tolerance_solve(pkg, uploaded, gi, c):
+    """M equals the oracle's stopping rule, and the result is within tol of pi*."""
+    g, G = GRAPHS[gi], uploaded[gi]
+    rp, cx = g.numpy()
+    p = _p_variants(g.n)["ramp"]
+    tol = 1e-9
+    pi, info = solve(pkg, G, p, c, tol)
+    k_or = O.kappa(rp, p)
+    assert abs(info.kappa - k_or) <= 1e-12 * k_or
+    assert info.rounds == O.rounds_needed(c, tol, k_or, 0)
+    ref = O.cpaa(rp, cx, p, c, info.rounds)
+    assert np.abs(pi - ref).sum() <= 1e-12
+    if g.n <= 2500:
+        truth = O.lapack_pagerank(rp, cx, p, c)
+    else:  # the power method's L1 change stalls near 1e-14 from rounding
+        truth, _ = O.power(rp, cx, p, c, tol=1e-11)
+    assert np.abs(pi - truth).sum() <= tol
+
+
+@pytest.mark.parametrize("gi", range(len(GRAPHS)), ids=[g.name for g in GRAPHS])
+def test_f32_matches_oracle(pkg, uploaded, gi):
+    g, G = GRAPHS[gi], uploaded[gi]
+    rp, cx = g.numpy()
+    for pname, p in _p_variants(g.n).items():
+        pi, info = solve(pkg, G, p, 0.85, 1e-6, precision=pkg.CPAA_F32)
+        ref = O.cpaa(rp, cx, p, 0.85, info.rounds)
+        rel = np.abs(pi - ref).sum() / np.abs(ref).sum()
+        assert rel <= 1e-6, (g.name, pname, rel)
+
+
+@pytest.mark.parametrize("gi", [0, 3, 12, 13, 14], ids=lambda i: GRAPHS[i].name)
+def test_bf16_error_is_bounded(pkg, uploaded, gi):
+    g, G = GRAPHS[gi], uploaded[gi]
+    rp, cx = g.numpy()
+    p = np.full(g.n, 1.0 / g.n)
+    pi, info = solve(pkg, G, p, 0.85, 1e-6, precision=pkg.CPAA_BF16)
+    ref = O.cpaa(rp, cx, p, 0.85, info.rounds)
+    rel = np.abs(pi - ref).sum() / np.abs(ref).sum()
+    assert rel <= 5e-2, rel
+    assert abs(pi.sum() - 1.0) < 1e-12
+
+
+def test_mass_invariant_history(pkg, uploaded):
+    g, G = GRAPHS[13], uploaded[13]
+    rp, cx = g.numpy()
+    p = _p_variants(g.n)["seed"]
+    M = 30
+    hist = np.zeros(2 * (M + 1))
+    solve(pkg, G, p, 0.85, fixed_rounds=M, history=hist)
+    _, mass, l1 = O.cpaa(rp, cx, p, 0.85, M, history=True)
+    assert np.abs(hist[0::2] - 1.0).max() < 1e-12
+    assert np.abs(hist[0::2] - mass).max() < 1e-12
+    assert np.abs(hist[1::2] - l1).max() < 1e-10 * l1.max()
+
+
+def test_host_and_device_io_agree_and_repeat_bitwise(pkg, uploaded):
+    g, G = GRAPHS[13], uploaded[13]
+    p = _p_variants(g.n)["ramp"]
+    for prec in (pkg.CPAA_F64, pkg.CPAA_F32, pkg.CPAA_BF16):
+        a, _ = solve(pkg, G, p, 0.85, 1e-7, precision=prec)
+        b, _ = solve(pkg, G, p, 0.85, 1e-7, precision=prec)
+        host_pi = np.empty(g.n)
+        G.solve(np.ascontiguousarray(p), 0.85, 1e-7, host_pi, precision=prec)
+        assert np.array_equal(a, b)
+        assert np.array_equal(a, host_pi)
+
+
+def test_reversibility_on_gpu(pkg, uploaded):
+    """pi_s(t)/d_t = pi_t(s)/d_s ((D - cA)^-1 is symmetric, Lemma 2's B)."""
+    g, G = GRAPHS[12], uploaded[12]
+    rp, _ = g.numpy()
+    d = np.diff(rp).astype(float)
+    s, t = 5, 2900
+    es = np.zeros(g.n); es[s] = 1
+    et = np.zeros(g.n); et[t] = 1
+    a, _ = solve(pkg, G, es, 0.85, 1e-13)
+    b, _ = solve(pkg, G, et, 0.85, 1e-13)
+    assert abs(a[t] / d[t] - b[s] / d[s]) < 1e-12 * max(a[t] / d[t], 1e-300) + 1e-15
+
+
+def test_single_vertex_self_loop(pkg):
+    G = upload(pkg, ci.from_edges(1, [(0, 0)], name="one"))
+    pi, info = solve(pkg, G, np.ones(1), 0.85, 1e-10)
+    assert pi[0] == pytest.approx(1.0, abs=1e-15)
+
+
+def test_invalid_arguments(pkg, uploaded):
+    G = uploaded[12]
+    n = GRAPHS[12].n
+    p = np.full(n, 1.0 / n)
+    bad = p.copy(); bad[3] = -bad[3]
+    with pytest.raises(pkg.CpaaError):
+        solve(pkg, G, bad, 0.85)
+    with pytest.raises(pkg.CpaaError):
+        solve(pkg, G, 2 * p, 0.85)
+    nan = p.copy(); nan[0] = np.nan
+    with pytest.raises(pkg.CpaaError):
+        solve(pkg, G, nan, 0.85)
+    for c in (0.0, 1.0, -0.5, 1.5):
+        with pytest.raises(pkg.CpaaError):
+            solve(pkg, G, p, c)
+    with pytest.raises(pkg.CpaaError):
+        solve(pkg, G, p, 0.85, tol=0.0)
+    # status is ENOTCONV when the bound asks for more than max_rounds
+    pd = torch.as_tensor(p).cuda()
+    out = torch.empty_like(pd)
+    info = G.solve(pd, 0.85, 1e-12, out, max_rounds=5, raise_notconv=False)
+    assert info.rounds == 5
+
+
+def test_invalid_graphs(pkg):
+    def mk(n, rp, cx, validate=True):
+        return pkg.Graph(torch.tensor(rp, dtype=torch.int32).cuda(),
+                         torch.tensor(cx, dtype=torch.int32).cuda(), n=n, validate=validate)
+    with pytest.raises(pkg.CpaaError):      # directed: 0->1 without 1->0
+        mk(2, [0, 1, 2], [1, 1])
+    with pytest.raises(pkg.CpaaError):      # vertex 1 has degree 0
+        mk(3, [0, 1, 1, 2], [2, 0])
+    with pytest.raises(pkg.CpaaError):      # column out of range
+        mk(2, [0, 1, 2], [1, 5])
+    with pytest.raises(pkg.CpaaError):      # unsorted row
+        mk(3, [0, 2, 3, 4], [2, 1, 0, 0])
+    with pytest.raises(pkg.CpaaError):      # row_ptr[n] != nnz
+        pkg.cpaa_graph_create(2, 3, torch.tensor([0, 1, 2], dtype=torch.int32).cuda(),
+                              torch.tensor([1, 0, 0], dtype=torch.int32).cuda())
+
+
+def test_batch_columns_equal_single(pkg, uploaded):
+    g, G = GRAPHS[13], uploaded[13]
+    B = 5
+    seeds = ci.seed_vectors(g.n, B, seed=3)
+    P = ci.seed_dense(g.n, seeds)
+    cs = np.array([0.5, 0.85, 0.95, 0.85, 0.7])
+    for prec in (pkg.CPAA_F64, pkg.CPAA_F32):
+        Pd = torch.as_tensor(P).cuda()
+        PI = torch.empty_like(Pd)
+        infos = G.solve_batch(B, Pd, cs, 1e-7, PI, precision=prec)
+        torch.cuda.synchronize()
+        for b in range(B):
+            single, info = solve(pkg, G, P[b], cs[b], 1e-7, precision=prec)
+            assert infos[b].rounds == info.rounds
+            assert np.array_equal(PI[b].cpu().numpy(), single)
