@@ -151,6 +151,41 @@ cpaa_status cpaa_solve_batch(cpaa_graph *g, int B, const double *P, const double
                              double tol, double *PI, const cpaa_options *opt,
                              cpaa_info *info);
 
+/* Largest n that cpaa_solve_fixed_noalloc accepts.  That call keeps two FP64
+ * iterate vectors and an FP64 accumulator (24 bytes per vertex) plus a small
+ * reduction area in a fixed 32 MiB scratch array per GPU. */
+#define CPAA_NOALLOC_MAX_N 1300000
+
+/* Solve without allocating any memory.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory
+ * themselves -- code running inside an application whose allocator owns the
+ * device (a framework's caching allocator or a fixed arena), a process held to
+ * a strict memory budget, or a loop that cannot afford the device-wide
+ * synchronisation cudaMalloc / cudaFree can cause.  It calls no allocation
+ * routine; all its intermediate vectors live in one 32 MiB device array that
+ * the library reserves on every GPU that loads it, for the life of the process.
+ *   n, nnz, row_ptr, col_idx  the graph as for cpaa_graph_create, in DEVICE
+ *                             memory; 1 <= n <= CPAA_NOALLOC_MAX_N
+ *   p                         FP64[n] in device memory, p >= 0, sum 1 (not checked)
+ *   c                         damping factor in (0, 1)
+ *   rounds                    Algorithm 1's M (0..2000); cpaa_rounds_needed
+ *                             gives the M for a tolerance
+ *   normalize                 as in cpaa_options
+ *   pi                        FP64[n] output in device memory
+ *   stream                    cudaStream_t, NULL = legacy default stream
+ * Arithmetic is FP64 and matches cpaa_solve with fixed_rounds = rounds to
+ * rounding.  The call returns after the stream has finished its work (it reads
+ * back an error counter): CPAA_EINVAL if n is beyond CPAA_NOALLOC_MAX_N or an
+ * argument is out of range, and also if the CSR had a column outside [0, n) or
+ * a row of degree <= 0 (such entries are skipped, never read out of bounds).
+ * The first call on a device looks up the scratch array's address (make it
+ * before any stream capture).  All calls share that array and it keeps the
+ * previous call's contents; calls that overlap on the GPU race, so serialise
+ * them. */
+cpaa_status cpaa_solve_fixed_noalloc(int64_t n, int64_t nnz, const int32_t *row_ptr,
+                                     const int32_t *col_idx, const double *p, double c,
+                                     int rounds, int normalize, double *pi, void *stream);
+
 /* The stopping rule on its own: the smallest M in [1, max_rounds] with
  * bound(M) < tol, or -1.  normalize as in cpaa_options; bound as in
  * cpaa_info.bound (Eq. 41 times kappa, plus the normalisation term). */

@@ -18,7 +18,8 @@ __all__ = [
     "CPAA_DEVICE_IO", "CPAA_TIME_ROUNDS",
     "cpaa_options_init", "cpaa_graph_create", "cpaa_graph_destroy", "cpaa_graph_info",
     "cpaa_solve", "cpaa_solve_batch", "cpaa_rounds_needed", "cpaa_l1_bound",
-    "cpaa_status_string", "cpaa_last_error", "Graph", "EXPORTED_SYMBOLS",
+    "cpaa_status_string", "cpaa_last_error", "cpaa_solve_fixed_noalloc", "Graph",
+    "EXPORTED_SYMBOLS", "CPAA_NOALLOC_MAX_N",
 ]
 
 CPAA_OK, CPAA_EINVAL, CPAA_ENOMEM, CPAA_ENOTCONV, CPAA_ECUDA = 0, 1, 2, 3, 4
@@ -26,6 +27,7 @@ CPAA_ETIMEOUT, CPAA_EBUSY, CPAA_ECANCELLED, CPAA_ENOTFOUND = 5, 6, 7, 8
 CPAA_F64, CPAA_F32, CPAA_BF16 = 0, 1, 2
 CPAA_GRAPH_DEVICE_INPUT, CPAA_GRAPH_VALIDATE = 1, 2
 CPAA_DEVICE_IO = 1
+CPAA_NOALLOC_MAX_N = 1300000
 CPAA_TIME_ROUNDS = 2
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -35,7 +37,7 @@ library_path = os.path.join(HERE, "_build", "libcpaa.so")
 EXPORTED_SYMBOLS = [
     "cpaa_options_init", "cpaa_graph_create", "cpaa_graph_destroy", "cpaa_graph_info",
     "cpaa_solve", "cpaa_solve_batch", "cpaa_rounds_needed", "cpaa_l1_bound",
-    "cpaa_status_string", "cpaa_last_error",
+    "cpaa_status_string", "cpaa_last_error", "cpaa_solve_fixed_noalloc",
 ]
 
 
@@ -90,6 +92,8 @@ def lib():
     L.cpaa_rounds_needed.argtypes = [dbl, dbl, dbl, cint, cint]
     L.cpaa_l1_bound.restype = dbl
     L.cpaa_l1_bound.argtypes = [dbl, cint, dbl, cint]
+    L.cpaa_solve_fixed_noalloc.restype = cint
+    L.cpaa_solve_fixed_noalloc.argtypes = [i64, i64, vp, vp, vp, dbl, cint, cint, vp, vp]
     L.cpaa_status_string.restype = ctypes.c_char_p
     L.cpaa_status_string.argtypes = [cint]
     L.cpaa_last_error.restype = ctypes.c_char_p
@@ -208,6 +212,16 @@ def cpaa_solve_batch(g, B, P, c, tol, PI, precision=CPAA_F32, normalize=0, fixed
                                 ctypes.byref(o), infos)
     _check(st, raise_notconv)
     return list(infos)
+
+
+def cpaa_solve_fixed_noalloc(n, nnz, row_ptr, col_idx, p, c, rounds, pi, normalize=0,
+                             stream=None):
+    """Fixed-round FP64 solve that allocates nothing (all arguments in device
+    memory; intermediates in the library's fixed per-device scratch array)."""
+    st = lib().cpaa_solve_fixed_noalloc(int(n), int(nnz), _addr(row_ptr), _addr(col_idx), _addr(p),
+                                        float(c), int(rounds), int(normalize), _addr(pi),
+                                        _stream_of(p, stream))
+    return _check(st)
 
 
 def cpaa_rounds_needed(c, tol, kappa, normalize=0, max_rounds=2000):
