@@ -126,7 +126,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "200"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -222,6 +222,145 @@ def oracle_sample(rp, cx, rounds, threads):
 
 # -- main arms ----------------------------------------------------------------------
 
+def run_batch(pkg, args, stream):
+    """256 personalised vectors (1-16 uniform seeds each) on the 4M-vertex
+    Chung-Lu graph, c = 0.85, tol 1e-6: cpaa_solve_batch in FP32 against the
+    plain FP64 single-vector solve, per query (time to the same L1 bound)."""
+    import torch
+    import cpaa_inputs as ci
+    g = ci.chung_lu(1 << 22, 64_000_000, seed=0, device="cuda")
+    n, nnz = g.n, g.nnz
+    G = pkg.Graph(g.row_ptr, g.col_idx, n=n)
+    del g
+    B = 256
+    seeds = ci.seed_vectors(n, B, max_seeds=16, seed=0)
+    P = torch.zeros((B, n), dtype=torch.float64, device="cuda")
+    for b, (s, w) in enumerate(seeds):
+        P[b, torch.as_tensor(s.astype(np.int64), device="cuda")] = torch.as_tensor(w, device="cuda")
+    PI = torch.empty_like(P)
+    cs = np.full(B, 0.85)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = G.solve_batch(B, P, cs, 1e-6, PI, precision=pkg.CPAA_F32)  # warm-up
+    torch.cuda.synchronize()
+    e0.record(stream)
+    infos = G.solve_batch(B, P, cs, 1e-6, PI, precision=pkg.CPAA_F32)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1)
+    # plain FP64 single-vector form on a sample of the same queries
+    sample = list(range(0, B, 16))
+    pi = torch.empty((n,), dtype=torch.float64, device="cuda")
+    G.solve(P[0], 0.85, 1e-6, pi, precision=pkg.CPAA_F64)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for b in sample:
+        G.solve(P[b], 0.85, 1e-6, pi, precision=pkg.CPAA_F64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_single = e0.elapsed_time(e1) / len(sample)
+    l1 = float((PI[sample[-1]] - pi).abs().sum().item())
+    G.close()
+    rounds = [i.rounds for i in infos]
+    return {"workload": "Chung-Lu n=2^22, 6.4e7 pair draws, gamma=2.1, seed 0, + ring; 256 vectors "
+                        "uniform over 1-16 seeds; c=0.85; tol 1e-6 L1",
+            "n": n, "nnz": nnz, "B": B, "precision": "f32",
+            "ms_batch": t_batch, "ms_per_query_batched_f32": t_batch / B,
+            "ms_per_query_single_f64": t_single,
+            "speedup_batched_f32_vs_single_f64": t_single / (t_batch / B),
+            "effective_gteps": nnz * sum(rounds) / (t_batch * 1e-3) / 1e9,
+            "rounds_min_max": [min(rounds), max(rounds)],
+            "l1_batched_f32_vs_single_f64_last_sample": l1}
+
+
+def run_serving(pkg, args):
+    """Continuous-batching server over 8 resident Chung-Lu graphs (10k..8M
+    vertices, mean degree 16).  Queries: a uniform graph, 1-16 distinct uniform
+    seeds, c uniform over {0.5, 0.85, 0.95}, tol 1e-6.  First a closed loop with
+    512 queries outstanding gives the saturated rate; then an open-loop Poisson
+    stream at 0.7 x that rate; latency = submit -> result ready (server side)."""
+    import threading
+    import torch
+    import cpaa_inputs as ci
+    sizes = [10_000, 50_000, 200_000, 500_000, 1_000_000, 2_000_000, 4_000_000, 8_000_000]
+    G = []
+    for i, n in enumerate(sizes):
+        g = ci.chung_lu(n, 8 * n, seed=100 + i, device="cuda")
+        G.append(pkg.Graph(g.row_ptr, g.col_idx, n=g.n))
+        del g
+    torch.cuda.empty_cache()
+    nnz_total = sum(x.nnz for x in G)
+    rng = np.random.default_rng(0)
+
+    def make(count):
+        out = []
+        for _ in range(count):
+            gi = int(rng.integers(len(sizes)))
+            k = int(rng.integers(1, 17))
+            seeds = rng.choice(sizes[gi], size=k, replace=False).astype(np.int32)
+            out.append((gi, seeds, float(rng.choice([0.5, 0.85, 0.95]))))
+        return out
+
+    def run(queries, rate):
+        S = pkg.Server(64 << 30)
+        ids = [S.add_graph(x, 16) for x in G]
+        tickets = []
+        lock = threading.Condition()
+        done = {"n": 0, "t_last": 0.0}
+
+        def consumer():
+            i = 0
+            while i < len(queries):
+                with lock:
+                    while i >= len(tickets):
+                        lock.wait()
+                    t = tickets[i]
+                S.wait(t, None)
+                i += 1
+                done["n"] = i
+                done["t_last"] = time.perf_counter()
+
+        th = threading.Thread(target=consumer)
+        th.start()
+        t0 = time.perf_counter()
+        if rate is None:  # closed loop: at most 512 outstanding
+            for q in queries:
+                while len(tickets) - done["n"] >= 512:
+                    time.sleep(50e-6)
+                t = S.submit(ids[q[0]], q[1], None, q[2], 1e-6)
+                with lock:
+                    tickets.append(t)
+                    lock.notify()
+        else:
+            arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(queries)))
+            for q, ta in zip(queries, arrivals):
+                dt = t0 + ta - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                t = S.submit(ids[q[0]], q[1], None, q[2], 1e-6)
+                with lock:
+                    tickets.append(t)
+                    lock.notify()
+        th.join()
+        st = S.stats()
+        S.close()
+        return len(queries) / (done["t_last"] - t0), st
+
+    sat_qps, sat_st = run(make(args.serve_queries // 4), None)
+    rate = 0.7 * sat_qps
+    qps, st = run(make(args.serve_queries), rate)
+    for x in G:
+        x.close()
+    return {"workload": "8 Chung-Lu graphs (n = 10k..8M, mean degree 16, gamma 2.1) resident; "
+                        "queries: uniform graph, 1-16 seeds, c in {0.5, 0.85, 0.95}, tol 1e-6; "
+                        "FP32, 16 slots per graph",
+            "nnz_total": nnz_total, "queries": args.serve_queries,
+            "saturated_qps": sat_qps, "poisson_rate_qps": rate, "achieved_qps": qps,
+            "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3, "mean_ms": st["mean_us"] / 1e3,
+            "admit_p50_ms": st["admit_p50_us"] / 1e3, "saturated_p50_ms": sat_st["p50_us"] / 1e3,
+            "saturated_p99_ms": sat_st["p99_us"] / 1e3, "completed": st["completed"],
+            "failed": st["failed"]}
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
@@ -296,10 +435,16 @@ def run_ours(args):
     barrier(world)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     e0.record(stream)
-    infos = [solve(prec) for _ in range(args.steps)]
+    infos = []
+    for i in range(args.steps):
+        marks[i].record(stream)
+        infos.append(solve(prec))
+    marks[-1].record(stream)
     e1.record(stream)
     torch.cuda.synchronize()
+    step_ms = [marks[i].elapsed_time(marks[i + 1]) for i in range(args.steps)]
     barrier(world)
     clk = clocks.stop()
     local_ms = e0.elapsed_time(e1)
@@ -351,6 +496,23 @@ def run_ours(args):
     e2e = {"value": e2e_units / e2e_s / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": 8 * n,
            "d2h_bytes_per_step": 8 * n}
 
+    # ---- batched personalised queries (the 4M-vertex, 256-vector configuration)
+    batch = None
+    if not args.skip_batch:
+        del G
+        torch.cuda.empty_cache()
+        batch = run_batch(pkg, args, stream)
+        G = None
+
+    # ---- serving: continuous batching over 8 resident graphs
+    serving = None
+    if not args.skip_serve:
+        if G is not None:
+            del G
+            G = None
+        torch.cuda.empty_cache()
+        serving = run_serving(pkg, args)
+
     # ---- CPU oracle baseline on a bounded sample
     cpu = None
     if cpu_graph is not None:
@@ -362,7 +524,8 @@ def run_ours(args):
                "sample": "%d round(s) of the FP64 oracle recurrence on the full graph (%.1f s)"
                          % (args.ref_rounds, dt)}
 
-    G.close()
+    if G is not None:
+        G.close()
     if rank != 0:
         return 0
     line = {
@@ -373,7 +536,8 @@ def run_ours(args):
         "config": {"workload": wl["desc"], "n": n, "nnz": nnz, "rounds": rounds,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (col_idx %.2f GB), no flush" % (4 * nnz / 1e9),
-                   "graph_gen_s": round(gen_s, 2), "graph_create_s": round(create_s, 2)},
+                   "graph_gen_s": round(gen_s, 2), "graph_create_s": round(create_s, 2),
+                   "step_ms": [round(x, 3) for x in step_ms]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": profiled_traffic(prec, args.workload),
                      "kernel": "cheb_step_kernel<%s>" % prec, "alg_bytes_per_launch": ab,
@@ -381,8 +545,10 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk,
-        "gpu_launches": sum(i.rounds + 5 for i in infos),
+        "gpu_launches": sum(i.rounds + 6 for i in infos),
         "f64": f64,
+        "batch": batch,
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -399,6 +565,9 @@ def main(argv=None):
     ap.add_argument("--ref-rounds", type=int, default=2,
                     help="oracle rounds per CPU sample (bounded CPU work)")
     ap.add_argument("--skip-f64", action="store_true")
+    ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--skip-serve", action="store_true")
+    ap.add_argument("--serve-queries", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)
     if args.impl == "reference":

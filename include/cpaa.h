@@ -86,7 +86,9 @@ typedef struct {
     unsigned flags;           /* CPAA_DEVICE_IO | CPAA_TIME_ROUNDS */
     void *stream;             /* cudaStream_t to run on; NULL = legacy default stream */
     double *history;          /* optional host array [2*(M+1)]: sum T_k and sum |T_k|
-                                 for k = 0..M (the mass view of Sec. 4.1) */
+                                 for k = 0..M (the mass view of Sec. 4.1); cpaa_solve only */
+    int batch_width;          /* cpaa_solve_batch: vectors per tile, 1/2/4/8/16, or 0 to pick
+                                 the widest whose gathered array fits in L2 (default 0) */
 } cpaa_options;
 
 typedef struct {
@@ -150,6 +152,77 @@ cpaa_status cpaa_solve(cpaa_graph *g, const double *p, double c, double tol, dou
 cpaa_status cpaa_solve_batch(cpaa_graph *g, int B, const double *P, const double *c,
                              double tol, double *PI, const cpaa_options *opt,
                              cpaa_info *info);
+
+/* ------------------------------------------------------------------------
+ * Serving: a continuous-batching request loop over resident graphs.
+ *
+ * Queries are personalised PageRank vectors with a few seed vertices, each
+ * with its own damping c and tolerance (Sec. 2.1: p uniform over the seeds,
+ * or weighted).  Every added graph gets a fixed number of column slots whose
+ * device memory is reserved from the server's budget when the graph is added;
+ * a query waits in its graph's queue until a slot is free, then joins the
+ * graph's running tile before the next round, while the other columns of the
+ * tile keep going (each column has its own round counter, coefficients and
+ * stopping round).  Each graph runs on its own CUDA stream, so the work of
+ * different graphs overlaps on the device.  A query's result does not depend
+ * on what else is running: every column's arithmetic is the same, in the same
+ * order, whatever the other columns hold.
+ * ------------------------------------------------------------------------ */
+typedef struct cpaa_server cpaa_server;
+
+/* Most seed vertices one query may name. */
+#define CPAA_SERVER_MAX_SEEDS 64
+
+typedef struct {
+    uint64_t submitted, completed, cancelled, failed;
+    int64_t pending;      /* queued, not yet in a slot */
+    int64_t running;      /* in a slot */
+    int64_t slots;        /* total slots over all graphs */
+    int64_t device_bytes; /* reserved from the budget */
+    double p50_us, p99_us, mean_us; /* submit -> result ready, completed queries */
+    double admit_p50_us;  /* submit -> slot */
+} cpaa_server_stats;
+
+/* Create a server.  device_mem_budget bounds the device memory of all slots;
+ * opt (NULL for defaults) sets the precision (default for serving: CPAA_F32),
+ * normalize and max_rounds; its stream and flags are ignored.  Starts two host
+ * threads (scheduler, completion). */
+cpaa_status cpaa_server_create(size_t device_mem_budget, const cpaa_options *opt,
+                               cpaa_server **out);
+
+/* Make a graph resident in the server with up to max_slots (1..16, rounded
+ * down to a power of two; 0 = 16) concurrent queries, as many as the remaining
+ * budget allows.  CPAA_ENOMEM if not even one slot fits.  The graph must
+ * outlive the server and must not be used by other calls while the server
+ * runs.  *graph_id receives the id for cpaa_server_submit. */
+cpaa_status cpaa_server_add_graph(cpaa_server *s, cpaa_graph *g, int max_slots, int *graph_id);
+
+/* Queue a query: seeds[nseeds] (distinct vertex ids, 1 <= nseeds <=
+ * CPAA_SERVER_MAX_SEEDS), weights[nseeds] (>= 0, summing to 1; NULL for
+ * uniform 1/nseeds), damping c in (0,1), L1 tolerance tol > 0.  Returns at
+ * once with a ticket.  CPAA_EBUSY if the graph's queue is full. */
+cpaa_status cpaa_server_submit(cpaa_server *s, int graph_id, int nseeds, const int32_t *seeds,
+                               const double *weights, double c, double tol, uint64_t *ticket);
+
+/* Wait up to timeout_us (< 0: forever) for a query.  A finished query's vector
+ * waits in its slot's device memory (holding the slot) until this call copies
+ * it to pi -- n doubles in the caller's vertex order, host or device memory,
+ * or NULL to discard it -- fills info (may be NULL; mass, l1 and sum_pibar are
+ * NaN: they are not reduced when serving), frees the slot and releases the
+ * ticket.  CPAA_ETIMEOUT leaves the query in place; CPAA_ECANCELLED releases a
+ * cancelled query; CPAA_ENOTFOUND names no query. */
+cpaa_status cpaa_server_wait(cpaa_server *s, uint64_t ticket, double *pi, cpaa_info *info,
+                             int64_t timeout_us);
+
+/* Cancel a query: a queued or running one leaves its slot at the next round, a
+ * finished one's uncollected vector is discarded. */
+cpaa_status cpaa_server_cancel(cpaa_server *s, uint64_t ticket);
+
+/* Counters and latency percentiles so far. */
+cpaa_status cpaa_server_get_stats(cpaa_server *s, cpaa_server_stats *out);
+
+/* Stop the threads (running queries are cancelled) and free the slots. */
+cpaa_status cpaa_server_destroy(cpaa_server *s);
 
 /* Largest n that cpaa_solve_fixed_noalloc accepts.  That call keeps two FP64
  * iterate vectors and an FP64 accumulator (24 bytes per vertex) plus a small

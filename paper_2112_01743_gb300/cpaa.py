@@ -19,7 +19,9 @@ __all__ = [
     "cpaa_options_init", "cpaa_graph_create", "cpaa_graph_destroy", "cpaa_graph_info",
     "cpaa_solve", "cpaa_solve_batch", "cpaa_rounds_needed", "cpaa_l1_bound",
     "cpaa_status_string", "cpaa_last_error", "cpaa_solve_fixed_noalloc", "Graph",
-    "EXPORTED_SYMBOLS", "CPAA_NOALLOC_MAX_N",
+    "EXPORTED_SYMBOLS", "CPAA_NOALLOC_MAX_N", "CPAA_SERVER_MAX_SEEDS", "CpaaServerStats",
+    "cpaa_server_create", "cpaa_server_add_graph", "cpaa_server_submit", "cpaa_server_wait",
+    "cpaa_server_cancel", "cpaa_server_get_stats", "cpaa_server_destroy", "Server",
 ]
 
 CPAA_OK, CPAA_EINVAL, CPAA_ENOMEM, CPAA_ENOTCONV, CPAA_ECUDA = 0, 1, 2, 3, 4
@@ -28,6 +30,7 @@ CPAA_F64, CPAA_F32, CPAA_BF16 = 0, 1, 2
 CPAA_GRAPH_DEVICE_INPUT, CPAA_GRAPH_VALIDATE = 1, 2
 CPAA_DEVICE_IO = 1
 CPAA_NOALLOC_MAX_N = 1300000
+CPAA_SERVER_MAX_SEEDS = 64
 CPAA_TIME_ROUNDS = 2
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -38,6 +41,8 @@ EXPORTED_SYMBOLS = [
     "cpaa_options_init", "cpaa_graph_create", "cpaa_graph_destroy", "cpaa_graph_info",
     "cpaa_solve", "cpaa_solve_batch", "cpaa_rounds_needed", "cpaa_l1_bound",
     "cpaa_status_string", "cpaa_last_error", "cpaa_solve_fixed_noalloc",
+    "cpaa_server_create", "cpaa_server_add_graph", "cpaa_server_submit", "cpaa_server_wait",
+    "cpaa_server_cancel", "cpaa_server_get_stats", "cpaa_server_destroy",
 ]
 
 
@@ -51,13 +56,25 @@ class CpaaOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("normalize", ctypes.c_int),
                 ("fixed_rounds", ctypes.c_int), ("max_rounds", ctypes.c_int),
                 ("flags", ctypes.c_uint), ("stream", ctypes.c_void_p),
-                ("history", ctypes.POINTER(ctypes.c_double))]
+                ("history", ctypes.POINTER(ctypes.c_double)), ("batch_width", ctypes.c_int)]
 
 
 class CpaaInfo(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_int), ("bound", ctypes.c_double), ("kappa", ctypes.c_double),
                 ("mass", ctypes.c_double), ("l1", ctypes.c_double), ("sum_pibar", ctypes.c_double),
                 ("rounds_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class CpaaServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("cancelled", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("pending", ctypes.c_int64), ("running", ctypes.c_int64), ("slots", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("p50_us", ctypes.c_double),
+                ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double),
+                ("admit_p50_us", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -94,6 +111,20 @@ def lib():
     L.cpaa_l1_bound.argtypes = [dbl, cint, dbl, cint]
     L.cpaa_solve_fixed_noalloc.restype = cint
     L.cpaa_solve_fixed_noalloc.argtypes = [i64, i64, vp, vp, vp, dbl, cint, cint, vp, vp]
+    L.cpaa_server_create.restype = cint
+    L.cpaa_server_create.argtypes = [ctypes.c_size_t, ctypes.POINTER(CpaaOptions), ctypes.POINTER(vp)]
+    L.cpaa_server_add_graph.restype = cint
+    L.cpaa_server_add_graph.argtypes = [vp, vp, cint, ctypes.POINTER(cint)]
+    L.cpaa_server_submit.restype = cint
+    L.cpaa_server_submit.argtypes = [vp, cint, cint, vp, vp, dbl, dbl, ctypes.POINTER(ctypes.c_uint64)]
+    L.cpaa_server_wait.restype = cint
+    L.cpaa_server_wait.argtypes = [vp, ctypes.c_uint64, vp, ctypes.POINTER(CpaaInfo), i64]
+    L.cpaa_server_cancel.restype = cint
+    L.cpaa_server_cancel.argtypes = [vp, ctypes.c_uint64]
+    L.cpaa_server_get_stats.restype = cint
+    L.cpaa_server_get_stats.argtypes = [vp, ctypes.POINTER(CpaaServerStats)]
+    L.cpaa_server_destroy.restype = cint
+    L.cpaa_server_destroy.argtypes = [vp]
     L.cpaa_status_string.restype = ctypes.c_char_p
     L.cpaa_status_string.argtypes = [cint]
     L.cpaa_last_error.restype = ctypes.c_char_p
@@ -201,12 +232,13 @@ def cpaa_solve(g, p, c, tol, pi, precision=CPAA_F64, normalize=0, fixed_rounds=0
 
 
 def cpaa_solve_batch(g, B, P, c, tol, PI, precision=CPAA_F32, normalize=0, fixed_rounds=0,
-                     max_rounds=0, stream=None, raise_notconv=True):
+                     max_rounds=0, stream=None, raise_notconv=True, batch_width=0):
     """Column b of P (n x B column-major, i.e. B vectors back to back) with
     damping c[b] -> column b of PI.  Returns a list of B info records."""
     dev = _is_device(P)
     cvec = np.ascontiguousarray(np.broadcast_to(np.asarray(c, dtype=np.float64), (int(B),)))
     o = _options(precision, normalize, fixed_rounds, max_rounds, dev, _stream_of(P, stream), None)
+    o.batch_width = int(batch_width)
     infos = (CpaaInfo * int(B))()
     st = lib().cpaa_solve_batch(g, int(B), _addr(P), cvec.ctypes.data, float(tol), _addr(PI),
                                 ctypes.byref(o), infos)
@@ -222,6 +254,90 @@ def cpaa_solve_fixed_noalloc(n, nnz, row_ptr, col_idx, p, c, rounds, pi, normali
                                         float(c), int(rounds), int(normalize), _addr(pi),
                                         _stream_of(p, stream))
     return _check(st)
+
+
+def cpaa_server_create(budget_bytes, precision=CPAA_F32, normalize=0, max_rounds=0):
+    o = cpaa_options_init()
+    o.precision = int(precision)
+    o.normalize = int(normalize)
+    if max_rounds:
+        o.max_rounds = int(max_rounds)
+    h = ctypes.c_void_p()
+    _check(lib().cpaa_server_create(int(budget_bytes), ctypes.byref(o), ctypes.byref(h)))
+    return h.value
+
+
+def cpaa_server_add_graph(s, g, max_slots=0):
+    gid = ctypes.c_int()
+    _check(lib().cpaa_server_add_graph(s, g, int(max_slots), ctypes.byref(gid)))
+    return gid.value
+
+
+def cpaa_server_submit(s, graph_id, seeds, weights, c, tol):
+    sd = np.ascontiguousarray(seeds, dtype=np.int32)
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    t = ctypes.c_uint64()
+    _check(lib().cpaa_server_submit(s, int(graph_id), int(sd.size), sd.ctypes.data,
+                                    None if w is None else w.ctypes.data, float(c), float(tol),
+                                    ctypes.byref(t)))
+    return t.value
+
+
+def cpaa_server_wait(s, ticket, pi=None, timeout_us=-1, raise_errors=True):
+    """Wait for a query; returns (status, info).  pi: host float64 array or None."""
+    info = CpaaInfo()
+    st = lib().cpaa_server_wait(s, ctypes.c_uint64(ticket), _addr(pi), ctypes.byref(info),
+                                int(timeout_us))
+    if raise_errors and st not in (CPAA_OK, CPAA_ETIMEOUT, CPAA_ECANCELLED):
+        _check(st)
+    return st, info
+
+
+def cpaa_server_cancel(s, ticket):
+    return lib().cpaa_server_cancel(s, ctypes.c_uint64(ticket))
+
+
+def cpaa_server_get_stats(s):
+    o = CpaaServerStats()
+    _check(lib().cpaa_server_get_stats(s, ctypes.byref(o)))
+    return o.as_dict()
+
+
+def cpaa_server_destroy(s):
+    return _check(lib().cpaa_server_destroy(s))
+
+
+class Server:
+    """Owning wrapper of a cpaa_server handle."""
+
+    def __init__(self, budget_bytes, precision=CPAA_F32, normalize=0, max_rounds=0):
+        self.handle = cpaa_server_create(budget_bytes, precision, normalize, max_rounds)
+
+    def add_graph(self, graph, max_slots=0):
+        return cpaa_server_add_graph(self.handle, graph.handle, max_slots)
+
+    def submit(self, graph_id, seeds, weights, c, tol):
+        return cpaa_server_submit(self.handle, graph_id, seeds, weights, c, tol)
+
+    def wait(self, ticket, pi=None, timeout_us=-1):
+        return cpaa_server_wait(self.handle, ticket, pi, timeout_us)
+
+    def cancel(self, ticket):
+        return cpaa_server_cancel(self.handle, ticket)
+
+    def stats(self):
+        return cpaa_server_get_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            cpaa_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def cpaa_rounds_needed(c, tol, kappa, normalize=0, max_rounds=2000):

@@ -1,28 +1,18 @@
-// graph.cu -- graph upload, degree vectors, row tiling and validation.
+// graph.cu -- graph upload, validation, relabelling and the SELL-C-sigma /
+// hub layout the round kernel walks (see internal.h).
 //
 // The graph is the undirected G of Sec. 2.1 held as symmetric CSR.  Its
-// degrees d_u = row_ptr[u+1] - row_ptr[u] give P = A D^-1; the step kernels
+// degrees d_u = row_ptr[u+1] - row_ptr[u] give P = A D^-1; the round kernels
 // work in the scaled space y = D^-1 T (see step.cu), so the graph also keeps
-// d and 1/d in FP64 and FP32.
+// d and 1/d in FP64 and FP32, in the new vertex order.
 #include <algorithm>
 #include <cstring>
+#include <numeric>
+#include <thread>
 
 #include "internal.h"
 
 namespace cpaa {
-
-__global__ void degree_kernel(const int32_t *__restrict__ row_ptr, int64_t n, double *deg64,
-                              double *inv64, float *deg32, float *inv32) {
-    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n;
-         u += (int64_t)gridDim.x * blockDim.x) {
-        const int d = row_ptr[u + 1] - row_ptr[u];
-        const double dd = (double)d;
-        deg64[u] = dd;
-        inv64[u] = 1.0 / dd;
-        deg32[u] = (float)d;
-        inv32[u] = 1.0f / (float)d;
-    }
-}
 
 // Row of entry e (row_ptr[row] <= e < row_ptr[row+1]); rows are non-empty.
 __device__ __forceinline__ int64_t row_of(const int32_t *row_ptr, int64_t n, int64_t e) {
@@ -59,46 +49,135 @@ __global__ void validate_kernel(const int32_t *__restrict__ row_ptr,
     }
 }
 
+// Per-vertex arrays in the new order, and the inverse permutation.
+__global__ void vertex_arrays_kernel(const int32_t *__restrict__ row_ptr,
+                                     const int32_t *__restrict__ perm, int64_t n, double *deg64,
+                                     double *inv64, float *deg32, float *inv32, int32_t *inv_perm) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t u = perm[r];
+        const int d = row_ptr[u + 1] - row_ptr[u];
+        deg64[r] = (double)d;
+        inv64[r] = 1.0 / (double)d;
+        deg32[r] = (float)d;
+        inv32[r] = 1.0f / (float)d;
+        inv_perm[u] = (int32_t)r;
+    }
+}
+
+// One warp per SELL chunk: lane l writes entry i of row n_hub + 32c + l at
+// chunk_off[c] + 32 i + l, relabelled; padding gets the sentinel n.
+__global__ void build_sell_kernel(const int32_t *__restrict__ row_ptr,
+                                  const int32_t *__restrict__ col_idx,
+                                  const int32_t *__restrict__ perm,
+                                  const int32_t *__restrict__ inv_perm, int64_t n, int n_hub,
+                                  int num_chunks, const int64_t *__restrict__ chunk_off,
+                                  const int32_t *__restrict__ chunk_len, int32_t *sell) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < num_chunks;
+         c += nwarps) {
+        const int64_t r = n_hub + c * kChunkRows + lane;
+        int e0 = 0, d = 0;
+        if (r < n) {
+            const int32_t u = perm[r];
+            e0 = row_ptr[u];
+            d = row_ptr[u + 1] - e0;
+        }
+        const int64_t off = chunk_off[c];
+        const int len = chunk_len[c];
+        for (int i = 0; i < len; ++i)
+            sell[off + (int64_t)i * kChunkRows + lane] = (i < d) ? inv_perm[col_idx[e0 + i]] : (int32_t)n;
+    }
+}
+
+// One CTA per hub row: relabelled copy of its entries.
+__global__ void build_hub_kernel(const int32_t *__restrict__ row_ptr,
+                                 const int32_t *__restrict__ col_idx,
+                                 const int32_t *__restrict__ perm,
+                                 const int32_t *__restrict__ inv_perm,
+                                 const int32_t *__restrict__ hub_row_ptr, int n_hub,
+                                 int32_t *hub_col) {
+    for (int h = blockIdx.x; h < n_hub; h += gridDim.x) {
+        const int32_t u = perm[h];
+        const int e0 = row_ptr[u], d = row_ptr[u + 1] - e0;
+        const int o = hub_row_ptr[h];
+        for (int i = threadIdx.x; i < d; i += blockDim.x) hub_col[o + i] = inv_perm[col_idx[e0 + i]];
+    }
+}
+
 static void release(cpaa_graph *g) {
     if (!g) return;
     Workspace &w = g->ws;
     cudaFree(w.y0); cudaFree(w.y1); cudaFree(w.rho); cudaFree(w.comp); cudaFree(w.red);
-    cudaFree(w.prep_part); cudaFree(w.prep_out); cudaFree(w.d_pi); cudaFree(w.d_p);
-    if (w.h_prep) cudaFreeHost(w.h_prep);
-    cudaFree(g->row_ptr); cudaFree(g->col_idx); cudaFree(g->deg64); cudaFree(g->inv_deg64);
-    cudaFree(g->deg32); cudaFree(g->inv_deg32); cudaFree(g->tiles); cudaFree(g->long_part);
-    cudaFree(g->long_cnt);
+    cudaFree(w.long_part); cudaFree(w.part); cudaFree(w.sums); cudaFree(w.io);
+    if (w.h_sums) cudaFreeHost(w.h_sums);
+    cudaFree(g->perm); cudaFree(g->hub_row_ptr); cudaFree(g->hub_col); cudaFree(g->hub_tiles);
+    cudaFree(g->long_cnt); cudaFree(g->sell_col); cudaFree(g->chunk_off);
+    cudaFree(g->chunk_len); cudaFree(g->chunk_order); cudaFree(g->deg64); cudaFree(g->inv_deg64);
+    cudaFree(g->deg32); cudaFree(g->inv_deg32);
     delete g;
 }
 
-// Greedy tiling over the host copy of row_ptr (see internal.h for the
-// encoding).  One pass, O(n).
-static void build_tiles(const int32_t *rp, int64_t n, std::vector<int4> &chunks,
-                        std::vector<int4> &blocks, int &num_long, int &total_chunks) {
-    num_long = 0;
-    total_chunks = 0;
-    int64_t r = 0;
-    while (r < n) {
-        const int64_t d = (int64_t)rp[r + 1] - rp[r];
-        if (d + 1 > kTileItems) {
-            const int nch = (int)((d + kTileItems - 1) / kTileItems);
-            for (int j = 0; j < nch; ++j)
-                chunks.push_back(make_int4((int)r, j, total_chunks, num_long + 1));
-            total_chunks += nch;
-            ++num_long;
-            ++r;
-            continue;
-        }
-        const int64_t r0 = r;
-        int64_t items = 0;
-        while (r < n) {
-            const int64_t dr = (int64_t)rp[r + 1] - rp[r];
-            if (dr + 1 > kTileItems || items + dr + 1 > kTileItems) break;
-            items += dr + 1;
-            ++r;
-        }
-        blocks.push_back(make_int4((int)r0, (int)r, 0, 0));
+// Host side of the relabelling: hub rows by decreasing degree, then windows
+// of kSortWindow rows sorted by decreasing degree (stable).
+struct HostLayout {
+    std::vector<int32_t> perm;
+    int n_hub = 0;
+    std::vector<int32_t> hub_row_ptr;
+    std::vector<int64_t> chunk_off;
+    std::vector<int32_t> chunk_len;
+    std::vector<int32_t> chunk_order;
+    std::vector<int4> hub_tiles;
+    int64_t sell_entries = 0;
+};
+
+static void host_layout(const int32_t *rp, int64_t n, HostLayout &L) {
+    auto deg = [&](int32_t u) { return rp[u + 1] - rp[u]; };
+    std::vector<int32_t> hubs, rest;
+    rest.reserve((size_t)n);
+    for (int64_t u = 0; u < n; ++u) (deg((int32_t)u) > kHubDegree ? hubs : rest).push_back((int32_t)u);
+    std::stable_sort(hubs.begin(), hubs.end(), [&](int32_t a, int32_t b) { return deg(a) > deg(b); });
+    const int64_t nrest = (int64_t)rest.size();
+    const int64_t nwin = (nrest + kSortWindow - 1) / kSortWindow;
+    const int nth = (int)std::max<int64_t>(1, std::min<int64_t>(16, nwin / 64));
+    std::vector<std::thread> th;
+    for (int t = 0; t < nth; ++t)
+        th.emplace_back([&, t]() {
+            for (int64_t w = t; w < nwin; w += nth) {
+                auto b = rest.begin() + w * kSortWindow;
+                auto e = rest.begin() + std::min<int64_t>(nrest, (w + 1) * kSortWindow);
+                std::stable_sort(b, e, [&](int32_t a, int32_t c) { return deg(a) > deg(c); });
+            }
+        });
+    for (auto &x : th) x.join();
+    L.n_hub = (int)hubs.size();
+    L.perm = hubs;
+    L.perm.insert(L.perm.end(), rest.begin(), rest.end());
+    L.hub_row_ptr.assign((size_t)L.n_hub + 1, 0);
+    int slot = 0;
+    for (int h = 0; h < L.n_hub; ++h) {
+        const int d = deg(hubs[h]);
+        L.hub_row_ptr[h + 1] = L.hub_row_ptr[h] + d;
+        const int nt = (d + kHubTileEntries - 1) / kHubTileEntries;
+        for (int j = 0; j < nt; ++j) L.hub_tiles.push_back(make_int4(h, j, slot, h + 1));
+        slot += nt;
     }
+    const int64_t nch = (nrest + kChunkRows - 1) / kChunkRows;
+    L.chunk_off.resize((size_t)nch);
+    L.chunk_len.resize((size_t)nch);
+    int64_t off = 0;
+    for (int64_t c = 0; c < nch; ++c) {
+        const int len = deg(rest[(size_t)(c * kChunkRows)]);
+        L.chunk_off[c] = off;
+        L.chunk_len[c] = len;
+        off += (int64_t)len * kChunkRows;
+    }
+    L.sell_entries = off;
+    L.chunk_order.resize((size_t)nch);
+    std::iota(L.chunk_order.begin(), L.chunk_order.end(), 0);
+    std::stable_sort(L.chunk_order.begin(), L.chunk_order.end(),
+                     [&](int32_t a, int32_t b) { return L.chunk_len[a] > L.chunk_len[b]; });
 }
 
 }  // namespace cpaa
@@ -111,12 +190,12 @@ extern "C" cpaa_status cpaa_graph_create(int64_t n, int64_t nnz, const int32_t *
     clear_error();
     if (!out) return fail(CPAA_EINVAL, "out is NULL");
     *out = nullptr;
-    if (n < 1 || n >= (int64_t(1) << 31)) return fail(CPAA_EINVAL, "n out of range [1, 2^31)");
+    if (n < 1 || n >= (int64_t(1) << 31) - 1) return fail(CPAA_EINVAL, "n out of range [1, 2^31 - 1)");
     if (nnz < 1 || nnz >= (int64_t(1) << 31)) return fail(CPAA_EINVAL, "nnz out of range [1, 2^31)");
     if (!row_ptr || !col_idx) return fail(CPAA_EINVAL, "row_ptr / col_idx is NULL");
     const bool dev_in = (flags & CPAA_GRAPH_DEVICE_INPUT) != 0;
 
-    // Host copy of row_ptr: needed for the tiling in any case.
+    // Host copy of row_ptr: the layout is planned on the host.
     std::vector<int32_t> hrp((size_t)n + 1);
     if (dev_in) {
         CPAA_CUDA(cudaMemcpy(hrp.data(), row_ptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost));
@@ -136,65 +215,113 @@ extern "C" cpaa_status cpaa_graph_create(int64_t n, int64_t nnz, const int32_t *
     g->nnz = nnz;
     cudaGetDevice(&g->device);
     cpaa_status st;
+    int32_t *d_rp = nullptr, *d_ci = nullptr, *d_inv = nullptr;
+    size_t rp_bytes = sizeof(int32_t) * (n + 1), ci_bytes = sizeof(int32_t) * nnz;
 #define ALLOC(ptr, bytes)                                                      \
     do {                                                                       \
         st = dev_alloc(g, (void **)&(ptr), (bytes));                           \
-        if (st != CPAA_OK) { release(g); return st; }                          \
+        if (st != CPAA_OK) goto fail_out;                                      \
     } while (0)
 #define CK(call)                                                               \
     do {                                                                       \
         cudaError_t e_ = (call);                                               \
-        if (e_ != cudaSuccess) { st = cuda_fail(e_, #call); release(g); return st; } \
+        if (e_ != cudaSuccess) { st = cuda_fail(e_, #call); goto fail_out; }   \
     } while (0)
+    {
+        // original CSR on the device (a temporary copy)
+        const cudaMemcpyKind kind = dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        ALLOC(d_rp, rp_bytes);
+        ALLOC(d_ci, ci_bytes);
+        CK(cudaMemcpy(d_rp, row_ptr, rp_bytes, kind));
+        CK(cudaMemcpy(d_ci, col_idx, ci_bytes, kind));
 
-    ALLOC(g->row_ptr, sizeof(int32_t) * (n + 1));
-    ALLOC(g->col_idx, sizeof(int32_t) * (nnz + 4));
-    const cudaMemcpyKind kind = dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    CK(cudaMemcpy(g->row_ptr, row_ptr, sizeof(int32_t) * (n + 1), kind));
-    CK(cudaMemcpy(g->col_idx, col_idx, sizeof(int32_t) * nnz, kind));
-    CK(cudaMemset(g->col_idx + nnz, 0, sizeof(int32_t) * 4));
-
-    if (flags & CPAA_GRAPH_VALIDATE) {
-        unsigned long long *bad = nullptr;
-        ALLOC(bad, 3 * sizeof(unsigned long long));
-        CK(cudaMemset(bad, 0, 3 * sizeof(unsigned long long)));
-        validate_kernel<<<1024, 256>>>(g->row_ptr, g->col_idx, n, nnz, bad);
-        CK(cudaGetLastError());
-        unsigned long long hb[3];
-        CK(cudaMemcpy(hb, bad, sizeof(hb), cudaMemcpyDeviceToHost));
-        dev_free(g, (void **)&bad, 3 * sizeof(unsigned long long));
-        if (hb[0] || hb[1] || hb[2]) {
-            std::string m = "invalid CSR: " + std::to_string(hb[0]) + " column(s) out of range, " +
-                            std::to_string(hb[1]) + " unsorted/duplicate entr(ies), " +
-                            std::to_string(hb[2]) + " entr(ies) without a mirror (graph not undirected)";
-            release(g);
-            return fail(CPAA_EINVAL, m);
+        if (flags & CPAA_GRAPH_VALIDATE) {
+            unsigned long long *bad = nullptr;
+            ALLOC(bad, 3 * sizeof(unsigned long long));
+            CK(cudaMemset(bad, 0, 3 * sizeof(unsigned long long)));
+            validate_kernel<<<1024, 256>>>(d_rp, d_ci, n, nnz, bad);
+            CK(cudaGetLastError());
+            unsigned long long hb[3];
+            CK(cudaMemcpy(hb, bad, sizeof(hb), cudaMemcpyDeviceToHost));
+            dev_free(g, (void **)&bad, 3 * sizeof(unsigned long long));
+            if (hb[0] || hb[1] || hb[2]) {
+                st = fail(CPAA_EINVAL, "invalid CSR: " + std::to_string(hb[0]) + " column(s) out of range, " +
+                                           std::to_string(hb[1]) + " unsorted/duplicate entr(ies), " +
+                                           std::to_string(hb[2]) +
+                                           " entr(ies) without a mirror (graph not undirected)");
+                goto fail_out;
+            }
         }
+
+        HostLayout L;
+        host_layout(hrp.data(), n, L);
+        g->n_hub = L.n_hub;
+        g->hub_nnz = L.hub_row_ptr.back();
+        g->num_hub_tiles = (int)L.hub_tiles.size();
+        g->num_chunks = (int)L.chunk_off.size();
+        g->num_long_chunks = 0;
+        while (g->num_long_chunks < g->num_chunks &&
+               L.chunk_len[L.chunk_order[g->num_long_chunks]] > kLongChunk)
+            ++g->num_long_chunks;
+        g->sell_entries = L.sell_entries;
+
+        ALLOC(g->perm, sizeof(int32_t) * n);
+        ALLOC(d_inv, sizeof(int32_t) * n);
+        CK(cudaMemcpy(g->perm, L.perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+        ALLOC(g->deg64, sizeof(double) * n);
+        ALLOC(g->inv_deg64, sizeof(double) * n);
+        ALLOC(g->deg32, sizeof(float) * n);
+        ALLOC(g->inv_deg32, sizeof(float) * n);
+        vertex_arrays_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 8192), 256>>>(
+            d_rp, g->perm, n, g->deg64, g->inv_deg64, g->deg32, g->inv_deg32, d_inv);
+        CK(cudaGetLastError());
+
+        ALLOC(g->hub_row_ptr, sizeof(int32_t) * (L.n_hub + 1));
+        CK(cudaMemcpy(g->hub_row_ptr, L.hub_row_ptr.data(), sizeof(int32_t) * (L.n_hub + 1),
+                      cudaMemcpyHostToDevice));
+        ALLOC(g->hub_col, sizeof(int32_t) * (g->hub_nnz + 4));
+        CK(cudaMemset(g->hub_col, 0, sizeof(int32_t) * (g->hub_nnz + 4)));
+        if (L.n_hub > 0) {
+            build_hub_kernel<<<std::min(L.n_hub, 4096), 256>>>(d_rp, d_ci, g->perm, d_inv, g->hub_row_ptr,
+                                                                L.n_hub, g->hub_col);
+            CK(cudaGetLastError());
+        }
+        ALLOC(g->hub_tiles, sizeof(int4) * std::max<size_t>(1, L.hub_tiles.size()));
+        if (!L.hub_tiles.empty())
+            CK(cudaMemcpy(g->hub_tiles, L.hub_tiles.data(), sizeof(int4) * L.hub_tiles.size(),
+                          cudaMemcpyHostToDevice));
+        ALLOC(g->long_cnt, sizeof(int) * std::max(1, g->n_hub));
+        CK(cudaMemset(g->long_cnt, 0, sizeof(int) * std::max(1, g->n_hub)));
+
+        const int nch = std::max(1, g->num_chunks);
+        ALLOC(g->chunk_off, sizeof(int64_t) * nch);
+        ALLOC(g->chunk_len, sizeof(int32_t) * nch);
+        ALLOC(g->chunk_order, sizeof(int32_t) * nch);
+        ALLOC(g->sell_col, sizeof(int32_t) * std::max<int64_t>(4, g->sell_entries));
+        if (g->num_chunks > 0) {
+            CK(cudaMemcpy(g->chunk_off, L.chunk_off.data(), sizeof(int64_t) * g->num_chunks, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(g->chunk_len, L.chunk_len.data(), sizeof(int32_t) * g->num_chunks, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(g->chunk_order, L.chunk_order.data(), sizeof(int32_t) * g->num_chunks,
+                          cudaMemcpyHostToDevice));
+            build_sell_kernel<<<(unsigned)std::min<int64_t>(((int64_t)g->num_chunks * 32 + 255) / 256, 16384), 256>>>(
+                d_rp, d_ci, g->perm, d_inv, n, L.n_hub, g->num_chunks, g->chunk_off, g->chunk_len, g->sell_col);
+            CK(cudaGetLastError());
+        }
+        CK(cudaDeviceSynchronize());
+        dev_free(g, (void **)&d_inv, sizeof(int32_t) * n);
+        dev_free(g, (void **)&d_ci, ci_bytes);
+        dev_free(g, (void **)&d_rp, rp_bytes);
+        *out = g;
+        return CPAA_OK;
     }
-
-    ALLOC(g->deg64, sizeof(double) * n);
-    ALLOC(g->inv_deg64, sizeof(double) * n);
-    ALLOC(g->deg32, sizeof(float) * n);
-    ALLOC(g->inv_deg32, sizeof(float) * n);
-    degree_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256>>>(
-        g->row_ptr, n, g->deg64, g->inv_deg64, g->deg32, g->inv_deg32);
-    CK(cudaGetLastError());
-
-    std::vector<int4> chunks, blocks;
-    build_tiles(hrp.data(), n, chunks, blocks, g->num_long, g->total_chunks);
-    g->num_chunk_tiles = (int)chunks.size();
-    g->num_tiles = (int)(chunks.size() + blocks.size());
-    chunks.insert(chunks.end(), blocks.begin(), blocks.end());
-    ALLOC(g->tiles, sizeof(int4) * chunks.size());
-    CK(cudaMemcpy(g->tiles, chunks.data(), sizeof(int4) * chunks.size(), cudaMemcpyHostToDevice));
-    ALLOC(g->long_part, sizeof(double) * std::max(1, g->total_chunks));
-    ALLOC(g->long_cnt, sizeof(int) * std::max(1, g->num_long));
-    CK(cudaMemset(g->long_cnt, 0, sizeof(int) * std::max(1, g->num_long)));
-    CK(cudaDeviceSynchronize());
+fail_out:
+    if (d_inv) dev_free(g, (void **)&d_inv, sizeof(int32_t) * n);
+    if (d_ci) dev_free(g, (void **)&d_ci, ci_bytes);
+    if (d_rp) dev_free(g, (void **)&d_rp, rp_bytes);
+    release(g);
+    return st;
 #undef ALLOC
 #undef CK
-    *out = g;
-    return CPAA_OK;
 }
 
 extern "C" cpaa_status cpaa_graph_destroy(cpaa_graph *g) {
@@ -212,6 +339,6 @@ extern "C" cpaa_status cpaa_graph_info(const cpaa_graph *g, int64_t *n, int64_t 
     if (n) *n = g->n;
     if (nnz) *nnz = g->nnz;
     if (device_bytes) *device_bytes = g->device_bytes;
-    if (num_tiles) *num_tiles = g->num_tiles;
+    if (num_tiles) *num_tiles = (int64_t)g->num_hub_tiles + g->num_chunks;
     return CPAA_OK;
 }

@@ -1,0 +1,791 @@
+// server.cu -- cpaa_server_*: continuous batching of personalised PageRank
+// queries over resident graphs (see cpaa.h).
+//
+// Per graph: W column slots in one row-major [(n+1) x W] tile (the same
+// layout and round kernel as cpaa_solve_batch), one CUDA stream, a FIFO of
+// queued queries.  Two host threads:
+//   scheduler   - admits queued queries into free slots between rounds (a new
+//                 column's y_0 goes into the buffer the next round gathers
+//                 from, y[G & 1] after G rounds, so every column follows the
+//                 tile's ping-pong parity), launches one round per graph with
+//                 per-column first/active masks and coefficients, and after a
+//                 column's last round queues its finalisation;
+//   completion  - waits for a finished column's finalisation and marks the
+//                 query done; its vector stays in the slot's device buffer
+//                 until cpaa_server_wait copies it out and frees the slot (an
+//                 uncollected result holds its slot: back-pressure).
+// At most kInFlight rounds per graph are queued ahead of the device, so new
+// queries join quickly.  Each column's arithmetic is the same whatever the
+// other columns hold, so a result is bit-identical alone and in a mix.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <limits>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+
+#include "device_common.cuh"
+
+namespace cpaa {
+namespace srv {
+
+using clk = std::chrono::steady_clock;
+constexpr int kInFlight = 4;
+constexpr size_t kMaxQueue = size_t(1) << 20;
+
+__device__ __forceinline__ void sput(double *p, double v) { *p = v; }
+__device__ __forceinline__ void sput(float *p, double v) { *p = __double2float_rn(v); }
+__device__ __forceinline__ void sput(__nv_bfloat16 *p, double v) { *p = __double2bfloat16(v); }
+__device__ __forceinline__ double sget(const double *p) { return *p; }
+__device__ __forceinline__ double sget(const float *p) { return (double)*p; }
+__device__ __forceinline__ double sget(const __nv_bfloat16 *p) { return (double)__bfloat162float(*p); }
+
+struct SeedArgs {
+    int count;
+    int col;
+    double c0half;
+    int32_t r[CPAA_SERVER_MAX_SEEDS];  // new ids
+    double w[CPAA_SERVER_MAX_SEEDS];
+};
+
+// Column b of a new query: y_0 = D^-1 p, rho = (c_0/2) y_0, comp = 0, with p
+// zero outside the seeds (same arithmetic as the dense prep of solve.cu).
+template <class S, class R, int W>
+__global__ void slot_zero_kernel(S *y0, R *rho, R *comp, int64_t n, int b) {
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        y0[u * W + b] = S(0.0f);
+        rho[u * W + b] = R(0);
+        if (comp) comp[u * W + b] = R(0);
+    }
+}
+
+template <class S, class R, int W>
+__global__ void slot_seed_kernel(const SeedArgs a, const double *__restrict__ inv64, S *y0, R *rho) {
+    const int i = threadIdx.x;
+    if (i < a.count) {
+        const int64_t u = a.r[i];
+        sput(y0 + u * W + a.col, __dmul_rn(a.w[i], inv64[u]));
+        sput(rho + u * W + a.col, __dmul_rn(a.c0half, sget(y0 + u * W + a.col)));
+    }
+}
+
+// Normaliser of column b (fixed order, as in solve.cu) and the finalisation
+// into out (caller's order).
+template <class R, int W>
+__global__ void __launch_bounds__(kThreads) col_norm_kernel(const R *__restrict__ rho,
+                                                            const double *__restrict__ deg64,
+                                                            int64_t n, int b, double *part) {
+    __shared__ double s[kThreads];
+    double v = 0.0;
+    for (int64_t u = blockIdx.x * (int64_t)kThreads + threadIdx.x; u < n;
+         u += (int64_t)gridDim.x * kThreads)
+        v = __fma_rn(deg64[u], sget(rho + u * W + b), v);
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] = __dadd_rn(s[threadIdx.x], s[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+__global__ void __launch_bounds__(kThreads) col_sum_kernel(const double *part, int nblocks, double *out) {
+    __shared__ double s[kThreads];
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += kThreads) v = __dadd_rn(v, part[b]);
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] = __dadd_rn(s[threadIdx.x], s[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = s[0];
+}
+
+template <class R, int W>
+__global__ void __launch_bounds__(kThreads) col_finalize_kernel(const R *__restrict__ rho,
+                                                                const double *__restrict__ deg64,
+                                                                const int32_t *__restrict__ perm,
+                                                                int64_t n, int b, const double *sum,
+                                                                int normalize, double one_minus_c,
+                                                                double *out) {
+    const double scale = normalize == 0 ? __drcp_rn(*sum) : one_minus_c;
+    for (int64_t u = blockIdx.x * (int64_t)kThreads + threadIdx.x; u < n;
+         u += (int64_t)gridDim.x * kThreads)
+        out[perm[u]] = __dmul_rn(scale, __dmul_rn(deg64[u], sget(rho + u * W + b)));
+}
+
+struct GraphState;
+struct Request {
+    uint64_t ticket = 0;
+    int graph = 0;
+    SeedArgs seeds{};
+    double c = 0, tol = 0, kappa = 0;
+    int M = 0;
+    bool notconv = false;
+    enum State { PENDING, RUNNING, DONE, CANCELLED } state = PENDING;
+    bool cancel = false;
+    bool collecting = false;  // cpaa_server_wait is copying the result out
+    bool spilling = false;    // the completion thread is moving it to host memory
+    GraphState *gs = nullptr; // where the result waits (state DONE), or NULL once spilled
+    int slot = -1;
+    std::vector<double> host; // the result after a spill
+    clk::time_point t_submit, t_admit, t_done;
+};
+using ReqP = std::shared_ptr<Request>;
+
+enum SlotState { FREE, LIVE, FINISHING, READY };
+struct Slot {
+    ReqP req;
+    int k = 0;
+    SlotState st = FREE;
+    std::vector<double> ck;
+    cudaEvent_t done = nullptr;
+};
+
+struct GraphState {
+    int id = 0;
+    cpaa_graph *g = nullptr;
+    int W = 1;
+    cudaStream_t stream = nullptr;
+    void *y[2] = {nullptr, nullptr};
+    void *rho = nullptr, *comp = nullptr, *long_part = nullptr;
+    int *long_cnt = nullptr;
+    double *red = nullptr, *result = nullptr, *part = nullptr, *sums = nullptr;
+    size_t bytes = 0;
+    std::vector<int32_t> inv_perm;  // caller id -> new id
+    std::vector<double> deg;        // caller order
+    std::vector<Slot> slots;
+    std::deque<ReqP> pending;
+    int64_t G = 0;  // rounds launched
+    cudaEvent_t ring[kInFlight] = {};
+};
+
+struct Completion {
+    GraphState *gs;
+    int slot;
+    ReqP req;
+    bool spill;  // move a finished, uncollected result to host memory
+};
+
+}  // namespace srv
+}  // namespace cpaa
+
+using namespace cpaa;
+using namespace cpaa::srv;
+
+struct cpaa_server {
+    size_t budget = 0, used = 0;
+    int prec = CPAA_F32, normalize = 0, max_rounds = kDefaultMaxRounds;
+    int device = 0;
+    std::vector<std::unique_ptr<GraphState>> graphs;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done, cv_comp;
+    std::unordered_map<uint64_t, ReqP> reqs;
+    uint64_t next_ticket = 1;
+    std::deque<Completion> comps;
+    std::thread sched, comp_th;
+    bool stop = false;
+    cudaStream_t copy_stream = nullptr;
+    std::mutex copy_mu;
+    uint64_t submitted = 0, completed = 0, cancelled = 0, failed = 0;
+    std::vector<double> lat_us, admit_us;
+};
+
+namespace cpaa {
+namespace srv {
+
+static size_t vbytes(int prec) { return prec == CPAA_F64 ? 8 : prec == CPAA_F32 ? 4 : 2; }
+static size_t rbytes(int prec) { return prec == CPAA_F64 ? 8 : 4; }
+
+static size_t graph_bytes(const cpaa_graph *g, int prec, int W) {
+    const size_t n = (size_t)g->n;
+    return 2 * (n + 1) * W * vbytes(prec) + 2 * n * W * rbytes(prec) + n * W * 8 +
+           (size_t)std::max(1, g->num_hub_tiles) * W * 8 + (size_t)std::max(1, g->n_hub) * 4 +
+           (size_t)kPrepBlocks * 8 + (size_t)W * 8 + 2 * kRedSlots * 8 * (size_t)W;
+}
+
+template <class S, class R, int W>
+static void launch_slot_prep(GraphState &gs, int b, const SeedArgs &a) {
+    const int64_t n = gs.g->n;
+    const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 2048);
+    R *comp = std::is_same<R, float>::value ? (R *)gs.comp : nullptr;
+    S *y0 = (S *)gs.y[gs.G & 1];  // the buffer the next round gathers from
+    slot_zero_kernel<S, R, W><<<grid, 256, 0, gs.stream>>>(y0, (R *)gs.rho, comp, n, b);
+    slot_seed_kernel<S, R, W><<<1, CPAA_SERVER_MAX_SEEDS, 0, gs.stream>>>(a, gs.g->inv_deg64, y0, (R *)gs.rho);
+}
+
+template <class R, int W>
+static void launch_slot_final(GraphState &gs, int b, int normalize, double c) {
+    const int64_t n = gs.g->n;
+    const int blocks = stats_blocks(n);
+    const unsigned grid = (unsigned)std::min<int64_t>((n + kThreads - 1) / kThreads, 8192);
+    col_norm_kernel<R, W><<<blocks, kThreads, 0, gs.stream>>>((const R *)gs.rho, gs.g->deg64, n, b, gs.part);
+    col_sum_kernel<<<1, kThreads, 0, gs.stream>>>(gs.part, blocks, gs.sums + b);
+    col_finalize_kernel<R, W><<<grid, kThreads, 0, gs.stream>>>((const R *)gs.rho, gs.g->deg64, gs.g->perm, n, b,
+                                                               gs.sums + b, normalize, 1.0 - c,
+                                                               gs.result + (size_t)b * n);
+}
+
+template <class S, class R>
+static void slot_prep_w(GraphState &gs, int b, const SeedArgs &a) {
+    switch (gs.W) {
+        case 1: launch_slot_prep<S, R, 1>(gs, b, a); break;
+        case 2: launch_slot_prep<S, R, 2>(gs, b, a); break;
+        case 4: launch_slot_prep<S, R, 4>(gs, b, a); break;
+        case 8: launch_slot_prep<S, R, 8>(gs, b, a); break;
+        case 16: launch_slot_prep<S, R, 16>(gs, b, a); break;
+    }
+}
+
+template <class R>
+static void slot_final_w(GraphState &gs, int b, int normalize, double c) {
+    switch (gs.W) {
+        case 1: launch_slot_final<R, 1>(gs, b, normalize, c); break;
+        case 2: launch_slot_final<R, 2>(gs, b, normalize, c); break;
+        case 4: launch_slot_final<R, 4>(gs, b, normalize, c); break;
+        case 8: launch_slot_final<R, 8>(gs, b, normalize, c); break;
+        case 16: launch_slot_final<R, 16>(gs, b, normalize, c); break;
+    }
+}
+
+static void slot_prep(cpaa_server *s, GraphState &gs, int b, const SeedArgs &a) {
+    if (s->prec == CPAA_F64) slot_prep_w<double, double>(gs, b, a);
+    else if (s->prec == CPAA_F32) slot_prep_w<float, float>(gs, b, a);
+    else slot_prep_w<__nv_bfloat16, float>(gs, b, a);
+}
+
+static void slot_final(cpaa_server *s, GraphState &gs, int b, double c) {
+    if (s->prec == CPAA_F64) slot_final_w<double>(gs, b, s->normalize, c);
+    else slot_final_w<float>(gs, b, s->normalize, c);
+}
+
+static double us_since(clk::time_point a, clk::time_point b) {
+    return std::chrono::duration<double, std::micro>(b - a).count();
+}
+
+// One scheduling pass over a graph; true if anything was launched.
+static bool step_graph(cpaa_server *s, GraphState &gs) {
+    // at most kInFlight rounds queued: launch G+1 waits for launch G+1-kInFlight
+    if (gs.G + 1 > kInFlight && cudaEventQuery(gs.ring[(gs.G + 1) % kInFlight]) == cudaErrorNotReady)
+        return false;
+    std::vector<std::pair<int, SeedArgs>> admitted;
+    unsigned live = 0;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        const auto now = clk::now();
+        for (int b = 0; b < gs.W; ++b) {
+            Slot &sl = gs.slots[b];
+            if (sl.st == LIVE && sl.req->cancel) {
+                sl.req->state = Request::CANCELLED;
+                sl.req->t_done = now;
+                ++s->cancelled;
+                sl.req.reset();
+                sl.st = FREE;
+                s->cv_done.notify_all();
+            }
+        }
+        {
+            for (int b = 0; b < gs.W && !gs.pending.empty(); ++b) {
+                Slot &sl = gs.slots[b];
+                if (sl.st != FREE) continue;
+                ReqP r;
+                while (!gs.pending.empty() && !r) {
+                    r = gs.pending.front();
+                    gs.pending.pop_front();
+                    if (r->cancel) {  // cancelled while queued
+                        r->state = Request::CANCELLED;
+                        r->t_done = now;
+                        ++s->cancelled;
+                        s->cv_done.notify_all();
+                        r.reset();
+                    }
+                }
+                if (!r) break;
+                sl.req = r;
+                sl.k = 0;
+                sl.st = LIVE;
+                cheb_coeffs(r->c, r->M, sl.ck);
+                r->state = Request::RUNNING;
+                r->t_admit = now;
+                s->admit_us.push_back(us_since(r->t_submit, now));
+                SeedArgs a = r->seeds;
+                a.col = b;
+                a.c0half = sl.ck[0] / 2.0;
+                admitted.emplace_back(b, a);
+            }
+        }
+        for (int b = 0; b < gs.W; ++b)
+            if (gs.slots[b].st == LIVE) live |= 1u << b;
+        // queued queries but no free slot: spill uncollected results to host memory
+        if (!gs.pending.empty()) {
+            bool any_free = false;
+            for (auto &sl : gs.slots) any_free |= sl.st == FREE;
+            if (!any_free) {
+                bool queued = false;
+                for (int b = 0; b < gs.W; ++b) {
+                    Slot &sl = gs.slots[b];
+                    if (sl.st == READY && !sl.req->collecting && !sl.req->spilling) {
+                        sl.req->spilling = true;
+                        s->comps.push_back({&gs, b, sl.req, true});
+                        queued = true;
+                    }
+                }
+                if (queued) s->cv_comp.notify_one();
+            }
+        }
+    }
+    for (auto &a : admitted) slot_prep(s, gs, a.first, a.second);
+    if (!live) return !admitted.empty();
+
+    StepLaunch sl;
+    sl.g = gs.g;
+    sl.precision = s->prec;
+    sl.width = gs.W;
+    sl.y_src = gs.y[gs.G & 1];
+    sl.y_io = gs.y[(gs.G + 1) & 1];
+    sl.rho = gs.rho;
+    sl.comp = gs.comp;
+    sl.long_part = gs.long_part;
+    sl.red = gs.red;
+    sl.active = live;
+    sl.reduce = 0;
+    sl.first = ~live & ((1u << gs.W) - 1u);
+    sl.long_cnt = gs.long_cnt;
+    sl.stream = gs.stream;
+    for (int b = 0; b < kMaxWidth; ++b) sl.ck[b] = 0.0;
+    for (int b = 0; b < gs.W; ++b) {
+        if (!(live >> b & 1u)) continue;
+        const int k = gs.slots[b].k + 1;  // this column's round
+        sl.ck[b] = gs.slots[b].ck[k];
+        if (k == 1) sl.first |= 1u << b;
+    }
+    if (launch_step(sl) != cudaSuccess) return false;
+    ++gs.G;
+    cudaEventRecord(gs.ring[gs.G % kInFlight], gs.stream);
+    std::vector<Completion> done;
+    for (int b = 0; b < gs.W; ++b) {
+        if (!(live >> b & 1u)) continue;
+        Slot &slot = gs.slots[b];
+        if (++slot.k == slot.req->M) {
+            slot_final(s, gs, b, slot.req->c);
+            cudaEventRecord(slot.done, gs.stream);
+            done.push_back({&gs, b, slot.req, false});
+        }
+    }
+    if (!done.empty()) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (auto &c : done) {
+            gs.slots[c.slot].st = FINISHING;
+            s->comps.push_back(c);
+        }
+        s->cv_comp.notify_one();
+    }
+    return true;
+}
+
+static void scheduler_main(cpaa_server *s) {
+    cudaSetDevice(s->device);
+    for (;;) {
+        std::vector<GraphState *> gl;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            auto busy = [&]() {
+                for (auto &g : s->graphs) {
+                    if (!g->pending.empty()) return true;
+                    for (auto &sl : g->slots)
+                        if (sl.st == LIVE) return true;
+                }
+                return false;
+            };
+            s->cv_work.wait_for(lk, std::chrono::milliseconds(2), [&]() { return s->stop || busy(); });
+            if (s->stop) return;
+            for (auto &g : s->graphs) gl.push_back(g.get());
+        }
+        bool progressed = false;
+        for (auto *g : gl) progressed |= step_graph(s, *g);
+        if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+static void completion_main(cpaa_server *s) {
+    cudaSetDevice(s->device);
+    for (;;) {
+        Completion c;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_comp.wait(lk, [&]() { return s->stop || !s->comps.empty(); });
+            if (s->comps.empty()) return;  // stop requested and nothing left
+            c = s->comps.front();
+            s->comps.pop_front();
+        }
+        GraphState &gs = *c.gs;
+        if (c.spill) {
+            const int64_t n = gs.g->n;
+            std::vector<double> h((size_t)n);
+            cudaError_t e;
+            {
+                std::lock_guard<std::mutex> ck(s->copy_mu);
+                e = cudaMemcpyAsync(h.data(), gs.result + (size_t)c.slot * n, sizeof(double) * n,
+                                    cudaMemcpyDeviceToHost, s->copy_stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s->copy_stream);
+            }
+            std::lock_guard<std::mutex> lk(s->mu);
+            c.req->spilling = false;
+            if (e == cudaSuccess && c.req->state == Request::DONE && c.req->gs == &gs) {
+                c.req->host.swap(h);
+                Slot &sl = gs.slots[c.slot];
+                sl.req.reset();
+                sl.st = FREE;
+                c.req->gs = nullptr;
+                c.req->slot = -1;
+                s->cv_work.notify_one();
+            }
+            s->cv_done.notify_all();
+            continue;
+        }
+        const cudaError_t e = cudaEventSynchronize(gs.slots[c.slot].done);
+        std::lock_guard<std::mutex> lk(s->mu);
+        const auto now = clk::now();
+        c.req->t_done = now;
+        if (e == cudaSuccess) {
+            c.req->state = Request::DONE;
+            c.req->gs = &gs;
+            c.req->slot = c.slot;
+            gs.slots[c.slot].st = READY;
+            ++s->completed;
+            s->lat_us.push_back(us_since(c.req->t_submit, now));
+        } else {
+            c.req->state = Request::CANCELLED;
+            gs.slots[c.slot].req.reset();
+            gs.slots[c.slot].st = FREE;
+            ++s->failed;
+            s->cv_work.notify_one();
+        }
+        s->cv_done.notify_all();
+    }
+}
+
+// Free a READY slot (caller holds s->mu).
+static void release_slot(cpaa_server *s, Request &r) {
+    if (r.gs && r.slot >= 0) {
+        Slot &sl = r.gs->slots[r.slot];
+        sl.req.reset();
+        sl.st = FREE;
+        r.gs = nullptr;
+        r.slot = -1;
+        s->cv_work.notify_one();
+    }
+}
+
+static void free_graph_state(GraphState &gs) {
+    cudaFree(gs.y[0]); cudaFree(gs.y[1]); cudaFree(gs.rho); cudaFree(gs.comp); cudaFree(gs.long_part);
+    cudaFree(gs.long_cnt); cudaFree(gs.red); cudaFree(gs.result); cudaFree(gs.part); cudaFree(gs.sums);
+    for (auto &e : gs.ring) if (e) cudaEventDestroy(e);
+    for (auto &sl : gs.slots) if (sl.done) cudaEventDestroy(sl.done);
+    if (gs.stream) cudaStreamDestroy(gs.stream);
+}
+
+static double percentile(std::vector<double> v, double q) {
+    if (v.empty()) return 0.0;
+    const size_t k = std::min(v.size() - 1, (size_t)(q * (v.size() - 1) + 0.5));
+    std::nth_element(v.begin(), v.begin() + k, v.end());
+    return v[k];
+}
+
+}  // namespace srv
+}  // namespace cpaa
+
+extern "C" cpaa_status cpaa_server_create(size_t device_mem_budget, const cpaa_options *opt,
+                                          cpaa_server **out) {
+    clear_error();
+    if (!out) return fail(CPAA_EINVAL, "out is NULL");
+    *out = nullptr;
+    cpaa_options o;
+    if (opt) o = *opt;
+    else {
+        cpaa_options_init(&o);
+        o.precision = CPAA_F32;
+    }
+    if (o.precision != CPAA_F64 && o.precision != CPAA_F32 && o.precision != CPAA_BF16)
+        return fail(CPAA_EINVAL, "unknown precision");
+    if (o.normalize != 0 && o.normalize != 1) return fail(CPAA_EINVAL, "normalize must be 0 or 1");
+    cpaa_server *s = new cpaa_server();
+    s->budget = device_mem_budget;
+    s->prec = o.precision;
+    s->normalize = o.normalize;
+    s->max_rounds = o.max_rounds > 0 ? o.max_rounds : kDefaultMaxRounds;
+    cudaGetDevice(&s->device);
+    cudaError_t e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete s;
+        return cuda_fail(e, "cudaStreamCreateWithFlags");
+    }
+    s->sched = std::thread(scheduler_main, s);
+    s->comp_th = std::thread(completion_main, s);
+    *out = s;
+    return CPAA_OK;
+}
+
+extern "C" cpaa_status cpaa_server_add_graph(cpaa_server *s, cpaa_graph *g, int max_slots, int *graph_id) {
+    clear_error();
+    if (!s || !g || !graph_id) return fail(CPAA_EINVAL, "NULL argument");
+    if (max_slots < 0 || max_slots > kMaxWidth) return fail(CPAA_EINVAL, "max_slots must lie in [0, 16]");
+    int W = max_slots == 0 ? kMaxWidth : max_slots;
+    while (W & (W - 1)) --W;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        while (W >= 1 && s->used + graph_bytes(g, s->prec, W) > s->budget) W /= 2;
+        if (W < 1) return fail(CPAA_ENOMEM, "device memory budget too small for one slot of this graph");
+    }
+    auto gs = std::make_unique<GraphState>();
+    gs->g = g;
+    gs->W = W;
+    const int64_t n = g->n;
+    cpaa_status st = CPAA_OK;
+    cudaSetDevice(s->device);
+#define SALLOC(ptr, bytes)                                                       \
+    do {                                                                         \
+        cudaError_t e_ = cudaMalloc((void **)&(ptr), (bytes));                   \
+        if (e_ != cudaSuccess) { st = cuda_fail(e_, "cudaMalloc (server slots)"); goto fail_out; } \
+    } while (0)
+#define SCK(call)                                                                \
+    do {                                                                         \
+        cudaError_t e_ = (call);                                                 \
+        if (e_ != cudaSuccess) { st = cuda_fail(e_, #call); goto fail_out; }     \
+    } while (0)
+    {
+        const size_t vb = (size_t)(n + 1) * W * vbytes(s->prec), rb = (size_t)n * W * rbytes(s->prec);
+        SCK(cudaStreamCreateWithFlags(&gs->stream, cudaStreamNonBlocking));
+        SALLOC(gs->y[0], vb);
+        SALLOC(gs->y[1], vb);
+        SALLOC(gs->rho, rb);
+        SALLOC(gs->comp, rb);
+        SALLOC(gs->long_part, (size_t)std::max(1, g->num_hub_tiles) * W * 8);
+        SALLOC(gs->long_cnt, (size_t)std::max(1, g->n_hub) * 4);
+        SALLOC(gs->red, 2 * kRedSlots * 8 * (size_t)W);
+        SALLOC(gs->result, (size_t)n * W * 8);
+        SALLOC(gs->part, (size_t)kPrepBlocks * 8);
+        SALLOC(gs->sums, (size_t)W * 8);
+        SCK(cudaMemsetAsync(gs->y[0], 0, vb, gs->stream));
+        SCK(cudaMemsetAsync(gs->y[1], 0, vb, gs->stream));
+        SCK(cudaMemsetAsync(gs->long_cnt, 0, (size_t)std::max(1, g->n_hub) * 4, gs->stream));
+        for (auto &e : gs->ring) SCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        gs->slots.resize(W);
+        for (auto &sl : gs->slots) SCK(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
+        // host copies for admission: caller id -> new id, and degrees
+        std::vector<int32_t> perm((size_t)n);
+        std::vector<double> deg((size_t)n);
+        SCK(cudaMemcpy(perm.data(), g->perm, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+        SCK(cudaMemcpy(deg.data(), g->deg64, sizeof(double) * n, cudaMemcpyDeviceToHost));
+        gs->inv_perm.resize((size_t)n);
+        gs->deg.resize((size_t)n);
+        for (int64_t r = 0; r < n; ++r) {
+            gs->inv_perm[perm[r]] = (int32_t)r;
+            gs->deg[perm[r]] = deg[r];
+        }
+        SCK(cudaStreamSynchronize(gs->stream));
+        gs->bytes = graph_bytes(g, s->prec, W);
+        std::lock_guard<std::mutex> lk(s->mu);
+        gs->id = (int)s->graphs.size();
+        s->used += gs->bytes;
+        *graph_id = gs->id;
+        s->graphs.push_back(std::move(gs));
+        return CPAA_OK;
+    }
+fail_out:
+    free_graph_state(*gs);
+    return st;
+#undef SALLOC
+#undef SCK
+}
+
+extern "C" cpaa_status cpaa_server_submit(cpaa_server *s, int graph_id, int nseeds, const int32_t *seeds,
+                                          const double *weights, double c, double tol, uint64_t *ticket) {
+    clear_error();
+    if (!s || !seeds || !ticket) return fail(CPAA_EINVAL, "NULL argument");
+    GraphState *gs = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (graph_id < 0 || graph_id >= (int)s->graphs.size()) return fail(CPAA_ENOTFOUND, "unknown graph id");
+        gs = s->graphs[graph_id].get();
+    }
+    if (nseeds < 1 || nseeds > CPAA_SERVER_MAX_SEEDS)
+        return fail(CPAA_EINVAL, "nseeds must lie in [1, CPAA_SERVER_MAX_SEEDS]");
+    if (!(c > 0.0 && c < 1.0)) return fail(CPAA_EINVAL, "damping c must lie in (0, 1)");
+    if (!(tol > 0.0)) return fail(CPAA_EINVAL, "tol must be > 0");
+    const int64_t n = gs->g->n;
+    auto r = std::make_shared<Request>();
+    r->graph = graph_id;
+    r->c = c;
+    r->tol = tol;
+    r->seeds.count = nseeds;
+    double sumw = 0.0, q = 0.0;
+    for (int i = 0; i < nseeds; ++i) {
+        const int32_t v = seeds[i];
+        if (v < 0 || v >= n) return fail(CPAA_EINVAL, "seed vertex out of range");
+        for (int j = 0; j < i; ++j)
+            if (seeds[j] == v) return fail(CPAA_EINVAL, "seed vertices must be distinct");
+        const double w = weights ? weights[i] : 1.0 / nseeds;
+        if (!(w >= 0.0) || !(w < INFINITY)) return fail(CPAA_EINVAL, "weights must be finite and >= 0");
+        r->seeds.r[i] = gs->inv_perm[v];
+        r->seeds.w[i] = w;
+        sumw += w;
+        q += w * w / gs->deg[v];
+    }
+    if (!(std::fabs(sumw - 1.0) <= 1e-9)) return fail(CPAA_EINVAL, "weights must sum to 1");
+    r->kappa = std::sqrt((double)gs->g->nnz) * std::sqrt(q);
+    r->M = cpaa_rounds_needed(c, tol, r->kappa, s->normalize, s->max_rounds);
+    if (r->M < 0) {
+        r->M = s->max_rounds;
+        r->notconv = true;
+    }
+    r->t_submit = clk::now();
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (gs->pending.size() >= kMaxQueue) return fail(CPAA_EBUSY, "queue full");
+    r->ticket = s->next_ticket++;
+    s->reqs[r->ticket] = r;
+    gs->pending.push_back(r);
+    ++s->submitted;
+    *ticket = r->ticket;
+    s->cv_work.notify_one();
+    return CPAA_OK;
+}
+
+extern "C" cpaa_status cpaa_server_wait(cpaa_server *s, uint64_t ticket, double *pi, cpaa_info *info,
+                                        int64_t timeout_us) {
+    clear_error();
+    if (!s) return fail(CPAA_EINVAL, "server is NULL");
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return fail(CPAA_ENOTFOUND, "unknown ticket");
+    ReqP r = it->second;
+    auto ready = [&]() {
+        return (r->state == Request::DONE && !r->collecting && !r->spilling) ||
+               r->state == Request::CANCELLED;
+    };
+    if (timeout_us < 0) s->cv_done.wait(lk, ready);
+    else if (!s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready))
+        return fail(CPAA_ETIMEOUT, "query not finished yet");
+    if (r->state == Request::CANCELLED) {
+        s->reqs.erase(r->ticket);
+        return fail(CPAA_ECANCELLED, "query was cancelled");
+    }
+    r->collecting = true;  // the slot stays READY until the copy is done
+    GraphState *gs = r->gs;
+    const int slot = r->slot;
+    lk.unlock();
+    cudaError_t e = cudaSuccess;
+    if (pi) {
+        std::lock_guard<std::mutex> ck(s->copy_mu);
+        if (gs) {  // still in its slot
+            const int64_t n = gs->g->n;
+            e = cudaMemcpyAsync(pi, gs->result + (size_t)slot * n, sizeof(double) * n, cudaMemcpyDefault,
+                                s->copy_stream);
+        } else {   // spilled to host memory
+            e = cudaMemcpyAsync(pi, r->host.data(), sizeof(double) * r->host.size(), cudaMemcpyDefault,
+                                s->copy_stream);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->copy_stream);
+    }
+    lk.lock();
+    release_slot(s, *r);
+    s->reqs.erase(r->ticket);
+    lk.unlock();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync (server result)");
+    if (info) {
+        info->rounds = r->M;
+        info->kappa = r->kappa;
+        info->bound = cpaa_l1_bound(r->c, r->M, r->kappa, s->normalize);
+        info->mass = info->l1 = info->sum_pibar = std::numeric_limits<double>::quiet_NaN();  // not reduced when serving
+        info->rounds_ms = 0.0;
+    }
+    if (r->notconv) return fail(CPAA_ENOTCONV, "the L1 bound needs more than max_rounds rounds");
+    return CPAA_OK;
+}
+
+extern "C" cpaa_status cpaa_server_cancel(cpaa_server *s, uint64_t ticket) {
+    clear_error();
+    if (!s) return fail(CPAA_EINVAL, "server is NULL");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return fail(CPAA_ENOTFOUND, "unknown ticket");
+    ReqP r = it->second;
+    if (r->state == Request::CANCELLED) return fail(CPAA_EINVAL, "query already cancelled");
+    if (r->state == Request::DONE) {
+        if (r->collecting || r->spilling) return fail(CPAA_EBUSY, "query result is being copied; retry");
+        release_slot(s, *r);  // discard a finished result
+        r->state = Request::CANCELLED;
+        ++s->cancelled;
+        s->cv_done.notify_all();
+        return CPAA_OK;
+    }
+    if (r->state == Request::PENDING) {  // still queued: leave the queue now
+        auto &q = s->graphs[r->graph]->pending;
+        q.erase(std::remove(q.begin(), q.end(), r), q.end());
+        r->state = Request::CANCELLED;
+        r->t_done = clk::now();
+        ++s->cancelled;
+        s->cv_done.notify_all();
+        return CPAA_OK;
+    }
+    r->cancel = true;  // running: the scheduler frees its slot at its next pass
+    s->cv_work.notify_one();
+    return CPAA_OK;
+}
+
+extern "C" cpaa_status cpaa_server_get_stats(cpaa_server *s, cpaa_server_stats *out) {
+    clear_error();
+    if (!s || !out) return fail(CPAA_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    out->submitted = s->submitted;
+    out->completed = s->completed;
+    out->cancelled = s->cancelled;
+    out->failed = s->failed;
+    out->pending = 0;
+    out->running = 0;
+    out->slots = 0;
+    for (auto &g : s->graphs) {
+        out->pending += (int64_t)g->pending.size();
+        out->slots += g->W;
+        for (auto &sl : g->slots)
+            if (sl.st != FREE) ++out->running;
+    }
+    out->device_bytes = (int64_t)s->used;
+    out->p50_us = percentile(s->lat_us, 0.50);
+    out->p99_us = percentile(s->lat_us, 0.99);
+    double m = 0;
+    for (double v : s->lat_us) m += v;
+    out->mean_us = s->lat_us.empty() ? 0.0 : m / s->lat_us.size();
+    out->admit_p50_us = percentile(s->admit_us, 0.50);
+    return CPAA_OK;
+}
+
+extern "C" cpaa_status cpaa_server_destroy(cpaa_server *s) {
+    clear_error();
+    if (!s) return CPAA_OK;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    s->cv_comp.notify_all();
+    if (s->sched.joinable()) s->sched.join();
+    if (s->comp_th.joinable()) s->comp_th.join();
+    cudaSetDevice(s->device);
+    for (auto &g : s->graphs) cudaStreamSynchronize(g->stream);
+    {
+        // queries still queued or running end as cancelled
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (auto &kv : s->reqs) kv.second->state = Request::CANCELLED;
+        s->cv_done.notify_all();
+    }
+    for (auto &g : s->graphs) free_graph_state(*g);
+    if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+    delete s;
+    return CPAA_OK;
+}

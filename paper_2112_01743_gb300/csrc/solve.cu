@@ -1,12 +1,18 @@
-// solve.cu -- cpaa_solve: one personalised PageRank vector (Algorithm 1).
+// solve.cu -- the solve driver (Algorithm 1) for a tile of W vectors, and
+// cpaa_solve (W = 1).  batch.cu drives tiles of W > 1 through run_tile.
 //
+//   stats:     per vector, in a fixed order: sum p, sum p^2/d (for kappa) and a
+//              count of invalid entries;
+//   host:      kappa = sqrt(nnz) sqrt(sum p^2/d); M from the L1 bound;
 //   prep:      y_0 = D^-1 p, rho = (c_0/2) y_0 (Algorithm 1's initial
-//              accumulator, in scaled space), and in fixed order the sums
-//              sum p, sum p^2/d (for kappa) and a count of invalid entries;
-//   host:      kappa = sqrt(nnz) sqrt(sum p^2/d), M from the L1 bound;
-//   rounds:    M launches of the step kernel (step.cu);
+//              accumulator, in scaled space), comp = 0;
+//   rounds:    max M launches of the round kernel (step.cu); a vector stops
+//              accumulating after its own M;
 //   finalize:  pi = d * rho / sum(d * rho) (Algorithm 1's last line) or
-//              (1 - c) d * rho (Sec. 2.1).
+//              (1 - c) d * rho (Sec. 2.1), the sum in a fixed order.
+// Every sum a vector's result depends on runs in an order fixed by n alone,
+// and every rounding is an explicit intrinsic, so a vector gives the same bits
+// alone (cpaa_solve) and in any batch.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -15,21 +21,14 @@
 
 namespace cpaa {
 
-constexpr int kPrepBlocks = 1024;
-
-template <class S> struct VecOf;
-template <> struct VecOf<double> { using A = double; };
-template <> struct VecOf<float> { using A = float; };
-template <> struct VecOf<__nv_bfloat16> { using A = float; };
-
 __device__ __forceinline__ void put(double *p, double v) { *p = v; }
-__device__ __forceinline__ void put(float *p, double v) { *p = (float)v; }
+__device__ __forceinline__ void put(float *p, double v) { *p = __double2float_rn(v); }
 __device__ __forceinline__ void put(__nv_bfloat16 *p, double v) { *p = __double2bfloat16(v); }
 __device__ __forceinline__ double get(const double *p) { return *p; }
 __device__ __forceinline__ double get(const float *p) { return (double)*p; }
 __device__ __forceinline__ double get(const __nv_bfloat16 *p) { return (double)__bfloat162float(*p); }
 
-// Fixed-shape CTA sum of nq values per thread into out[0..nq).
+// Fixed-shape CTA sum of NQ values per thread into out[0..NQ).
 template <int NQ>
 __device__ __forceinline__ void cta_sum(double (&v)[NQ], double *out) {
     __shared__ double s[NQ][kThreads];
@@ -37,142 +36,289 @@ __device__ __forceinline__ void cta_sum(double (&v)[NQ], double *out) {
     __syncthreads();
     for (int o = kThreads / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o)
-            for (int q = 0; q < NQ; ++q) s[q][threadIdx.x] += s[q][threadIdx.x + o];
+            for (int q = 0; q < NQ; ++q) s[q][threadIdx.x] = __dadd_rn(s[q][threadIdx.x], s[q][threadIdx.x + o]);
         __syncthreads();
     }
     if (threadIdx.x == 0)
         for (int q = 0; q < NQ; ++q) out[q] = s[q][0];
+    __syncthreads();
 }
 
-// part[b][0..5] = sum p, sum p^2/d, #invalid, sum T_0, sum |T_0|, sum d rho_0
-template <class S, class R>
-__global__ void __launch_bounds__(kThreads) prep_kernel(const double *__restrict__ p, int64_t n,
-                                                        const double *__restrict__ deg64,
-                                                        const double *__restrict__ inv64,
-                                                        double c0half, S *y0, R *rho, R *comp,
-                                                        double *part) {
-    double v[6] = {0, 0, 0, 0, 0, 0};
+// Per-block partial sums of one vector p (caller's order, read through perm):
+// part[block][0..2] = sum p, sum p^2/d, #invalid (negative, NaN or inf).
+__global__ void __launch_bounds__(kThreads) stats_kernel(const double *__restrict__ p,
+                                                         const int32_t *__restrict__ perm, int64_t n,
+                                                         const double *__restrict__ inv64,
+                                                         double *part) {
+    double v[3] = {0, 0, 0};
     for (int64_t u = blockIdx.x * (int64_t)kThreads + threadIdx.x; u < n;
          u += (int64_t)gridDim.x * kThreads) {
-        const double pu = p[u];
-        const double d = deg64[u];
-        if (!(pu >= 0.0) || !(pu < INFINITY)) v[2] += 1.0;  // negative, NaN or inf
-        v[0] += pu;
-        v[1] += pu * pu * inv64[u];
-        put(y0 + u, pu * inv64[u]);
-        const double yq = get(y0 + u);
-        put(rho + u, c0half * yq);
-        if (comp) put(comp + u, 0.0);
-        const double r = get(rho + u);
-        v[3] += yq * d;
-        v[4] += fabs(yq * d);
-        v[5] += r * d;
+        const double pu = p[perm[u]];
+        if (!(pu >= 0.0) || !(pu < INFINITY)) v[2] = __dadd_rn(v[2], 1.0);
+        v[0] = __dadd_rn(v[0], pu);
+        v[1] = __fma_rn(__dmul_rn(pu, pu), inv64[u], v[1]);
     }
-    cta_sum<6>(v, part + 6 * blockIdx.x);
+    cta_sum<3>(v, part + 3 * blockIdx.x);
 }
 
 // One CTA: out[q] = sum over blocks of part[b][q], fixed order.
-__global__ void __launch_bounds__(kThreads) prep_reduce_kernel(const double *part, int nblocks,
-                                                               double *out, double *red0) {
-    double v[6] = {0, 0, 0, 0, 0, 0};
+template <int NQ>
+__global__ void __launch_bounds__(kThreads) block_sum_kernel(const double *part, int nblocks,
+                                                             double *out) {
+    double v[NQ];
+    for (int q = 0; q < NQ; ++q) v[q] = 0.0;
     for (int b = threadIdx.x; b < nblocks; b += kThreads)
-        for (int q = 0; q < 6; ++q) v[q] += part[6 * b + q];
-    double r[6];
-    cta_sum<6>(v, r);
-    if (threadIdx.x == 0) {
-        out[0] = r[0];
-        out[1] = r[1];
-        out[2] = r[2];
-        // round 0 of the per-round reductions lives in slot 0 of red0
-        red0[0 * kRedSlots] = r[3];
-        red0[1 * kRedSlots] = r[4];
-        red0[2 * kRedSlots] = r[5];
+        for (int q = 0; q < NQ; ++q) v[q] = __dadd_rn(v[q], part[NQ * b + q]);
+    cta_sum<NQ>(v, out);
+}
+
+struct TileCols {
+    const double *p[kMaxWidth];  // column b of the caller's input (device)
+    double *pi[kMaxWidth];       // column b of the output (device)
+    double c0half[kMaxWidth];
+    double scale[kMaxWidth];     // (1 - c) for normalize = 1
+};
+
+// y_0 = D^-1 p, rho = (c_0/2) y_0, comp = 0 for the W columns of a tile.
+template <class S, class R, int W>
+__global__ void __launch_bounds__(kThreads) prep_kernel(const TileCols cols,
+                                                        const int32_t *__restrict__ perm, int64_t n,
+                                                        const double *__restrict__ inv64, S *y0,
+                                                        R *rho, R *comp) {
+    for (int64_t u = blockIdx.x * (int64_t)kThreads + threadIdx.x; u < n;
+         u += (int64_t)gridDim.x * kThreads) {
+        const int32_t src = perm[u];
+        const double inv = inv64[u];
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            put(y0 + u * W + b, __dmul_rn(cols.p[b][src], inv));
+            put(rho + u * W + b, __dmul_rn(cols.c0half[b], get(y0 + u * W + b)));
+            if (comp) put(comp + u * W + b, 0.0);
+        }
     }
 }
 
-// Normaliser of Algorithm 1's last line, sum_u pibar[u] = sum_u d_u rho[u],
-// in a fixed order: per-CTA partials over a fixed grid, then one CTA.  The
-// order depends only on n, so a vector's result never depends on what else
-// ran before or beside it.
-template <class R>
+// Per-block partials of sum_u d_u rho[u] for each column (fixed order).
+template <class R, int W>
 __global__ void __launch_bounds__(kThreads) norm_partial_kernel(const R *__restrict__ rho,
                                                                 const double *__restrict__ deg64,
                                                                 int64_t n, double *part) {
-    double v[1] = {0.0};
+    double v[W];
+#pragma unroll
+    for (int b = 0; b < W; ++b) v[b] = 0.0;
     for (int64_t u = blockIdx.x * (int64_t)kThreads + threadIdx.x; u < n;
          u += (int64_t)gridDim.x * kThreads)
-        v[0] += deg64[u] * get(rho + u);
-    cta_sum<1>(v, part + blockIdx.x);
+#pragma unroll
+        for (int b = 0; b < W; ++b) v[b] = __fma_rn(deg64[u], get(rho + u * W + b), v[b]);
+    cta_sum<W>(v, part + W * blockIdx.x);
 }
 
-__global__ void __launch_bounds__(kThreads) norm_reduce_kernel(const double *part, int nblocks,
-                                                               double *out) {
-    double v[1] = {0.0};
-    for (int b = threadIdx.x; b < nblocks; b += kThreads) v[0] += part[b];
-    cta_sum<1>(v, out);
-}
-
-// pi[u] = scale * d_u * rho[u]; scale = 1 / sum(d rho) or (1 - c).
-template <class R>
-__global__ void __launch_bounds__(kThreads) finalize_kernel(const R *__restrict__ rho,
+// pi_b[perm[u]] = scale_b * d_u * rho[u][b].
+template <class R, int W>
+__global__ void __launch_bounds__(kThreads) finalize_kernel(const TileCols cols,
+                                                            const R *__restrict__ rho,
                                                             const double *__restrict__ deg64,
-                                                            int64_t n, const double *sum_pibar,
-                                                            int normalize, double one_minus_c,
-                                                            double *pi) {
-    const double scale = normalize == 0 ? 1.0 / *sum_pibar : one_minus_c;
+                                                            const int32_t *__restrict__ perm,
+                                                            int64_t n, const double *sums,
+                                                            int normalize) {
+    __shared__ double s_scale[W];
+    if (threadIdx.x < W)
+        s_scale[threadIdx.x] = normalize == 0 ? __drcp_rn(sums[threadIdx.x]) : cols.scale[threadIdx.x];
+    __syncthreads();
     for (int64_t u = blockIdx.x * (int64_t)kThreads + threadIdx.x; u < n;
-         u += (int64_t)gridDim.x * kThreads)
-        pi[u] = scale * (deg64[u] * get(rho + u));
+         u += (int64_t)gridDim.x * kThreads) {
+        const int32_t dst = perm[u];
+        const double d = deg64[u];
+#pragma unroll
+        for (int b = 0; b < W; ++b)
+            cols.pi[b][dst] = __dmul_rn(s_scale[b], __dmul_rn(d, get(rho + u * W + b)));
+    }
 }
 
 static size_t store_bytes(int prec) { return prec == CPAA_F64 ? 8 : prec == CPAA_F32 ? 4 : 2; }
-static size_t rho_bytes(int prec) { return prec == CPAA_F64 ? 8 : 4; }
 
-static cpaa_status ensure_workspace(cpaa_graph *g, int prec, int max_rounds, bool host_io) {
+int stats_blocks(int64_t n) { return (int)std::min<int64_t>((n + kThreads - 1) / kThreads, kPrepBlocks); }
+
+cpaa_status ensure_workspace(cpaa_graph *g, int prec, int width, int max_rounds) {
     Workspace &w = g->ws;
     const int64_t n = g->n;
     cpaa_status st;
-    if (w.precision != prec) {
+    const size_t vb = store_bytes(prec) * (size_t)(n + 1) * width;
+    const size_t rb = 8 * (size_t)n * width;  // sized for FP64 so precisions can share it
+    if (w.vec_bytes < vb) {
         dev_free(g, &w.y0, w.vec_bytes);
         dev_free(g, &w.y1, w.vec_bytes);
-        dev_free(g, &w.rho, n * 8);
-        dev_free(g, &w.comp, n * 4);
-        w.precision = -1;
-        w.vec_bytes = store_bytes(prec) * n;
-        if ((st = dev_alloc(g, &w.y0, w.vec_bytes)) != CPAA_OK) return st;
-        if ((st = dev_alloc(g, &w.y1, w.vec_bytes)) != CPAA_OK) return st;
-        // rho is sized for FP64 so a later precision switch can reuse it
-        if ((st = dev_alloc(g, &w.rho, n * 8)) != CPAA_OK) return st;
-        if ((st = dev_alloc(g, &w.comp, n * 4)) != CPAA_OK) return st;
-        w.precision = prec;
+        w.vec_bytes = 0;
+        if ((st = dev_alloc(g, &w.y0, vb)) != CPAA_OK) return st;
+        if ((st = dev_alloc(g, &w.y1, vb)) != CPAA_OK) return st;
+        w.vec_bytes = vb;
     }
-    if (w.red_rounds < max_rounds + 1) {
-        dev_free(g, (void **)&w.red, sizeof(double) * kRedQ * kRedSlots * w.red_rounds);
-        w.red_rounds = 0;
-        if ((st = dev_alloc(g, (void **)&w.red, sizeof(double) * kRedQ * kRedSlots * (max_rounds + 1))) != CPAA_OK)
-            return st;
-        w.red_rounds = max_rounds + 1;
+    if (w.rho_bytes < rb) {
+        dev_free(g, &w.rho, w.rho_bytes);
+        dev_free(g, &w.comp, w.rho_bytes);
+        w.rho_bytes = 0;
+        if ((st = dev_alloc(g, &w.rho, rb)) != CPAA_OK) return st;
+        if ((st = dev_alloc(g, &w.comp, rb)) != CPAA_OK) return st;
+        w.rho_bytes = rb;
     }
-    if (!w.prep_part) {
-        if ((st = dev_alloc(g, (void **)&w.prep_part, sizeof(double) * 6 * kPrepBlocks)) != CPAA_OK) return st;
-        if ((st = dev_alloc(g, (void **)&w.prep_out, sizeof(double) * 4)) != CPAA_OK) return st;
-        CPAA_CUDA(cudaMallocHost((void **)&w.h_prep, sizeof(double) * 4));
+    const size_t red = sizeof(double) * 2 * kRedSlots * (size_t)width * (max_rounds + 1);
+    if (w.red_bytes < red) {
+        dev_free(g, (void **)&w.red, w.red_bytes);
+        w.red_bytes = 0;
+        if ((st = dev_alloc(g, (void **)&w.red, red)) != CPAA_OK) return st;
+        w.red_bytes = red;
     }
-    if (host_io && !w.d_pi) {
-        if ((st = dev_alloc(g, (void **)&w.d_pi, sizeof(double) * n)) != CPAA_OK) return st;
-        if ((st = dev_alloc(g, (void **)&w.d_p, sizeof(double) * n)) != CPAA_OK) return st;
+    const size_t lp = sizeof(double) * std::max(1, g->num_hub_tiles) * (size_t)width;
+    if (w.long_part_bytes < lp) {
+        dev_free(g, &w.long_part, w.long_part_bytes);
+        w.long_part_bytes = 0;
+        if ((st = dev_alloc(g, &w.long_part, lp)) != CPAA_OK) return st;
+        w.long_part_bytes = lp;
     }
-    (void)rho_bytes;
+    if (!w.part) {
+        if ((st = dev_alloc(g, (void **)&w.part, sizeof(double) * kMaxWidth * kPrepBlocks * 3)) != CPAA_OK) return st;
+        if ((st = dev_alloc(g, (void **)&w.sums, sizeof(double) * 4 * kMaxWidth)) != CPAA_OK) return st;
+        CPAA_CUDA(cudaMallocHost((void **)&w.h_sums, sizeof(double) * 4 * kMaxWidth));
+    }
     return CPAA_OK;
 }
 
-template <class S, class R>
-static void launch_prep(cpaa_graph *g, const double *p, double c0half, cudaStream_t st, int blocks) {
+// sum p, sum p^2/d and #invalid of one device vector into out[0..2] (device),
+// in the same order for every caller.
+cudaError_t launch_stats(cpaa_graph *g, const double *p, double *out, cudaStream_t st) {
+    const int blocks = stats_blocks(g->n);
+    stats_kernel<<<blocks, kThreads, 0, st>>>(p, g->perm, g->n, g->inv_deg64, g->ws.part);
+    block_sum_kernel<3><<<1, kThreads, 0, st>>>(g->ws.part, blocks, out);
+    return cudaGetLastError();
+}
+
+cpaa_status check_stats(const double *s, int64_t nnz, double *kappa) {
+    if (s[2] > 0.0) return fail(CPAA_EINVAL, "p has negative, NaN or infinite entries");
+    if (!(std::fabs(s[0] - 1.0) <= 1e-9)) return fail(CPAA_EINVAL, "p must sum to 1 (|sum p - 1| <= 1e-9)");
+    *kappa = std::sqrt((double)nnz) * std::sqrt(s[1]);
+    return CPAA_OK;
+}
+
+template <class S, class R, int W>
+static cudaError_t tile_kernels(cpaa_graph *g, const TileJob &job, cudaStream_t st, int phase) {
     Workspace &w = g->ws;
-    prep_kernel<S, R><<<blocks, kThreads, 0, st>>>(p, g->n, g->deg64, g->inv_deg64, c0half,
-                                                   (S *)w.y0, (R *)w.rho,
-                                                   std::is_same<R, float>::value ? (R *)w.comp : nullptr,
-                                                   w.prep_part);
+    const int64_t n = g->n;
+    TileCols cols;
+    for (int b = 0; b < kMaxWidth; ++b) {
+        const int bb = b < job.width ? b : 0;
+        cols.p[b] = job.p[bb];
+        cols.pi[b] = job.pi[bb];
+        cols.c0half[b] = job.c0half[bb];
+        cols.scale[b] = 1.0 - job.c[bb];
+    }
+    const unsigned grid = (unsigned)std::min<int64_t>((n + kThreads - 1) / kThreads, 8192);
+    if (phase == 0) {
+        prep_kernel<S, R, W><<<grid, kThreads, 0, st>>>(cols, g->perm, n, g->inv_deg64, (S *)w.y0,
+                                                        (R *)w.rho,
+                                                        std::is_same<R, float>::value ? (R *)w.comp : nullptr);
+    } else {
+        const int blocks = stats_blocks(n);
+        norm_partial_kernel<R, W><<<blocks, kThreads, 0, st>>>((const R *)w.rho, g->deg64, n, w.part);
+        block_sum_kernel<W><<<1, kThreads, 0, st>>>(w.part, blocks, w.sums);
+        finalize_kernel<R, W><<<grid, kThreads, 0, st>>>(cols, (const R *)w.rho, g->deg64, g->perm, n,
+                                                         w.sums, job.normalize);
+    }
+    return cudaGetLastError();
+}
+
+template <class S, class R>
+static cudaError_t tile_kernels_w(cpaa_graph *g, const TileJob &job, cudaStream_t st, int phase) {
+    switch (job.width) {
+        case 1: return tile_kernels<S, R, 1>(g, job, st, phase);
+        case 2: return tile_kernels<S, R, 2>(g, job, st, phase);
+        case 4: return tile_kernels<S, R, 4>(g, job, st, phase);
+        case 8: return tile_kernels<S, R, 8>(g, job, st, phase);
+        case 16: return tile_kernels<S, R, 16>(g, job, st, phase);
+    }
+    return cudaErrorInvalidValue;
+}
+
+static cudaError_t tile_phase(cpaa_graph *g, const TileJob &job, cudaStream_t st, int phase) {
+    switch (job.precision) {
+        case CPAA_F64: return tile_kernels_w<double, double>(g, job, st, phase);
+        case CPAA_F32: return tile_kernels_w<float, float>(g, job, st, phase);
+        case CPAA_BF16: return tile_kernels_w<__nv_bfloat16, float>(g, job, st, phase);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// Prep, the rounds and the finalisation of one tile (workspace must be sized).
+// rounds_ms (if not NULL) receives the device time of the round launches.
+cpaa_status run_tile(cpaa_graph *g, const TileJob &job, cudaStream_t st, bool history_all_rounds,
+                     float *rounds_ms) {
+    Workspace &w = g->ws;
+    const int64_t n = g->n;
+    const int W = job.width;
+    int maxM = 0;
+    for (int b = 0; b < W; ++b) maxM = std::max(maxM, job.rounds[b]);
+    const size_t vb = store_bytes(job.precision) * (size_t)W;
+    CPAA_CUDA(cudaMemsetAsync(w.red, 0, sizeof(double) * 2 * kRedSlots * W * (size_t)(maxM + 1), st));
+    CPAA_CUDA(cudaMemsetAsync(g->long_cnt, 0, sizeof(int) * std::max(1, g->n_hub), st));
+    CPAA_CUDA(cudaMemsetAsync((char *)w.y0 + vb * n, 0, vb, st));  // sentinel row n
+    CPAA_CUDA(cudaMemsetAsync((char *)w.y1 + vb * n, 0, vb, st));
+    CPAA_CUDA(tile_phase(g, job, st, 0));
+
+    std::vector<std::vector<double>> ck(W);
+    for (int b = 0; b < W; ++b) cheb_coeffs(job.c[b], job.rounds[b], ck[b]);
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (rounds_ms) {
+        CPAA_CUDA(cudaEventCreate(&ev[0]));
+        CPAA_CUDA(cudaEventCreate(&ev[1]));
+        CPAA_CUDA(cudaEventRecord(ev[0], st));
+    }
+    void *buf[2] = {w.y0, w.y1};
+    for (int k = 1; k <= maxM; ++k) {
+        StepLaunch sl;
+        sl.g = g;
+        sl.precision = job.precision;
+        sl.width = W;
+        sl.y_src = buf[(k - 1) & 1];
+        sl.y_io = buf[k & 1];
+        sl.rho = w.rho;
+        sl.comp = w.comp;
+        sl.long_part = w.long_part;
+        sl.red = w.red + (size_t)k * 2 * W * kRedSlots;
+        sl.active = 0;
+        sl.reduce = 0;
+        for (int b = 0; b < kMaxWidth; ++b) sl.ck[b] = 0.0;
+        for (int b = 0; b < W; ++b) {
+            if (k <= job.rounds[b]) {
+                sl.active |= 1u << b;
+                sl.ck[b] = ck[b][k];
+            }
+            if (k == job.rounds[b] || (history_all_rounds && k <= job.rounds[b])) sl.reduce |= 1u << b;
+        }
+        sl.first = (k == 1) ? (1u << W) - 1u : 0u;
+        sl.long_cnt = nullptr;
+        sl.stream = st;
+        CPAA_CUDA(launch_step(sl));
+    }
+    if (rounds_ms) {
+        CPAA_CUDA(cudaEventRecord(ev[1], st));
+        CPAA_CUDA(cudaEventSynchronize(ev[1]));
+        CPAA_CUDA(cudaEventElapsedTime(rounds_ms, ev[0], ev[1]));
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+    }
+    CPAA_CUDA(tile_phase(g, job, st, 1));
+    return CPAA_OK;
+}
+
+// Sums of column b (of a tile of `width`) in round k from the host copy h of
+// the reduction slots.
+void round_sums(int width, int b, int k, const std::vector<double> &h, double *sumT, double *sumA) {
+    double a = 0, c = 0;
+    for (int i = 0; i < kRedSlots; ++i) {
+        a += h[(((size_t)k * 2 + 0) * width + b) * kRedSlots + i];
+        c += h[(((size_t)k * 2 + 1) * width + b) * kRedSlots + i];
+    }
+    *sumT = a;
+    *sumA = c;
 }
 
 }  // namespace cpaa
@@ -197,37 +343,29 @@ extern "C" cpaa_status cpaa_solve(cpaa_graph *g, const double *p, double c, doub
     const bool host_io = (opt.flags & CPAA_DEVICE_IO) == 0;
     cudaStream_t st = (cudaStream_t)opt.stream;
     const int64_t n = g->n;
-    const int prec = opt.precision;
 
-    cpaa_status s = ensure_workspace(g, prec, max_rounds, host_io);
+    cpaa_status s = ensure_workspace(g, opt.precision, 1, max_rounds);
     if (s != CPAA_OK) return s;
     Workspace &w = g->ws;
+    if (host_io && w.io_bytes < 2 * sizeof(double) * (size_t)n) {
+        dev_free(g, (void **)&w.io, w.io_bytes);
+        w.io_bytes = 0;
+        if ((s = dev_alloc(g, (void **)&w.io, 2 * sizeof(double) * n)) != CPAA_OK) return s;
+        w.io_bytes = 2 * sizeof(double) * n;
+    }
     const double *dp = p;
     double *dpi = pi;
     if (host_io) {
-        CPAA_CUDA(cudaMemcpyAsync(w.d_p, p, sizeof(double) * n, cudaMemcpyHostToDevice, st));
-        dp = w.d_p;
-        dpi = w.d_pi;
+        CPAA_CUDA(cudaMemcpyAsync(w.io, p, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+        dp = w.io;
+        dpi = w.io + n;
     }
-
-    std::vector<double> ck;
-    cheb_coeffs(c, 0, ck);
-    const double c0half = ck[0] / 2.0;
-    const int blocks = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, kPrepBlocks);
-    CPAA_CUDA(cudaMemsetAsync(w.red, 0, sizeof(double) * kRedQ * kRedSlots * (max_rounds + 1), st));
-    CPAA_CUDA(cudaMemsetAsync(g->long_cnt, 0, sizeof(int) * std::max(1, g->num_long), st));
-    if (prec == CPAA_F64) launch_prep<double, double>(g, dp, c0half, st, blocks);
-    else if (prec == CPAA_F32) launch_prep<float, float>(g, dp, c0half, st, blocks);
-    else launch_prep<__nv_bfloat16, float>(g, dp, c0half, st, blocks);
-    CPAA_CUDA(cudaGetLastError());
-    prep_reduce_kernel<<<1, kThreads, 0, st>>>(w.prep_part, blocks, w.prep_out, w.red);
-    CPAA_CUDA(cudaGetLastError());
-    CPAA_CUDA(cudaMemcpyAsync(w.h_prep, w.prep_out, sizeof(double) * 3, cudaMemcpyDeviceToHost, st));
+    CPAA_CUDA(launch_stats(g, dp, w.sums, st));
+    CPAA_CUDA(cudaMemcpyAsync(w.h_sums, w.sums, sizeof(double) * 3, cudaMemcpyDeviceToHost, st));
     CPAA_CUDA(cudaStreamSynchronize(st));
-    const double sum_p = w.h_prep[0], q = w.h_prep[1], nbad = w.h_prep[2];
-    if (nbad > 0.0) return fail(CPAA_EINVAL, "p has negative, NaN or infinite entries");
-    if (!(std::fabs(sum_p - 1.0) <= 1e-9)) return fail(CPAA_EINVAL, "p must sum to 1 (|sum p - 1| <= 1e-9)");
-    const double kappa = std::sqrt((double)g->nnz) * std::sqrt(q);
+    double kappa = 0;
+    if ((s = check_stats(w.h_sums, g->nnz, &kappa)) != CPAA_OK) return s;
+    const double sum_p = w.h_sums[0];
 
     cpaa_status result = CPAA_OK;
     int M = opt.fixed_rounds;
@@ -238,77 +376,42 @@ extern "C" cpaa_status cpaa_solve(cpaa_graph *g, const double *p, double c, doub
             result = CPAA_ENOTCONV;
         }
     }
-    cheb_coeffs(c, M, ck);
-
-    const bool timed = (opt.flags & CPAA_TIME_ROUNDS) != 0;
-    cudaEvent_t ev[2] = {nullptr, nullptr};
-    if (timed) {
-        CPAA_CUDA(cudaEventCreate(&ev[0]));
-        CPAA_CUDA(cudaEventCreate(&ev[1]));
-        CPAA_CUDA(cudaEventRecord(ev[0], st));
-    }
-    void *buf[2] = {w.y0, w.y1};
-    for (int k = 1; k <= M; ++k) {
-        StepLaunch sl;
-        sl.g = g;
-        sl.precision = prec;
-        sl.y_src = buf[(k - 1) & 1];
-        sl.y_io = buf[k & 1];
-        sl.rho = w.rho;
-        sl.comp = w.comp;
-        sl.red = w.red + (size_t)k * kRedQ * kRedSlots;
-        sl.ck = ck[k];
-        sl.first = (k == 1);
-        sl.last = (k == M);
-        sl.stream = st;
-        CPAA_CUDA(launch_step(sl));
-    }
-    if (timed) CPAA_CUDA(cudaEventRecord(ev[1], st));
-    const unsigned fblocks = (unsigned)std::min<int64_t>((n + kThreads - 1) / kThreads, 4096);
-    double *sum_pibar = w.prep_out + 3;
-    if (prec == CPAA_F64) {
-        norm_partial_kernel<double><<<blocks, kThreads, 0, st>>>((const double *)w.rho, g->deg64, n, w.prep_part);
-        norm_reduce_kernel<<<1, kThreads, 0, st>>>(w.prep_part, blocks, sum_pibar);
-        finalize_kernel<double><<<fblocks, kThreads, 0, st>>>((const double *)w.rho, g->deg64, n, sum_pibar,
-                                                              opt.normalize, 1.0 - c, dpi);
-    } else {
-        norm_partial_kernel<float><<<blocks, kThreads, 0, st>>>((const float *)w.rho, g->deg64, n, w.prep_part);
-        norm_reduce_kernel<<<1, kThreads, 0, st>>>(w.prep_part, blocks, sum_pibar);
-        finalize_kernel<float><<<fblocks, kThreads, 0, st>>>((const float *)w.rho, g->deg64, n, sum_pibar,
-                                                             opt.normalize, 1.0 - c, dpi);
-    }
-    CPAA_CUDA(cudaGetLastError());
+    std::vector<double> ck0;
+    cheb_coeffs(c, 0, ck0);
+    TileJob job;
+    job.width = 1;
+    job.precision = opt.precision;
+    job.normalize = opt.normalize;
+    job.p[0] = dp;
+    job.pi[0] = dpi;
+    job.c[0] = c;
+    job.c0half[0] = ck0[0] / 2.0;
+    job.rounds[0] = M;
+    float rounds_ms = 0.0f;
+    if ((s = run_tile(g, job, st, true, (opt.flags & CPAA_TIME_ROUNDS) ? &rounds_ms : nullptr)) != CPAA_OK)
+        return s;
     if (host_io) CPAA_CUDA(cudaMemcpyAsync(pi, dpi, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
 
-    float rounds_ms = 0.0f;
-    if (timed) {
-        CPAA_CUDA(cudaEventSynchronize(ev[1]));
-        CPAA_CUDA(cudaEventElapsedTime(&rounds_ms, ev[0], ev[1]));
-        cudaEventDestroy(ev[0]);
-        cudaEventDestroy(ev[1]);
-    }
     if (info || opt.history) {
-        std::vector<double> h((size_t)(M + 1) * kRedQ * kRedSlots);
+        std::vector<double> h((size_t)(M + 1) * 2 * kRedSlots);
         CPAA_CUDA(cudaMemcpyAsync(h.data(), w.red, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st));
-        CPAA_CUDA(cudaMemcpyAsync(w.h_prep + 3, sum_pibar, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CPAA_CUDA(cudaMemcpyAsync(w.h_sums + 3, w.sums, sizeof(double), cudaMemcpyDeviceToHost, st));
         CPAA_CUDA(cudaStreamSynchronize(st));
-        auto sum = [&](int k, int qq) {
-            double a = 0;
-            for (int i = 0; i < kRedSlots; ++i) a += h[((size_t)k * kRedQ + qq) * kRedSlots + i];
-            return a;
-        };
-        if (opt.history)
-            for (int k = 0; k <= M; ++k) {
-                opt.history[2 * k] = sum(k, 0);
-                opt.history[2 * k + 1] = sum(k, 1);
-            }
+        // round 0 is T_0 = p >= 0: sum T_0 = sum |T_0| = sum p (from the stats)
+        if (opt.history) {
+            opt.history[0] = opt.history[1] = sum_p;
+            for (int k = 1; k <= M; ++k) round_sums(1, 0, k, h, &opt.history[2 * k], &opt.history[2 * k + 1]);
+        }
         if (info) {
             info->rounds = M;
             info->kappa = kappa;
             info->bound = cpaa_l1_bound(c, M, kappa, opt.normalize);
-            info->mass = sum(M, 0);
-            info->l1 = sum(M, 1);
-            info->sum_pibar = w.h_prep[3];
+            if (M == 0) {
+                info->mass = info->l1 = sum_p;
+            } else {
+                round_sums(1, 0, M, h, &info->mass, &info->l1);
+            }
+            info->sum_pibar = w.h_sums[3];
             info->rounds_ms = rounds_ms;
         }
     } else if (host_io) {

@@ -1,5 +1,8 @@
-// step.cu -- one round of the Chebyshev recurrence, fused with the
-// accumulation and the per-round reductions (Algorithm 1, Sec. 4.1).
+// step.cu -- one round of the Chebyshev recurrence for a tile of W vectors,
+// fused with the accumulation and the per-round reductions (Algorithm 1,
+// Sec. 4.1).  W = 1 is the single-vector solve; W > 1 is the batched form
+// (an SpMM: each gathered neighbour row brings W values at once).  Both use
+// this one kernel, so a vector's result does not depend on how it was batched.
 //
 // Scaled space.  The kernels keep y_k = D^-1 T_k p instead of T_k p.  Then
 //     (P T_k)[u] = sum_{j in N(u)} T_k[j] / d_j = sum_{j in N(u)} y_k[j],
@@ -11,277 +14,432 @@
 // the finalisation multiplies by d_u again.  y_{k+1} overwrites y_{k-1} in
 // place: row u is the only reader of y_{k-1}[u].
 //
-// Per-round reductions (the mass view of Sec. 4.1): sum_u T_k[u] and
-// sum_u |T_k[u]|.  Each CTA adds its values into one of kRedSlots FP64 slots
-// (diagnostics only: the slot atomics are not ordered).
+// Layout: vector b of a tile is column b of a row-major [(n+1) x W] array
+// (row n is the padding sentinel, kept at zero).  Column b accumulates while
+// bit b of `active` is set; its per-round sums (the mass view of Sec. 4.1,
+// sum_u T_k[u] and sum_u |T_k[u]|) are reduced when bit b of `reduce` is set.
 //
-// Work split.  See internal.h: block tiles of whole rows, walked by a merge
-// path inside the CTA (every thread gets kItemsPerThread consecutive items of
-// the rows+entries sequence), and chunk tiles of long rows combined by the
-// CTA holding the last ticket.  Each sum runs in a fixed order, so results
-// are the same from run to run.
-#include "internal.h"
+// Work split (internal.h): the first num_hub_tiles CTAs each sum one tile of
+// a hub row; the next num_long_chunks CTAs each take one long SELL chunk
+// (more than kLongChunk entries per row), its entries split over the CTA's
+// warps; every other CTA runs kWarps SELL chunks, one warp per chunk and one
+// lane per row, chunks taken longest first.  Every sum runs in a fixed order
+// (a lane adds its row's entries in CSR order, slices are added in warp
+// order; hub tiles use a fixed tree and the tiles are added in tile order), so
+// a result never depends on scheduling.
+#include <cstring>
+
+#include "device_common.cuh"
 
 namespace cpaa {
 
-template <int P> struct Prec;
-template <> struct Prec<CPAA_F64> {
-    using S = double;  // storage of y
-    using A = double;  // arithmetic
-    using R = double;  // accumulator rho
-    static constexpr bool kKahan = false;
-};
-template <> struct Prec<CPAA_F32> {
-    using S = float;
-    using A = float;
-    using R = float;
-    static constexpr bool kKahan = true;
-};
-template <> struct Prec<CPAA_BF16> {
-    using S = __nv_bfloat16;
-    using A = float;
-    using R = float;
-    static constexpr bool kKahan = true;
-};
-
-__device__ __forceinline__ double load_y(const double *p) { return __ldg(p); }
-__device__ __forceinline__ float load_y(const float *p) { return __ldg(p); }
-__device__ __forceinline__ float load_y(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
-
-__device__ __forceinline__ double to_acc(double v) { return v; }
-__device__ __forceinline__ float to_acc(float v) { return v; }
-__device__ __forceinline__ float to_acc(__nv_bfloat16 v) { return __bfloat162float(v); }
-
-template <class S> __device__ __forceinline__ S to_store(double v);
-template <> __device__ __forceinline__ double to_store<double>(double v) { return v; }
-template <class S> __device__ __forceinline__ S to_store_f(float v);
-template <> __device__ __forceinline__ float to_store_f<float>(float v) { return v; }
-template <> __device__ __forceinline__ __nv_bfloat16 to_store_f<__nv_bfloat16>(float v) {
-    return __float2bfloat16_rn(v);
-}
-__device__ __forceinline__ void store_y(double *p, double v) { *p = v; }
-__device__ __forceinline__ void store_y(float *p, float v) { *p = v; }
-__device__ __forceinline__ void store_y(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
-
-// Streaming 16-byte load of four column indices (read once per round).
-__device__ __forceinline__ int4 load_cols(const int32_t *p) { return __ldcs(reinterpret_cast<const int4 *>(p)); }
-
-template <int P>
+template <int P, int W>
 struct StepParams {
     using S = typename Prec<P>::S;
     using A = typename Prec<P>::A;
     using R = typename Prec<P>::R;
-    const int4 *tiles;
-    const int32_t *row_ptr;
-    const int32_t *col_idx;
+    // hub rows
+    const int4 *hub_tiles;
+    int num_hub_tiles;
+    const int32_t *hub_row_ptr;
+    const int32_t *hub_col;
+    A *long_part;  // [num_hub_tiles][W]
+    int *long_cnt;
+    // SELL chunks
+    const int32_t *sell_col;
+    const int64_t *chunk_off;
+    const int32_t *chunk_len;
+    const int32_t *chunk_order;
+    int num_chunks;
+    int num_long_chunks;  // chunk_order[0, num_long_chunks) take one CTA each
+    int n_hub;
+    int64_t n;
+    // vectors (new order)
     const A *deg;
     const A *inv_deg;
-    const S *y_src;
-    S *y_io;
-    R *rho;
-    R *comp;
-    A *long_part;
-    int *long_cnt;
-    double *red;
-    A ck;
-    int first;
-    int last;
+    const S *y_src;  // [(n+1) x W]
+    S *y_io;         // [(n+1) x W]
+    R *rho;          // [n x W]
+    R *comp;         // [n x W]
+    double *red;     // this round's [2][W][kRedSlots]
+    A ck[W];
+    unsigned active;
+    unsigned reduce;
+    unsigned first;  // columns in their first round (y_1 = D^-1 P y_0... scaled: s / d)
 };
 
-// Row epilogue: recurrence, accumulation, and this row's reduction terms.
-template <int P>
-__device__ __forceinline__ void row_update(const StepParams<P> &p, int u, typename Prec<P>::A s,
-                                           typename Prec<P>::A &sT, typename Prec<P>::A &sA,
-                                           double &sR) {
+// W consecutive values of one row, with the widest loads the row size allows.
+template <class T, int W>
+__device__ __forceinline__ void load_row(const T *p, T (&v)[W], bool stream) {
+    constexpr int B = W * (int)sizeof(T);
+    if constexpr (B % 16 == 0) {
+        uint4 raw[B / 16];
+#pragma unroll
+        for (int i = 0; i < B / 16; ++i)
+            raw[i] = stream ? __ldcs(reinterpret_cast<const uint4 *>(p) + i)
+                            : __ldg(reinterpret_cast<const uint4 *>(p) + i);
+        memcpy(v, raw, B);
+    } else if constexpr (B % 8 == 0) {
+        uint2 raw[B / 8];
+#pragma unroll
+        for (int i = 0; i < B / 8; ++i)
+            raw[i] = stream ? __ldcs(reinterpret_cast<const uint2 *>(p) + i)
+                            : __ldg(reinterpret_cast<const uint2 *>(p) + i);
+        memcpy(v, raw, B);
+    } else if constexpr (B % 4 == 0) {
+        unsigned raw[B / 4];
+#pragma unroll
+        for (int i = 0; i < B / 4; ++i)
+            raw[i] = stream ? __ldcs(reinterpret_cast<const unsigned *>(p) + i)
+                            : __ldg(reinterpret_cast<const unsigned *>(p) + i);
+        memcpy(v, raw, B);
+    } else {
+        unsigned short raw = __ldg(reinterpret_cast<const unsigned short *>(p));
+        memcpy(v, &raw, B);
+    }
+}
+
+template <class T, int W>
+__device__ __forceinline__ void store_row(T *p, const T (&v)[W], bool stream) {
+    constexpr int B = W * (int)sizeof(T);
+    if constexpr (B % 16 == 0) {
+        uint4 raw[B / 16];
+        memcpy(raw, v, B);
+#pragma unroll
+        for (int i = 0; i < B / 16; ++i) {
+            if (stream) __stcs(reinterpret_cast<uint4 *>(p) + i, raw[i]);
+            else reinterpret_cast<uint4 *>(p)[i] = raw[i];
+        }
+    } else if constexpr (B % 8 == 0) {
+        uint2 raw[B / 8];
+        memcpy(raw, v, B);
+#pragma unroll
+        for (int i = 0; i < B / 8; ++i) {
+            if (stream) __stcs(reinterpret_cast<uint2 *>(p) + i, raw[i]);
+            else reinterpret_cast<uint2 *>(p)[i] = raw[i];
+        }
+    } else if constexpr (B % 4 == 0) {
+        unsigned raw[B / 4];
+        memcpy(raw, v, B);
+#pragma unroll
+        for (int i = 0; i < B / 4; ++i) {
+            if (stream) __stcs(reinterpret_cast<unsigned *>(p) + i, raw[i]);
+            else reinterpret_cast<unsigned *>(p)[i] = raw[i];
+        }
+    } else {
+        unsigned short raw;
+        memcpy(&raw, v, B);
+        *reinterpret_cast<unsigned short *>(p) = raw;
+    }
+}
+
+// Gathered neighbour row j: W values in arithmetic precision.
+template <int P, int W>
+__device__ __forceinline__ void gather_row(const typename Prec<P>::S *y, int j,
+                                           typename Prec<P>::A (&x)[W]) {
+    using S = typename Prec<P>::S;
+    S v[W];
+    load_row<S, W>(y + (int64_t)j * W, v, false);
+#pragma unroll
+    for (int b = 0; b < W; ++b) x[b] = to_acc(v[b]);
+}
+
+// A row's own operands: the iterate it overwrites, the accumulator and its
+// compensation.
+template <int P, int W>
+struct RowOps {
+    typename Prec<P>::A y_old[W];
+    typename Prec<P>::R rr[W];
+    typename Prec<P>::R cmp[W];
+};
+
+template <int P, int W>
+__device__ __forceinline__ void load_ops(const StepParams<P, W> &p, int64_t r, RowOps<P, W> &o) {
+    using S = typename Prec<P>::S;
     using A = typename Prec<P>::A;
     using R = typename Prec<P>::R;
-    const A inv = p.inv_deg[u];
-    A y;
-    if (p.first) y = s * inv;
-    else y = (s + s) * inv - to_acc(p.y_io[u]);
-    store_y(p.y_io + u, y);
-    const A yq = to_acc(p.y_io[u]);  // the value later rounds will read
-    R r = p.rho[u];
-    if constexpr (Prec<P>::kKahan) {
-        R cmp = p.comp[u];
-        const R t1 = p.ck * yq - cmp;
-        const R t = r + t1;
-        cmp = (t - r) - t1;
-        r = t;
-        p.comp[u] = cmp;
-    } else {
-        r = r + p.ck * yq;
+    if (p.first == (W == 32 ? 0xffffffffu : ((1u << W) - 1u))) {
+#pragma unroll
+        for (int b = 0; b < W; ++b) o.y_old[b] = A(0);
+    } else {  // columns in their first round ignore the value read here
+        S v[W];
+        load_row<S, W>(p.y_io + r * W, v, true);
+#pragma unroll
+        for (int b = 0; b < W; ++b) o.y_old[b] = to_acc(v[b]);
     }
-    p.rho[u] = r;
-    const A d = p.deg[u];
-    const A T = yq * d;
-    sT += T;
-    sA += (T < A(0) ? -T : T);
-    if (p.last) sR += (double)r * (double)d;
-}
-
-// Reduce three per-thread values over the CTA and add them to this round's
-// slots.  Deterministic within the CTA; the slot atomics are not ordered.
-__device__ __forceinline__ void cta_reduce_add(double a, double b, double c, double *red) {
-    __shared__ double s_red[kThreads / 32][3];
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-        c += __shfl_xor_sync(0xffffffffu, c, o);
-    }
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) { s_red[w][0] = a; s_red[w][1] = b; s_red[w][2] = c; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double x = 0, y = 0, z = 0;
-        for (int i = 0; i < kThreads / 32; ++i) { x += s_red[i][0]; y += s_red[i][1]; z += s_red[i][2]; }
-        const int slot = blockIdx.x % kRedSlots;
-        atomicAdd(red + 0 * kRedSlots + slot, x);
-        atomicAdd(red + 1 * kRedSlots + slot, y);
-        atomicAdd(red + 2 * kRedSlots + slot, z);
+    load_row<R, W>(p.rho + r * W, o.rr, true);
+    if constexpr (Prec<P>::kKahan) load_row<R, W>(p.comp + r * W, o.cmp, true);
+    else {
+#pragma unroll
+        for (int b = 0; b < W; ++b) o.cmp[b] = R(0);
     }
 }
 
-template <int P>
-__global__ void __launch_bounds__(kThreads) cheb_step_kernel(const StepParams<P> p) {
+// Row epilogue: new iterates, accumulation, reduction terms.
+template <int P, int W>
+__device__ __forceinline__ void row_finish(const StepParams<P, W> &p, int64_t r,
+                                           const typename Prec<P>::A (&s)[W],
+                                           typename Prec<P>::A inv, typename Prec<P>::A d,
+                                           RowOps<P, W> &o, typename Prec<P>::A (&sT)[W],
+                                           typename Prec<P>::A (&sA)[W]) {
+    using S = typename Prec<P>::S;
     using A = typename Prec<P>::A;
-    __shared__ int s_end[kMaxTileRows + 1];      // row ends, relative to the tile's first entry
-    __shared__ A s_val[kTileItems];              // gathered y values of the tile's entries
-    __shared__ A s_sum[kMaxTileRows + 1];        // row sums
-    __shared__ int s_crow[kThreads];             // carry row of each thread
-    __shared__ A s_cval[kThreads];               // carry partial of each thread
-    __shared__ int s_last;
+    using R = typename Prec<P>::R;
+    S ys[W];
+#pragma unroll
+    for (int b = 0; b < W; ++b) {
+        const A y = new_iterate<P>(s[b], inv, o.y_old[b], (p.first >> b) & 1u);
+        store_y(&ys[b], y);
+        if (p.active >> b & 1u) accumulate<P>(o.rr[b], o.cmp[b], p.ck[b], y);
+        const A T = y * d;
+        sT[b] += T;
+        sA[b] += (T < A(0) ? -T : T);
+    }
+    store_row<S, W>(p.y_io + r * W, ys, false);
+    store_row<R, W>(p.rho + r * W, o.rr, true);
+    if constexpr (Prec<P>::kKahan) store_row<R, W>(p.comp + r * W, o.cmp, true);
+}
 
-    const int tid = threadIdx.x;
-    const int4 t = p.tiles[blockIdx.x];
-    A sT = 0, sA = 0;
-    double sR = 0;
-
-    if (t.w > 0) {
-        // ---- chunk of a long row ------------------------------------------
-        const int u = t.x, j = t.y, slot = t.z, lid = t.w - 1;
-        const int e0 = p.row_ptr[u], e1 = p.row_ptr[u + 1];
-        const int nch = (e1 - e0 + kTileItems - 1) / kTileItems;
-        const int c0 = e0 + j * kTileItems;
-        const int c1 = min(c0 + kTileItems, e1);
-        const int a0 = c0 & ~3;
-        const int nvec = (c1 - a0 + 3) >> 2;
-        A acc = 0;
-        for (int v = tid; v < nvec; v += kThreads) {
-            const int e = a0 + 4 * v;
-            const int4 q = load_cols(p.col_idx + e);
-            if (e >= c0 && e < c1) acc += load_y(p.y_src + q.x);
-            if (e + 1 >= c0 && e + 1 < c1) acc += load_y(p.y_src + q.y);
-            if (e + 2 >= c0 && e + 2 < c1) acc += load_y(p.y_src + q.z);
-            if (e + 3 >= c0 && e + 3 < c1) acc += load_y(p.y_src + q.w);
+// Sum per-thread values of the columns in `reduce` over the CTA and add them
+// to this round's slots.
+template <class A, int W>
+__device__ __forceinline__ void cta_reduce_add(const A (&sT)[W], const A (&sA)[W], unsigned reduce,
+                                               double *red) {
+    __shared__ double s_red[kWarps][2];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+    for (int b = 0; b < W; ++b) {
+        if (!(reduce >> b & 1u)) continue;  // uniform over the CTA
+        double a = (double)sT[b], c = (double)sA[b];
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            c += __shfl_xor_sync(0xffffffffu, c, o);
         }
-        // fixed-shape CTA sum
-        s_cval[tid] = acc;
+        if (l == 0) { s_red[w][0] = a; s_red[w][1] = c; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double x = 0, y = 0;
+            for (int i = 0; i < kWarps; ++i) { x += s_red[i][0]; y += s_red[i][1]; }
+            const int slot = blockIdx.x % kRedSlots;
+            atomicAdd(red + (0 * W + b) * kRedSlots + slot, x);
+            atomicAdd(red + (1 * W + b) * kRedSlots + slot, y);
+        }
+        __syncthreads();
+    }
+}
+
+template <int P, int W>
+__device__ __forceinline__ void hub_tile(const StepParams<P, W> &p, int4 t) {
+    using A = typename Prec<P>::A;
+    __shared__ A s_v[W][kThreads];
+    __shared__ int s_last;
+    const int tid = threadIdx.x;
+    const int h = t.x, j = t.y, slot = t.z, hub = t.w - 1;
+    const int e0 = p.hub_row_ptr[h], e1 = p.hub_row_ptr[h + 1];
+    const int nt = (e1 - e0 + kHubTileEntries - 1) / kHubTileEntries;
+    const int c0 = e0 + j * kHubTileEntries;
+    const int c1 = min(c0 + kHubTileEntries, e1);
+    const int a0 = c0 & ~3;
+    const int nvec = (c1 - a0 + 3) >> 2;
+    A acc[W];
+#pragma unroll
+    for (int b = 0; b < W; ++b) acc[b] = A(0);
+#pragma unroll 2
+    for (int v = tid; v < nvec; v += kThreads) {
+        const int e = a0 + 4 * v;
+        const int4 q = ld_stream4(p.hub_col + e);
+        A x0[W], x1[W], x2[W], x3[W];
+        // entries outside [c0, c1) gather the sentinel row n, which holds zeros
+        gather_row<P, W>(p.y_src, (e >= c0 && e < c1) ? q.x : (int)p.n, x0);
+        gather_row<P, W>(p.y_src, (e + 1 >= c0 && e + 1 < c1) ? q.y : (int)p.n, x1);
+        gather_row<P, W>(p.y_src, (e + 2 >= c0 && e + 2 < c1) ? q.z : (int)p.n, x2);
+        gather_row<P, W>(p.y_src, (e + 3 >= c0 && e + 3 < c1) ? q.w : (int)p.n, x3);
+#pragma unroll
+        for (int b = 0; b < W; ++b) acc[b] += ((x0[b] + x1[b]) + (x2[b] + x3[b]));
+    }
+#pragma unroll
+    for (int b = 0; b < W; ++b) s_v[b][tid] = acc[b];
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (tid < o)
+#pragma unroll
+            for (int b = 0; b < W; ++b) s_v[b][tid] = s_v[b][tid] + s_v[b][tid + o];
+        __syncthreads();
+    }
+    if (tid == 0) {
+#pragma unroll
+        for (int b = 0; b < W; ++b) p.long_part[(int64_t)(slot + j) * W + b] = s_v[b][0];
+        __threadfence();
+        const int ticket = atomicAdd(p.long_cnt + hub, 1);
+        s_last = (ticket == nt - 1);
+    }
+    __syncthreads();
+    A sT[W], sA[W];
+#pragma unroll
+    for (int b = 0; b < W; ++b) sT[b] = sA[b] = A(0);
+    if (s_last) {
+        __threadfence();
+        // every tile partial is visible: add them in tile order, fixed shape
+        A part[W];
+#pragma unroll
+        for (int b = 0; b < W; ++b) part[b] = A(0);
+        for (int c = tid; c < nt; c += kThreads)
+#pragma unroll
+            for (int b = 0; b < W; ++b) part[b] += __ldcg(p.long_part + (int64_t)(slot + c) * W + b);
+        __syncthreads();
+#pragma unroll
+        for (int b = 0; b < W; ++b) s_v[b][tid] = part[b];
         __syncthreads();
         for (int o = kThreads / 2; o > 0; o >>= 1) {
-            if (tid < o) s_cval[tid] = s_cval[tid] + s_cval[tid + o];
+            if (tid < o)
+#pragma unroll
+                for (int b = 0; b < W; ++b) s_v[b][tid] = s_v[b][tid] + s_v[b][tid + o];
             __syncthreads();
         }
         if (tid == 0) {
-            p.long_part[slot + j] = s_cval[0];
-            __threadfence();
-            const int ticket = atomicAdd(p.long_cnt + lid, 1);
-            s_last = (ticket == nch - 1);
-        }
-        __syncthreads();
-        if (s_last) {
-            __threadfence();
-            // every chunk partial is visible: add them in chunk order, in a
-            // fixed shape (thread i takes chunks i, i+256, ...)
-            A part = 0;
-            for (int c = tid; c < nch; c += kThreads) part += __ldcg(p.long_part + slot + c);
-            __syncthreads();
-            s_cval[tid] = part;
-            __syncthreads();
-            for (int o = kThreads / 2; o > 0; o >>= 1) {
-                if (tid < o) s_cval[tid] = s_cval[tid] + s_cval[tid + o];
-                __syncthreads();
-            }
-            if (tid == 0) {
-                row_update<P>(p, u, s_cval[0], sT, sA, sR);
-                p.long_cnt[lid] = 0;  // ready for the next round
-            }
-            cta_reduce_add((double)sT, (double)sA, sR, p.red);
-        }
-        return;
-    }
-
-    // ---- block tile of whole rows -------------------------------------------
-    const int r0 = t.x, r1 = t.y;
-    const int nrows = r1 - r0;
-    const int e0 = p.row_ptr[r0], e1 = p.row_ptr[r1];
-    const int nnz = e1 - e0;
-    for (int i = tid; i < nrows; i += kThreads) s_end[i] = p.row_ptr[r0 + 1 + i] - e0;
-    {
-        const int a0 = e0 & ~3;
-        const int nvec = (e1 - a0 + 3) >> 2;
-#pragma unroll 2
-        for (int v = tid; v < nvec; v += kThreads) {
-            const int e = a0 + 4 * v;
-            const int4 q = load_cols(p.col_idx + e);
-            const int k = e - e0;
-            if (k >= 0 && k < nnz) s_val[k] = load_y(p.y_src + q.x);
-            if (k + 1 >= 0 && k + 1 < nnz) s_val[k + 1] = load_y(p.y_src + q.y);
-            if (k + 2 >= 0 && k + 2 < nnz) s_val[k + 2] = load_y(p.y_src + q.z);
-            if (k + 3 >= 0 && k + 3 < nnz) s_val[k + 3] = load_y(p.y_src + q.w);
+            A s[W];
+#pragma unroll
+            for (int b = 0; b < W; ++b) s[b] = s_v[b][0];
+            RowOps<P, W> o;
+            load_ops<P, W>(p, h, o);
+            row_finish<P, W>(p, h, s, p.inv_deg[h], p.deg[h], o, sT, sA);
+            p.long_cnt[hub] = 0;  // ready for the next round
         }
     }
-    __syncthreads();
-
-    // merge path over (row ends, entries): thread tid owns diagonals [d0, d1)
-    const int items = nrows + nnz;
-    const int d0 = min(tid * kItemsPerThread, items);
-    const int d1 = min(d0 + kItemsPerThread, items);
-    int lo = max(d0 - nnz, 0), hi = min(d0, nrows);
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (s_end[mid] <= d0 - mid - 1) lo = mid + 1; else hi = mid;
-    }
-    int row = lo, k = d0 - lo;
-    int first_emit = -1;
-    A acc = 0;
-    for (int d = d0; d < d1; ++d) {
-        if (k < s_end[row]) {
-            acc += s_val[k];
-            ++k;
-        } else {
-            s_sum[row] = acc;
-            if (first_emit < 0) first_emit = row;
-            acc = 0;
-            ++row;
-        }
-    }
-    s_crow[tid] = (d0 < d1) ? row : -1;
-    s_cval[tid] = acc;
-    __syncthreads();
-    if (first_emit >= 0) {
-        // the row this thread closed first may have started in earlier threads
-        int j = tid - 1;
-        while (j >= 0 && s_crow[j] == first_emit) --j;
-        A pre = 0;
-        for (int i = j + 1; i < tid; ++i) pre += s_cval[i];
-        s_sum[first_emit] = pre + s_sum[first_emit];
-    }
-    __syncthreads();
-    for (int i = tid; i < nrows; i += kThreads) row_update<P>(p, r0 + i, s_sum[i], sT, sA, sR);
-    cta_reduce_add((double)sT, (double)sA, sR, p.red);
+    cta_reduce_add<A, W>(sT, sA, p.reduce, p.red);
 }
 
-template <int P>
+template <int W> struct Unroll { static constexpr int value = W >= 8 ? 1 : 8 / W; };
+
+// Sum of entries [i0, i1) of the lane's row in chunk `col` (SELL layout).
+template <int P, int W>
+__device__ __forceinline__ void chunk_sum(const StepParams<P, W> &p, const int32_t *col, int i0, int i1,
+                                          typename Prec<P>::A (&acc)[W]) {
+    using A = typename Prec<P>::A;
+    constexpr int U = Unroll<W>::value;
+#pragma unroll
+    for (int b = 0; b < W; ++b) acc[b] = A(0);
+    int i = i0;
+    for (; i + U <= i1; i += U) {
+        int jj[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) jj[k] = ld_stream(col + (int64_t)(i + k) * kChunkRows);
+        A x[U][W];
+#pragma unroll
+        for (int k = 0; k < U; ++k) gather_row<P, W>(p.y_src, jj[k], x[k]);
+#pragma unroll
+        for (int k = 0; k < U; ++k)
+#pragma unroll
+            for (int b = 0; b < W; ++b) acc[b] += x[k][b];
+    }
+    for (; i < i1; ++i) {
+        A x[W];
+        gather_row<P, W>(p.y_src, ld_stream(col + (int64_t)i * kChunkRows), x);
+#pragma unroll
+        for (int b = 0; b < W; ++b) acc[b] += x[b];
+    }
+}
+
+// A long chunk: warp w sums slice w of the entries of all 32 rows; the slices
+// are added in warp order and warp 0 finishes the rows.
+template <int P, int W>
+__device__ __forceinline__ void long_chunk(const StepParams<P, W> &p, int c) {
+    using A = typename Prec<P>::A;
+    __shared__ A s_part[kWarps][W][kChunkRows];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t off = p.chunk_off[c];
+    const int len = p.chunk_len[c];
+    const int per = (len + kWarps - 1) / kWarps;
+    const int i0 = min(len, warp * per), i1 = min(len, i0 + per);
+    A acc[W];
+    chunk_sum<P, W>(p, p.sell_col + off + lane, i0, i1, acc);
+#pragma unroll
+    for (int b = 0; b < W; ++b) s_part[warp][b][lane] = acc[b];
+    __syncthreads();
+    A sT[W], sA[W];
+#pragma unroll
+    for (int b = 0; b < W; ++b) sT[b] = sA[b] = A(0);
+    if (warp == 0) {
+        const int64_t r = p.n_hub + (int64_t)c * kChunkRows + lane;
+        A s[W];
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            s[b] = s_part[0][b][lane];
+            for (int q = 1; q < kWarps; ++q) s[b] += s_part[q][b][lane];
+        }
+        if (r < p.n) {
+            RowOps<P, W> o;
+            load_ops<P, W>(p, r, o);
+            row_finish<P, W>(p, r, s, ld_once(p.inv_deg + r), ld_once(p.deg + r), o, sT, sA);
+        }
+    }
+    cta_reduce_add<A, W>(sT, sA, p.reduce, p.red);
+}
+
+template <int P, int W>
+__global__ void __launch_bounds__(kThreads) cheb_step_kernel(const StepParams<P, W> p) {
+    using A = typename Prec<P>::A;
+    if ((int)blockIdx.x < p.num_hub_tiles) {
+        hub_tile<P, W>(p, p.hub_tiles[blockIdx.x]);
+        return;
+    }
+    const int b0 = (int)blockIdx.x - p.num_hub_tiles;
+    if (b0 < p.num_long_chunks) {
+        long_chunk<P, W>(p, p.chunk_order[b0]);
+        return;
+    }
+    const int lane = threadIdx.x & 31;
+    const int idx = p.num_long_chunks + (b0 - p.num_long_chunks) * kWarps + (threadIdx.x >> 5);
+    A sT[W], sA[W];
+#pragma unroll
+    for (int b = 0; b < W; ++b) sT[b] = sA[b] = A(0);
+    if (idx < p.num_chunks) {
+        const int c = p.chunk_order[idx];
+        const int64_t off = p.chunk_off[c];
+        const int len = p.chunk_len[c];
+        const int64_t r = p.n_hub + (int64_t)c * kChunkRows + lane;
+        const bool live = r < p.n;
+        // for narrow tiles the row's own operands are fetched before the gather
+        // so that their latency overlaps it
+        constexpr bool kEarly = W <= 4;
+        A inv = 0, d = 0;
+        RowOps<P, W> o;
+        if (live) {
+            inv = ld_once(p.inv_deg + r);
+            d = ld_once(p.deg + r);
+            if constexpr (kEarly) load_ops<P, W>(p, r, o);
+        }
+        A acc[W];
+        chunk_sum<P, W>(p, p.sell_col + off + lane, 0, len, acc);
+        if (live) {
+            if constexpr (!kEarly) load_ops<P, W>(p, r, o);
+            row_finish<P, W>(p, r, acc, inv, d, o, sT, sA);
+        }
+    }
+    cta_reduce_add<A, W>(sT, sA, p.reduce, p.red);
+}
+
+template <int P, int W>
 static cudaError_t launch_typed(const StepLaunch &s) {
     using A = typename Prec<P>::A;
     using S = typename Prec<P>::S;
     using R = typename Prec<P>::R;
     const cpaa_graph *g = s.g;
-    StepParams<P> p;
-    p.tiles = g->tiles;
-    p.row_ptr = g->row_ptr;
-    p.col_idx = g->col_idx;
+    StepParams<P, W> p;
+    p.hub_tiles = g->hub_tiles;
+    p.num_hub_tiles = g->num_hub_tiles;
+    p.hub_row_ptr = g->hub_row_ptr;
+    p.hub_col = g->hub_col;
+    p.long_part = reinterpret_cast<A *>(s.long_part);
+    p.long_cnt = s.long_cnt ? s.long_cnt : g->long_cnt;
+    p.sell_col = g->sell_col;
+    p.chunk_off = g->chunk_off;
+    p.chunk_len = g->chunk_len;
+    p.chunk_order = g->chunk_order;
+    p.num_chunks = g->num_chunks;
+    p.num_long_chunks = g->num_long_chunks;
+    p.n_hub = g->n_hub;
+    p.n = g->n;
     if constexpr (P == CPAA_F64) {
         p.deg = g->deg64;
         p.inv_deg = g->inv_deg64;
@@ -293,21 +451,34 @@ static cudaError_t launch_typed(const StepLaunch &s) {
     p.y_io = static_cast<S *>(s.y_io);
     p.rho = static_cast<R *>(s.rho);
     p.comp = static_cast<R *>(s.comp);
-    p.long_part = reinterpret_cast<A *>(g->long_part);
-    p.long_cnt = g->long_cnt;
     p.red = s.red;
-    p.ck = (A)s.ck;
+    for (int b = 0; b < W; ++b) p.ck[b] = (A)s.ck[b];
+    p.active = s.active;
+    p.reduce = s.reduce;
     p.first = s.first;
-    p.last = s.last;
-    cheb_step_kernel<P><<<g->num_tiles, kThreads, 0, s.stream>>>(p);
+    const int grid = g->num_hub_tiles + g->num_long_chunks +
+                     (g->num_chunks - g->num_long_chunks + kWarps - 1) / kWarps;
+    cheb_step_kernel<P, W><<<grid, kThreads, 0, s.stream>>>(p);
     return cudaGetLastError();
+}
+
+template <int P>
+static cudaError_t launch_w(const StepLaunch &s) {
+    switch (s.width) {
+        case 1: return launch_typed<P, 1>(s);
+        case 2: return launch_typed<P, 2>(s);
+        case 4: return launch_typed<P, 4>(s);
+        case 8: return launch_typed<P, 8>(s);
+        case 16: return launch_typed<P, 16>(s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_step(const StepLaunch &s) {
     switch (s.precision) {
-        case CPAA_F64: return launch_typed<CPAA_F64>(s);
-        case CPAA_F32: return launch_typed<CPAA_F32>(s);
-        case CPAA_BF16: return launch_typed<CPAA_BF16>(s);
+        case CPAA_F64: return launch_w<CPAA_F64>(s);
+        case CPAA_F32: return launch_w<CPAA_F32>(s);
+        case CPAA_BF16: return launch_w<CPAA_BF16>(s);
     }
     return cudaErrorInvalidValue;
 }

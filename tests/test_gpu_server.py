@@ -1,0 +1,144 @@
+"""The continuous-batching server: results against the oracle, bit-identical
+alone and in a mix, cancellation, timeouts, admission by memory budget."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import cpaa_inputs as ci
+from oracle import oracle as O
+from tests.gpu_util import upload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2112_01743_gb300 as pkg
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def served(pkg):
+    graphs = [ci.chung_lu(5000, 40000, seed=31), ci.chung_lu(60000, 600000, seed=32),
+              ci.grid_deleted(100, 120, 0.2, seed=3)]
+    G = [upload(pkg, g) for g in graphs]
+    S = pkg.Server(4 << 30)
+    ids = [S.add_graph(x, 8) for x in G]
+    yield pkg, graphs, G, S, ids
+    S.close()
+    for x in G:
+        x.close()
+
+
+def _queries(graphs, count, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        gi = int(rng.integers(len(graphs)))
+        n = graphs[gi].n
+        k = int(rng.integers(1, 17))
+        seeds = rng.choice(n, size=k, replace=False).astype(np.int32)
+        c = float(rng.choice([0.5, 0.85, 0.95]))
+        out.append((gi, seeds, None, c, 1e-6))
+    return out
+
+
+def test_alone_equals_in_mix_and_matches_oracle(served):
+    pkg, graphs, G, S, ids = served
+    gi = 1
+    n = graphs[gi].n
+    q = (ids[gi], np.array([5, 123, 40000], dtype=np.int32), None, 0.85, 1e-6)
+    alone = np.empty(n)
+    st, info = S.wait(S.submit(*q), alone, timeout_us=120_000_000)
+    assert st == pkg.CPAA_OK
+    # the same query submitted in the middle of a stream of others
+    mix = _queries(graphs, 80, seed=5)
+    tickets, tq = [], None
+    for i, (g2, seeds, w, c, tol) in enumerate(mix):
+        tickets.append((g2, seeds, c, S.submit(ids[g2], seeds, w, c, tol)))
+        if i == 40:
+            tq = S.submit(*q)
+    in_mix = np.empty(n)
+    st2, info2 = S.wait(tq, in_mix, timeout_us=120_000_000)
+    assert st2 == pkg.CPAA_OK and info2.rounds == info.rounds
+    assert np.array_equal(alone, in_mix)
+    rp, cx = graphs[gi].numpy()
+    p = np.zeros(n)
+    p[q[1]] = 1.0 / 3
+    ref = O.cpaa(rp, cx, p, 0.85, info.rounds)
+    assert np.abs(alone - ref).sum() / np.abs(ref).sum() <= 1e-6
+    # every query of the mix against the oracle (FP32 serving: relative L1 <= 1e-6)
+    out = {}
+    for g2, seeds, c, t in tickets:
+        pi = np.empty(graphs[g2].n)
+        st, inf = S.wait(t, pi, timeout_us=120_000_000)
+        assert st == pkg.CPAA_OK
+        out[t] = (g2, seeds, c, pi, inf.rounds)
+    for t in list(out)[::8]:
+        g2, seeds, c, pi, M = out[t]
+        rp, cx = graphs[g2].numpy()
+        p = np.zeros(graphs[g2].n)
+        p[seeds] = 1.0 / len(seeds)
+        ref = O.cpaa(rp, cx, p, c, M)
+        assert np.abs(pi - ref).sum() / np.abs(ref).sum() <= 1e-6
+        assert abs(pi.sum() - 1.0) < 1e-9
+    s = S.stats()
+    assert s["completed"] >= 82 and s["failed"] == 0
+    assert s["p99_us"] >= s["p50_us"] > 0
+
+
+def test_cancel_and_timeout(pkg):
+    g = ci.chung_lu(200000, 2000000, seed=41)
+    G = upload(pkg, g)
+    S = pkg.Server(1 << 30)
+    gid = S.add_graph(G, 1)  # one slot: later queries must queue
+    tickets = [S.submit(gid, np.array([i * 7 + 1], dtype=np.int32), None, 0.95, 1e-8) for i in range(12)]
+    last = tickets[-1]
+    st, _ = S.wait(last, None, timeout_us=0)
+    assert st == pkg.CPAA_ETIMEOUT
+    assert S.cancel(last) == pkg.CPAA_OK
+    st, _ = S.wait(last, None, timeout_us=120_000_000)
+    assert st == pkg.CPAA_ECANCELLED
+    with pytest.raises(pkg.CpaaError) as e:
+        S.wait(last, None, timeout_us=0)
+    assert e.value.status == pkg.CPAA_ENOTFOUND
+    for t in tickets[:-1]:
+        st, info = S.wait(t, None, timeout_us=120_000_000)
+        assert st == pkg.CPAA_OK
+    assert S.stats()["cancelled"] == 1
+    S.close()
+    G.close()
+
+
+def test_invalid_submissions(served):
+    pkg, graphs, G, S, ids = served
+    n = graphs[0].n
+    bad = [
+        (ids[0], np.array([n], dtype=np.int32), None, 0.85, 1e-6),          # out of range
+        (ids[0], np.array([3, 3], dtype=np.int32), None, 0.85, 1e-6),       # duplicate seed
+        (ids[0], np.array([3, 4], dtype=np.int32), np.array([0.5, 0.6]), 0.85, 1e-6),
+        (ids[0], np.array([3], dtype=np.int32), None, 1.0, 1e-6),
+        (ids[0], np.array([3], dtype=np.int32), None, 0.85, 0.0),
+        (ids[0], np.arange(65, dtype=np.int32), None, 0.85, 1e-6),          # too many seeds
+    ]
+    for q in bad:
+        with pytest.raises(pkg.CpaaError) as e:
+            S.submit(*q)
+        assert e.value.status == pkg.CPAA_EINVAL
+    with pytest.raises(pkg.CpaaError) as e:
+        S.submit(99, np.array([1], dtype=np.int32), None, 0.85, 1e-6)
+    assert e.value.status == pkg.CPAA_ENOTFOUND
+
+
+def test_admission_needs_memory(pkg):
+    g = ci.chung_lu(100000, 800000, seed=42)
+    G = upload(pkg, g)
+    S = pkg.Server(1 << 20)  # 1 MiB: not even one slot
+    with pytest.raises(pkg.CpaaError) as e:
+        S.add_graph(G, 4)
+    assert e.value.status == pkg.CPAA_ENOMEM
+    S.close()
+    G.close()
