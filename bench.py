@@ -272,6 +272,73 @@ def run_batch(pkg, args, stream):
             "l1_batched_f32_vs_single_f64_last_sample": l1}
 
 
+def run_small(pkg, args, stream):
+    """The 10,000-vertex Chung-Lu graph in FP64, uniform p, run until Eq. 41's
+    ERR_M < 1e-10 (39 rounds at c = 0.85): it fits in L2, so this is a latency
+    figure (time per solve and per round), not a bandwidth one."""
+    import torch
+    import cpaa_inputs as ci
+    g = ci.chung_lu(10_000, 100_000, seed=0, device="cuda")
+    G = pkg.Graph(g.row_ptr, g.col_idx, n=g.n)
+    n, nnz = g.n, g.nnz
+    p = torch.full((n,), 1.0 / n, dtype=torch.float64, device="cuda")
+    pi = torch.empty_like(p)
+    M = 39
+    for _ in range(5):
+        G.solve(p, 0.85, 0.0, pi, fixed_rounds=M, precision=pkg.CPAA_F64)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    e0.record(stream)
+    infos = [G.solve(p, 0.85, 0.0, pi, fixed_rounds=M, precision=pkg.CPAA_F64, time_rounds=True)
+             for _ in range(reps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    G.close()
+    return {"workload": "Chung-Lu n=10000, 1e5 pair draws, gamma 2.1, seed 0, + ring; FP64; c=0.85; "
+                        "uniform p; 39 rounds (ERR_M < 1e-10)", "n": n, "nnz": nnz, "rounds": M,
+            "ms_per_solve": ms, "us_per_round": 1e3 * sum(i.rounds_ms for i in infos) / (M * reps),
+            "gteps": nnz * M / (ms * 1e-3) / 1e9}
+
+
+def run_grid(pkg, args, stream):
+    """Precision study on the 4096 x 4096 lattice with 20% of its edges deleted
+    (spanning tree kept), c = 0.85, uniform p, tol 1e-6: FP64, FP32 and BF16
+    storage, each timed and compared with the FP64 result."""
+    import torch
+    import cpaa_inputs as ci
+    g = ci.grid_deleted(4096, 4096, 0.2, seed=0, device="cuda")
+    n, nnz = g.n, g.nnz
+    G = pkg.Graph(g.row_ptr, g.col_idx, n=n)
+    del g
+    p = torch.full((n,), 1.0 / n, dtype=torch.float64, device="cuda")
+    out = {}
+    res = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for name, prec in (("f64", pkg.CPAA_F64), ("f32", pkg.CPAA_F32), ("bf16", pkg.CPAA_BF16)):
+        pi = torch.empty_like(p)
+        for _ in range(3):
+            G.solve(p, 0.85, 1e-6, pi, precision=prec)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        infos = [G.solve(p, 0.85, 1e-6, pi, precision=prec, time_rounds=True) for _ in range(args.steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        rms = sum(i.rounds_ms for i in infos) / sum(i.rounds for i in infos)
+        res[name] = pi
+        out[name] = {"ms_per_solve": ms, "rounds": infos[0].rounds, "round_ms": rms,
+                     "gteps": nnz * infos[0].rounds / (ms * 1e-3) / 1e9,
+                     "hbm_frac_of_measured": alg_bytes_per_round(n, nnz, name) / (rms * 1e-3) / 1e9
+                     / measured_peak_gbs()[0]}
+    for name in ("f32", "bf16"):
+        out[name]["l1_vs_f64"] = float((res[name] - res["f64"]).abs().sum().item())
+    G.close()
+    return {"workload": "4096x4096 lattice, 20% of edges deleted (seed 0, spanning tree kept); "
+                        "c=0.85, uniform p, tol 1e-6", "n": n, "nnz": nnz, **out}
+
+
 def run_serving(pkg, args):
     """Continuous-batching server over 8 resident Chung-Lu graphs (10k..8M
     vertices, mean degree 16).  Queries: a uniform graph, 1-16 distinct uniform
@@ -426,12 +493,15 @@ def run_ours(args):
         return G.solve(p, wl["c"], wl["tol"], pi, precision=PREC[precision],
                        time_rounds=time_rounds)
 
-    # ---- main timed region (device-resident inputs)
+    # ---- main timed region (device-resident inputs).  The clock sampler starts
+    # before the warm-up so that its own start-up is not inside the timed region.
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(1.0)
     for _ in range(max(args.warmup, 3)):
         solve(prec)
     torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
+    clocks.lines.clear()  # keep only the samples taken during the timed region
     barrier(world)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -504,6 +574,20 @@ def run_ours(args):
         batch = run_batch(pkg, args, stream)
         G = None
 
+    # ---- the 10k-vertex FP64 configuration (latency)
+    small = None
+    if not args.skip_grid:
+        small = run_small(pkg, args, stream)
+
+    # ---- precision study on the lattice
+    grid = None
+    if not args.skip_grid:
+        if G is not None:
+            del G
+            G = None
+        torch.cuda.empty_cache()
+        grid = run_grid(pkg, args, stream)
+
     # ---- serving: continuous batching over 8 resident graphs
     serving = None
     if not args.skip_serve:
@@ -548,6 +632,8 @@ def run_ours(args):
         "gpu_launches": sum(i.rounds + 6 for i in infos),
         "f64": f64,
         "batch": batch,
+        "small": small,
+        "grid": grid,
         "serving": serving,
     }
     print(json.dumps(line), flush=True)
@@ -567,6 +653,7 @@ def main(argv=None):
     ap.add_argument("--skip-f64", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-serve", action="store_true")
+    ap.add_argument("--skip-grid", action="store_true")
     ap.add_argument("--serve-queries", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)

@@ -88,6 +88,7 @@ extern "C" cpaa_status cpaa_solve_batch(cpaa_graph *g, int B, const double *P, c
 
     cpaa_status s;
     Workspace &w = g->ws;
+    if ((s = ensure_reduction_buffers(g)) != CPAA_OK) return s;
     // device staging: host P and PI, plus 3 statistics per column
     const size_t need = sizeof(double) * ((host_io ? 2 * (size_t)n * B : 0) + 3 * (size_t)B);
     if (w.io_bytes < need) {

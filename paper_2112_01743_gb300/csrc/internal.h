@@ -43,7 +43,7 @@ constexpr int kSortWindow = 1024;
 constexpr int kHubDegree = 2048;
 constexpr int kHubTileEntries = 2048;
 constexpr int kLongChunk = 64;  // SELL chunks longer than this get a whole CTA
-constexpr int kRedSlots = 64;  // atomic slots per reduced scalar and round
+constexpr int kRedSlots = 256;  // atomic slots per reduced scalar and round
 constexpr int kRedQ = 2;       // reduced scalars per round: sum T, sum |T|
 constexpr int kDefaultMaxRounds = 2000;
 
@@ -157,6 +157,7 @@ cudaError_t launch_step(const StepLaunch &s);
 
 // Solve pieces (solve.cu), shared by cpaa_solve and cpaa_solve_batch.
 int stats_blocks(int64_t n);
+cpaa_status ensure_reduction_buffers(cpaa_graph *g);
 cpaa_status ensure_workspace(cpaa_graph *g, int prec, int width, int max_rounds);
 cudaError_t launch_stats(cpaa_graph *g, const double *p, double *out, cudaStream_t st);
 cpaa_status check_stats(const double *s, int64_t nnz, double *kappa);

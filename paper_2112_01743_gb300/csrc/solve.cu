@@ -139,6 +139,20 @@ static size_t store_bytes(int prec) { return prec == CPAA_F64 ? 8 : prec == CPAA
 
 int stats_blocks(int64_t n) { return (int)std::min<int64_t>((n + kThreads - 1) / kThreads, kPrepBlocks); }
 
+// The small buffers of the fixed-order reductions (needed before any stats pass).
+cpaa_status ensure_reduction_buffers(cpaa_graph *g) {
+    Workspace &w = g->ws;
+    cpaa_status st;
+    if (!w.part) {
+        if ((st = dev_alloc(g, (void **)&w.part, sizeof(double) * kMaxWidth * kPrepBlocks * 3)) != CPAA_OK) return st;
+    }
+    if (!w.sums) {
+        if ((st = dev_alloc(g, (void **)&w.sums, sizeof(double) * 4 * kMaxWidth)) != CPAA_OK) return st;
+    }
+    if (!w.h_sums) CPAA_CUDA(cudaMallocHost((void **)&w.h_sums, sizeof(double) * 4 * kMaxWidth));
+    return CPAA_OK;
+}
+
 cpaa_status ensure_workspace(cpaa_graph *g, int prec, int width, int max_rounds) {
     Workspace &w = g->ws;
     const int64_t n = g->n;
@@ -175,17 +189,13 @@ cpaa_status ensure_workspace(cpaa_graph *g, int prec, int width, int max_rounds)
         if ((st = dev_alloc(g, &w.long_part, lp)) != CPAA_OK) return st;
         w.long_part_bytes = lp;
     }
-    if (!w.part) {
-        if ((st = dev_alloc(g, (void **)&w.part, sizeof(double) * kMaxWidth * kPrepBlocks * 3)) != CPAA_OK) return st;
-        if ((st = dev_alloc(g, (void **)&w.sums, sizeof(double) * 4 * kMaxWidth)) != CPAA_OK) return st;
-        CPAA_CUDA(cudaMallocHost((void **)&w.h_sums, sizeof(double) * 4 * kMaxWidth));
-    }
-    return CPAA_OK;
+    return ensure_reduction_buffers(g);
 }
 
 // sum p, sum p^2/d and #invalid of one device vector into out[0..2] (device),
 // in the same order for every caller.
 cudaError_t launch_stats(cpaa_graph *g, const double *p, double *out, cudaStream_t st) {
+    if (!g->ws.part) return cudaErrorInvalidValue;  // ensure_reduction_buffers first
     const int blocks = stats_blocks(g->n);
     stats_kernel<<<blocks, kThreads, 0, st>>>(p, g->perm, g->n, g->inv_deg64, g->ws.part);
     block_sum_kernel<3><<<1, kThreads, 0, st>>>(g->ws.part, blocks, out);
@@ -388,7 +398,10 @@ extern "C" cpaa_status cpaa_solve(cpaa_graph *g, const double *p, double c, doub
     job.c0half[0] = ck0[0] / 2.0;
     job.rounds[0] = M;
     float rounds_ms = 0.0f;
-    if ((s = run_tile(g, job, st, true, (opt.flags & CPAA_TIME_ROUNDS) ? &rounds_ms : nullptr)) != CPAA_OK)
+    // per-round sums every round only when the caller asked for the history;
+    // otherwise just the last round's (for info)
+    if ((s = run_tile(g, job, st, opt.history != nullptr,
+                      (opt.flags & CPAA_TIME_ROUNDS) ? &rounds_ms : nullptr)) != CPAA_OK)
         return s;
     if (host_io) CPAA_CUDA(cudaMemcpyAsync(pi, dpi, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
 

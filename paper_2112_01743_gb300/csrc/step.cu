@@ -19,14 +19,14 @@
 // bit b of `active` is set; its per-round sums (the mass view of Sec. 4.1,
 // sum_u T_k[u] and sum_u |T_k[u]|) are reduced when bit b of `reduce` is set.
 //
-// Work split (internal.h): the first num_hub_tiles CTAs each sum one tile of
-// a hub row; the next num_long_chunks CTAs each take one long SELL chunk
-// (more than kLongChunk entries per row), its entries split over the CTA's
-// warps; every other CTA runs kWarps SELL chunks, one warp per chunk and one
-// lane per row, chunks taken longest first.  Every sum runs in a fixed order
-// (a lane adds its row's entries in CSR order, slices are added in warp
-// order; hub tiles use a fixed tree and the tiles are added in tile order), so
-// a result never depends on scheduling.
+// Work split (internal.h): a persistent grid.  CTAs first take the hub tiles
+// (one tile of a hub row each) and the long SELL chunks (more than kLongChunk
+// entries per row, split over the CTA's warps) round-robin; then every warp
+// takes short SELL chunks, one lane per row, round-robin from the
+// longest-first order.  Every sum runs in a fixed order (a lane adds its
+// row's entries in CSR order, slices are added in warp order; hub tiles use
+// shuffle trees over thread-strided sums and the tiles are added in tile
+// order), so a result never depends on scheduling.
 #include <cstring>
 
 #include "device_common.cuh"
@@ -200,38 +200,59 @@ __device__ __forceinline__ void row_finish(const StepParams<P, W> &p, int64_t r,
     if constexpr (Prec<P>::kKahan) store_row<R, W>(p.comp + r * W, o.cmp, true);
 }
 
-// Sum per-thread values of the columns in `reduce` over the CTA and add them
-// to this round's slots.
+// Add the per-thread sums of the columns in `reduce` to this round's slots:
+// a shuffle tree per warp, then one atomic per warp and column (no barrier, so
+// a warp that runs out of work never waits for the others).
 template <class A, int W>
-__device__ __forceinline__ void cta_reduce_add(const A (&sT)[W], const A (&sA)[W], unsigned reduce,
-                                               double *red) {
-    __shared__ double s_red[kWarps][2];
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+__device__ __forceinline__ void warp_reduce_add(const A (&sT)[W], const A (&sA)[W], unsigned reduce,
+                                                double *red) {
+    const int l = threadIdx.x & 31;
+    const int slot = (int)((blockIdx.x * (unsigned)kWarps + (threadIdx.x >> 5)) % kRedSlots);
 #pragma unroll
     for (int b = 0; b < W; ++b) {
-        if (!(reduce >> b & 1u)) continue;  // uniform over the CTA
+        if (!(reduce >> b & 1u)) continue;  // uniform over the grid
         double a = (double)sT[b], c = (double)sA[b];
         for (int o = 16; o > 0; o >>= 1) {
             a += __shfl_xor_sync(0xffffffffu, a, o);
             c += __shfl_xor_sync(0xffffffffu, c, o);
         }
-        if (l == 0) { s_red[w][0] = a; s_red[w][1] = c; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double x = 0, y = 0;
-            for (int i = 0; i < kWarps; ++i) { x += s_red[i][0]; y += s_red[i][1]; }
-            const int slot = blockIdx.x % kRedSlots;
-            atomicAdd(red + (0 * W + b) * kRedSlots + slot, x);
-            atomicAdd(red + (1 * W + b) * kRedSlots + slot, y);
+        if (l == 0) {
+            atomicAdd(red + (0 * W + b) * kRedSlots + slot, a);
+            atomicAdd(red + (1 * W + b) * kRedSlots + slot, c);
         }
-        __syncthreads();
     }
 }
 
+// Fixed-shape sum over the CTA of one value per thread and column: a shuffle
+// tree in each warp, then thread 0 adds the kWarps warp sums in warp order.
+// Returns the total in thread 0 (other threads: unspecified).
+template <class A, int W>
+__device__ __forceinline__ void cta_sum_w(A (&v)[W], A (&s_w)[kWarps][W]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int b = 0; b < W; ++b)
+        for (int o = 16; o > 0; o >>= 1) v[b] += __shfl_xor_sync(0xffffffffu, v[b], o);
+    if (lane == 0)
+#pragma unroll
+        for (int b = 0; b < W; ++b) s_w[warp][b] = v[b];
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            A t = s_w[0][b];
+            for (int q = 1; q < kWarps; ++q) t += s_w[q][b];
+            v[b] = t;
+        }
+}
+
+// One hub tile (kHubTileEntries entries of a hub row) by one CTA.  The CTA
+// that takes the row's last ticket adds the tile partials in tile order and
+// writes the row (an atomic ticket: no CTA waits for another).
 template <int P, int W>
-__device__ __forceinline__ void hub_tile(const StepParams<P, W> &p, int4 t) {
+__device__ __forceinline__ void hub_tile(const StepParams<P, W> &p, int4 t, typename Prec<P>::A (&sT)[W],
+                                         typename Prec<P>::A (&sA)[W]) {
     using A = typename Prec<P>::A;
-    __shared__ A s_v[W][kThreads];
+    __shared__ A s_w[kWarps][W];
     __shared__ int s_last;
     const int tid = threadIdx.x;
     const int h = t.x, j = t.y, slot = t.z, hub = t.w - 1;
@@ -257,26 +278,15 @@ __device__ __forceinline__ void hub_tile(const StepParams<P, W> &p, int4 t) {
 #pragma unroll
         for (int b = 0; b < W; ++b) acc[b] += ((x0[b] + x1[b]) + (x2[b] + x3[b]));
     }
-#pragma unroll
-    for (int b = 0; b < W; ++b) s_v[b][tid] = acc[b];
-    __syncthreads();
-    for (int o = kThreads / 2; o > 0; o >>= 1) {
-        if (tid < o)
-#pragma unroll
-            for (int b = 0; b < W; ++b) s_v[b][tid] = s_v[b][tid] + s_v[b][tid + o];
-        __syncthreads();
-    }
+    cta_sum_w<A, W>(acc, s_w);
     if (tid == 0) {
 #pragma unroll
-        for (int b = 0; b < W; ++b) p.long_part[(int64_t)(slot + j) * W + b] = s_v[b][0];
+        for (int b = 0; b < W; ++b) p.long_part[(int64_t)(slot + j) * W + b] = acc[b];
         __threadfence();
         const int ticket = atomicAdd(p.long_cnt + hub, 1);
         s_last = (ticket == nt - 1);
     }
     __syncthreads();
-    A sT[W], sA[W];
-#pragma unroll
-    for (int b = 0; b < W; ++b) sT[b] = sA[b] = A(0);
     if (s_last) {
         __threadfence();
         // every tile partial is visible: add them in tile order, fixed shape
@@ -286,27 +296,16 @@ __device__ __forceinline__ void hub_tile(const StepParams<P, W> &p, int4 t) {
         for (int c = tid; c < nt; c += kThreads)
 #pragma unroll
             for (int b = 0; b < W; ++b) part[b] += __ldcg(p.long_part + (int64_t)(slot + c) * W + b);
-        __syncthreads();
-#pragma unroll
-        for (int b = 0; b < W; ++b) s_v[b][tid] = part[b];
-        __syncthreads();
-        for (int o = kThreads / 2; o > 0; o >>= 1) {
-            if (tid < o)
-#pragma unroll
-                for (int b = 0; b < W; ++b) s_v[b][tid] = s_v[b][tid] + s_v[b][tid + o];
-            __syncthreads();
-        }
+        __syncthreads();  // s_w is free again
+        cta_sum_w<A, W>(part, s_w);
         if (tid == 0) {
-            A s[W];
-#pragma unroll
-            for (int b = 0; b < W; ++b) s[b] = s_v[b][0];
             RowOps<P, W> o;
             load_ops<P, W>(p, h, o);
-            row_finish<P, W>(p, h, s, p.inv_deg[h], p.deg[h], o, sT, sA);
+            row_finish<P, W>(p, h, part, p.inv_deg[h], p.deg[h], o, sT, sA);
             p.long_cnt[hub] = 0;  // ready for the next round
         }
     }
-    cta_reduce_add<A, W>(sT, sA, p.reduce, p.red);
+    __syncthreads();  // s_w and s_last are reused by the CTA's next item
 }
 
 template <int W> struct Unroll { static constexpr int value = W >= 8 ? 1 : 8 / W; };
@@ -340,10 +339,11 @@ __device__ __forceinline__ void chunk_sum(const StepParams<P, W> &p, const int32
     }
 }
 
-// A long chunk: warp w sums slice w of the entries of all 32 rows; the slices
-// are added in warp order and warp 0 finishes the rows.
+// A long chunk by one CTA: warp w sums slice w of the entries of all 32
+// rows; the slices are added in warp order and warp 0 finishes the rows.
 template <int P, int W>
-__device__ __forceinline__ void long_chunk(const StepParams<P, W> &p, int c) {
+__device__ __forceinline__ void long_chunk(const StepParams<P, W> &p, int c, typename Prec<P>::A (&sT)[W],
+                                           typename Prec<P>::A (&sA)[W]) {
     using A = typename Prec<P>::A;
     __shared__ A s_part[kWarps][W][kChunkRows];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -356,9 +356,6 @@ __device__ __forceinline__ void long_chunk(const StepParams<P, W> &p, int c) {
 #pragma unroll
     for (int b = 0; b < W; ++b) s_part[warp][b][lane] = acc[b];
     __syncthreads();
-    A sT[W], sA[W];
-#pragma unroll
-    for (int b = 0; b < W; ++b) sT[b] = sA[b] = A(0);
     if (warp == 0) {
         const int64_t r = p.n_hub + (int64_t)c * kChunkRows + lane;
         A s[W];
@@ -373,27 +370,28 @@ __device__ __forceinline__ void long_chunk(const StepParams<P, W> &p, int c) {
             row_finish<P, W>(p, r, s, ld_once(p.inv_deg + r), ld_once(p.deg + r), o, sT, sA);
         }
     }
-    cta_reduce_add<A, W>(sT, sA, p.reduce, p.red);
+    __syncthreads();  // s_part is reused by the CTA's next item
 }
 
+// Persistent grid (as many CTAs as fit on the GPU at once).  Phase 1: CTAs
+// take the CTA-sized items (hub tiles, then long chunks) round-robin.  Phase
+// 2: every warp takes short chunks round-robin from the longest-first order,
+// which balances the warps without any atomics.
 template <int P, int W>
 __global__ void __launch_bounds__(kThreads) cheb_step_kernel(const StepParams<P, W> p) {
     using A = typename Prec<P>::A;
-    if ((int)blockIdx.x < p.num_hub_tiles) {
-        hub_tile<P, W>(p, p.hub_tiles[blockIdx.x]);
-        return;
-    }
-    const int b0 = (int)blockIdx.x - p.num_hub_tiles;
-    if (b0 < p.num_long_chunks) {
-        long_chunk<P, W>(p, p.chunk_order[b0]);
-        return;
-    }
-    const int lane = threadIdx.x & 31;
-    const int idx = p.num_long_chunks + (b0 - p.num_long_chunks) * kWarps + (threadIdx.x >> 5);
     A sT[W], sA[W];
 #pragma unroll
     for (int b = 0; b < W; ++b) sT[b] = sA[b] = A(0);
-    if (idx < p.num_chunks) {
+    const int n_cta_items = p.num_hub_tiles + p.num_long_chunks;
+    for (int it = blockIdx.x; it < n_cta_items; it += gridDim.x) {
+        if (it < p.num_hub_tiles) hub_tile<P, W>(p, p.hub_tiles[it], sT, sA);
+        else long_chunk<P, W>(p, p.chunk_order[it - p.num_hub_tiles], sT, sA);
+    }
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (int)gridDim.x * kWarps;
+    for (int idx = p.num_long_chunks + (int)blockIdx.x * kWarps + (int)(threadIdx.x >> 5); idx < p.num_chunks;
+         idx += nwarps) {
         const int c = p.chunk_order[idx];
         const int64_t off = p.chunk_off[c];
         const int len = p.chunk_len[c];
@@ -416,7 +414,7 @@ __global__ void __launch_bounds__(kThreads) cheb_step_kernel(const StepParams<P,
             row_finish<P, W>(p, r, acc, inv, d, o, sT, sA);
         }
     }
-    cta_reduce_add<A, W>(sT, sA, p.reduce, p.red);
+    warp_reduce_add<A, W>(sT, sA, p.reduce, p.red);
 }
 
 template <int P, int W>
@@ -456,8 +454,15 @@ static cudaError_t launch_typed(const StepLaunch &s) {
     p.active = s.active;
     p.reduce = s.reduce;
     p.first = s.first;
-    const int grid = g->num_hub_tiles + g->num_long_chunks +
-                     (g->num_chunks - g->num_long_chunks + kWarps - 1) / kWarps;
+    static int per_sm = 0, sms = 0;  // per instantiation, on the current device
+    if (per_sm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cheb_step_kernel<P, W>, kThreads, 0);
+        if (per_sm < 1) per_sm = 1;
+    }
+    const int grid = per_sm * sms;
     cheb_step_kernel<P, W><<<grid, kThreads, 0, s.stream>>>(p);
     return cudaGetLastError();
 }

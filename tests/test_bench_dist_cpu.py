@@ -50,3 +50,22 @@ def test_alg_bytes_formula():
     n, nnz = 10, 100
     assert bench.alg_bytes_per_round(n, nnz, "f64") == 4 * nnz + 4 * (n + 1) + 4 * n + 24 * n + 16 * n
     assert bench.alg_bytes_per_round(n, nnz, "f32") == 4 * nnz + 4 * (n + 1) + 4 * n + 12 * n + 8 * n + 8 * n
+
+
+def test_reference_arm_json_line():
+    """bench.py --impl reference times the FP64 oracle (the only reference this
+    method has) and prints one JSON line with the contract's keys."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                          "--workload", "chung_lu_10k", "--steps", "2", "--warmup", "1"],
+                         capture_output=True, text=True, timeout=600, cwd=root)
+    assert out.returncode == 0, out.stderr
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "GTEPS" and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0

@@ -119,3 +119,31 @@ def test_config_grid_precision_study(pkg):
     assert errs["f32"] <= 1e-6
     assert errs["bf16"] <= 5e-2
     G.close()
+
+
+def test_config_batched_4M_sampled_columns(pkg):
+    """4M-vertex Chung-Lu, 256 personalised vectors (1-16 uniform seeds), c =
+    0.85, tol 1e-6, FP32 tiles: sampled columns against the oracle run for the
+    same rounds, and every column normalised to 1."""
+    g = ci.chung_lu(1 << 22, 64_000_000, seed=0, device="cuda")
+    G = pkg.Graph(g.row_ptr, g.col_idx, n=g.n)
+    rp, cx = g.numpy()
+    n = g.n
+    del g
+    B = 256
+    seeds = ci.seed_vectors(n, B, max_seeds=16, seed=0)
+    P = torch.zeros((B, n), dtype=torch.float64, device="cuda")
+    for b, (s, w) in enumerate(seeds):
+        P[b, torch.as_tensor(s.astype(np.int64), device="cuda")] = torch.as_tensor(w, device="cuda")
+    PI = torch.empty_like(P)
+    infos = G.solve_batch(B, P, np.full(B, 0.85), 1e-6, PI, precision=pkg.CPAA_F32)
+    torch.cuda.synchronize()
+    sums = PI.sum(dim=1).cpu().numpy()
+    assert np.abs(sums - 1.0).max() < 1e-9
+    for b in (0, 131):
+        p = P[b].cpu().numpy()
+        ref = O.cpaa(rp, cx, p, 0.85, infos[b].rounds)
+        rel = np.abs(PI[b].cpu().numpy() - ref).sum() / np.abs(ref).sum()
+        print("batched column %d: rounds %d, rel L1 %.3e" % (b, infos[b].rounds, rel))
+        assert rel <= 1e-6
+    G.close()

@@ -195,3 +195,21 @@ def test_batch_columns_equal_single(pkg, uploaded):
             single, info = solve(pkg, G, P[b], cs[b], 1e-7, precision=prec)
             assert infos[b].rounds == info.rounds
             assert np.array_equal(PI[b].cpu().numpy(), single)
+
+
+def test_batch_on_fresh_graph(pkg):
+    """A batch as the very first solve on a graph (no earlier single solve has
+    set up the workspace), with the automatic tile width."""
+    g = ci.chung_lu(50000, 600000, seed=77)
+    G = upload(pkg, g)
+    B = 20
+    P = ci.seed_dense(g.n, ci.seed_vectors(g.n, B, seed=8))
+    Pd = torch.as_tensor(P).cuda()
+    PI = torch.empty_like(Pd)
+    infos = G.solve_batch(B, Pd, np.full(B, 0.85), 1e-6, PI, precision=pkg.CPAA_F32)
+    torch.cuda.synchronize()
+    rp, cx = g.numpy()
+    for b in (0, 7, 19):
+        ref = O.cpaa(rp, cx, P[b], 0.85, infos[b].rounds)
+        assert np.abs(PI[b].cpu().numpy() - ref).sum() / np.abs(ref).sum() <= 1e-6
+    G.close()
