@@ -549,6 +549,26 @@ def run_ours(args):
                "speedup_of_%s" % prec: ms64 / (ms_total / args.steps),
                "l1_%s_vs_f64" % prec: l1}
 
+    # ---- the paper's comparison: power method (SPI) on the same kernels, same L1 bound
+    power = None
+    if not args.skip_power:
+        power = {}
+        for name in ("f64", "f32"):
+            pp = torch.empty_like(p)
+            G.power_solve(p, wl["c"], wl["tol"], pp, precision=PREC[name])
+            torch.cuda.synchronize()
+            e0.record(stream)
+            pinf = [G.power_solve(p, wl["c"], wl["tol"], pp, precision=PREC[name]) for _ in range(args.steps)]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_pow = e0.elapsed_time(e1) / args.steps
+            ms_cheb = (ms_total / args.steps) if name == prec else (f64["ms_per_solve"] if (f64 and name == "f64") else None)
+            power[name] = {"rounds": pinf[0].rounds, "ms_per_solve": ms_pow,
+                           "cpaa_rounds": rounds if name == prec else (f64["rounds"] if f64 else None),
+                           "cpaa_ms_per_solve": ms_cheb,
+                           "cpaa_speedup": (ms_pow / ms_cheb) if ms_cheb else None,
+                           "l1_vs_cpaa_same_precision": float((pp - pi_main).abs().sum().item()) if name == prec else None}
+
     # ---- end to end through the C ABI with host buffers (pinned)
     hp = torch.full((n,), 1.0 / n, dtype=torch.float64).pin_memory()
     hpi = torch.empty((n,), dtype=torch.float64).pin_memory()
@@ -631,6 +651,7 @@ def run_ours(args):
         "clocks": clk,
         "gpu_launches": sum(i.rounds + 6 for i in infos),
         "f64": f64,
+        "power": power,
         "batch": batch,
         "small": small,
         "grid": grid,
@@ -654,6 +675,7 @@ def main(argv=None):
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-serve", action="store_true")
     ap.add_argument("--skip-grid", action="store_true")
+    ap.add_argument("--skip-power", action="store_true")
     ap.add_argument("--serve-queries", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)

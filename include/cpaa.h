@@ -144,6 +144,15 @@ cpaa_status cpaa_graph_info(const cpaa_graph *g, int64_t *n, int64_t *nnz,
 cpaa_status cpaa_solve(cpaa_graph *g, const double *p, double c, double tol, double *pi,
                        const cpaa_options *opt, cpaa_info *info);
 
+/* The paper's comparison baseline on the same device layout and kernels: the
+ * power method x <- c P x + (1 - c) p from x = p (the SPI of Sec. 5.1, also its
+ * ground truth).  It runs T rounds, the smallest with 2 c^T < tol (since
+ * ||x_T - pi*||_1 <= c^T ||p - pi*||_1 <= 2 c^T), or opt->fixed_rounds.
+ * Arguments, info (bound = 2 c^T) and errors as cpaa_solve; CPAA_F64 or
+ * CPAA_F32 only. */
+cpaa_status cpaa_power_solve(cpaa_graph *g, const double *p, double c, double tol, double *pi,
+                             const cpaa_options *opt, cpaa_info *info);
+
 /* B personalised vectors at once (the batched form: the graph is read once
  * per step for a whole tile of vectors).  Column b of P (P + b*n) is solved
  * with damping c[b] and written to PI + b*n; info, if not NULL, has B

@@ -133,14 +133,19 @@ def cpaa(row_ptr, col_idx, p, c, M, normalize=0, nthreads=None, history=False):
     return (pi, mass, l1) if history else pi
 
 
-def power(row_ptr, col_idx, p, c, tol=1e-14, max_iter=100000, nthreads=None):
-    """Power method to an L1 bound of ``tol`` (the paper's SPI, Sec. 5.1)."""
+def power(row_ptr, col_idx, p, c, tol=1e-14, max_iter=100000, nthreads=None, rounds=None):
+    """Power method to an L1 bound of ``tol`` (the paper's SPI, Sec. 5.1), or for
+    exactly ``rounds`` rounds when that is given."""
     rp, rpp = _i32(row_ptr)
     ci, cip = _i32(col_idx)
     pv, pvp = _f64(p)
     x = np.empty(len(rp) - 1, dtype=np.float64)
+    if rounds is not None:  # a zero tolerance never stops early
+        tol, max_iter = 0.0, int(rounds)
     it = lib().orc_power(len(rp) - 1, rpp, cip, pvp, float(c), float(tol), int(max_iter),
                          int(nthreads or default_threads()), x.ctypes.data_as(_pf64))
+    if rounds is not None:
+        return x, int(rounds)
     if it < 0:
         raise RuntimeError("power method did not reach tol")
     return x, it

@@ -18,7 +18,7 @@ __all__ = [
     "CPAA_DEVICE_IO", "CPAA_TIME_ROUNDS",
     "cpaa_options_init", "cpaa_graph_create", "cpaa_graph_destroy", "cpaa_graph_info",
     "cpaa_solve", "cpaa_solve_batch", "cpaa_rounds_needed", "cpaa_l1_bound",
-    "cpaa_status_string", "cpaa_last_error", "cpaa_solve_fixed_noalloc", "Graph",
+    "cpaa_status_string", "cpaa_last_error", "cpaa_solve_fixed_noalloc", "cpaa_power_solve", "Graph",
     "EXPORTED_SYMBOLS", "CPAA_NOALLOC_MAX_N", "CPAA_SERVER_MAX_SEEDS", "CpaaServerStats",
     "cpaa_server_create", "cpaa_server_add_graph", "cpaa_server_submit", "cpaa_server_wait",
     "cpaa_server_cancel", "cpaa_server_get_stats", "cpaa_server_destroy", "Server",
@@ -40,7 +40,7 @@ library_path = os.path.join(HERE, "_build", "libcpaa.so")
 EXPORTED_SYMBOLS = [
     "cpaa_options_init", "cpaa_graph_create", "cpaa_graph_destroy", "cpaa_graph_info",
     "cpaa_solve", "cpaa_solve_batch", "cpaa_rounds_needed", "cpaa_l1_bound",
-    "cpaa_status_string", "cpaa_last_error", "cpaa_solve_fixed_noalloc",
+    "cpaa_status_string", "cpaa_last_error", "cpaa_solve_fixed_noalloc", "cpaa_power_solve",
     "cpaa_server_create", "cpaa_server_add_graph", "cpaa_server_submit", "cpaa_server_wait",
     "cpaa_server_cancel", "cpaa_server_get_stats", "cpaa_server_destroy",
 ]
@@ -102,6 +102,8 @@ def lib():
     L.cpaa_graph_info.argtypes = [vp] + [ctypes.POINTER(i64)] * 4
     L.cpaa_solve.restype = cint
     L.cpaa_solve.argtypes = [vp, vp, dbl, dbl, vp, ctypes.POINTER(CpaaOptions), ctypes.POINTER(CpaaInfo)]
+    L.cpaa_power_solve.restype = cint
+    L.cpaa_power_solve.argtypes = [vp, vp, dbl, dbl, vp, ctypes.POINTER(CpaaOptions), ctypes.POINTER(CpaaInfo)]
     L.cpaa_solve_batch.restype = cint
     L.cpaa_solve_batch.argtypes = [vp, cint, vp, vp, dbl, vp, ctypes.POINTER(CpaaOptions),
                                    ctypes.POINTER(CpaaInfo)]
@@ -227,6 +229,21 @@ def cpaa_solve(g, p, c, tol, pi, precision=CPAA_F64, normalize=0, fixed_rounds=0
                  time_rounds)
     info = CpaaInfo()
     st = lib().cpaa_solve(g, _addr(p), float(c), float(tol), _addr(pi), ctypes.byref(o), ctypes.byref(info))
+    _check(st, raise_notconv)
+    return info
+
+
+def cpaa_power_solve(g, p, c, tol, pi, precision=CPAA_F64, normalize=0, fixed_rounds=0, max_rounds=0,
+                     stream=None, history=None, raise_notconv=True, time_rounds=False):
+    """Power-method baseline (same layout and kernels): pi <- x_T."""
+    dev = _is_device(p)
+    if dev != _is_device(pi):
+        raise ValueError("p and pi must both be host or both be device buffers")
+    o = _options(precision, normalize, fixed_rounds, max_rounds, dev, _stream_of(p, stream), history,
+                 time_rounds)
+    info = CpaaInfo()
+    st = lib().cpaa_power_solve(g, _addr(p), float(c), float(tol), _addr(pi), ctypes.byref(o),
+                                ctypes.byref(info))
     _check(st, raise_notconv)
     return info
 
@@ -371,6 +388,9 @@ class Graph:
 
     def solve(self, p, c, tol, pi, **kw):
         return cpaa_solve(self.handle, p, c, tol, pi, **kw)
+
+    def power_solve(self, p, c, tol, pi, **kw):
+        return cpaa_power_solve(self.handle, p, c, tol, pi, **kw)
 
     def solve_batch(self, B, P, c, tol, PI, **kw):
         return cpaa_solve_batch(self.handle, B, P, c, tol, PI, **kw)

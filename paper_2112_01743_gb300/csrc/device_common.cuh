@@ -72,6 +72,16 @@ __device__ __forceinline__ typename Prec<P>::A new_iterate(typename Prec<P>::A s
     return round_y(y, (const S *)nullptr);
 }
 
+// One power-method round in scaled space (the paper's SPI baseline, Sec. 5.1):
+// x' = c P x + (1 - c) p  ->  y' = c s / d + q,  q = (1 - c) p / d.
+template <int P, class S = typename Prec<P>::S>
+__device__ __forceinline__ typename Prec<P>::A power_iterate(typename Prec<P>::A s, typename Prec<P>::A inv,
+                                                             typename Prec<P>::A c, typename Prec<P>::R q) {
+    using A = typename Prec<P>::A;
+    const A y = fma_rn(mul_rn(c, s), inv, (A)q);
+    return round_y(y, (const S *)nullptr);
+}
+
 // rho += c_k y (Kahan-compensated for the FP32 accumulator).
 template <int P>
 __device__ __forceinline__ void accumulate(typename Prec<P>::R &rr, typename Prec<P>::R &cmp,

@@ -78,8 +78,9 @@ struct TileJob {
     const double *p[kMaxWidth] = {};  // device input columns (caller's vertex order)
     double *pi[kMaxWidth] = {};       // device output columns
     double c[kMaxWidth] = {};
-    double c0half[kMaxWidth] = {};
+    double c0half[kMaxWidth] = {};   // power method: 1 - c (the accumulator slot holds q)
     int rounds[kMaxWidth] = {};
+    int power = 0;                    // 1: power-method rounds instead of Chebyshev ones
 };
 
 }  // namespace cpaa
@@ -150,6 +151,7 @@ struct StepLaunch {
     unsigned active;    // columns that still accumulate
     unsigned reduce;    // columns whose sums are reduced this round
     unsigned first;     // columns in their first round (k == 1)
+    int power;          // 1: power-method round (ck[b] = c, rho holds q = (1-c) p / d)
     int *long_cnt;      // hub ticket counters [n_hub], all zero; NULL = the graph's own
     cudaStream_t stream;
 };

@@ -355,6 +355,7 @@ static bool step_graph(cpaa_server *s, GraphState &gs) {
     sl.active = live;
     sl.reduce = 0;
     sl.first = ~live & ((1u << gs.W) - 1u);
+    sl.power = 0;
     sl.long_cnt = gs.long_cnt;
     sl.stream = gs.stream;
     for (int b = 0; b < kMaxWidth; ++b) sl.ck[b] = 0.0;

@@ -210,7 +210,8 @@ cpaa_status check_stats(const double *s, int64_t nnz, double *kappa) {
 }
 
 template <class S, class R, int W>
-static cudaError_t tile_kernels(cpaa_graph *g, const TileJob &job, cudaStream_t st, int phase) {
+static cudaError_t tile_kernels(cpaa_graph *g, const TileJob &job, cudaStream_t st, int phase,
+                                const void *final_src) {
     Workspace &w = g->ws;
     const int64_t n = g->n;
     TileCols cols;
@@ -227,32 +228,37 @@ static cudaError_t tile_kernels(cpaa_graph *g, const TileJob &job, cudaStream_t 
                                                         (R *)w.rho,
                                                         std::is_same<R, float>::value ? (R *)w.comp : nullptr);
     } else {
+        // the accumulator, or (power method) the last iterate, which has the
+        // same element type on the FP64 and FP32 paths
+        const R *src = (const R *)(final_src ? final_src : w.rho);
         const int blocks = stats_blocks(n);
-        norm_partial_kernel<R, W><<<blocks, kThreads, 0, st>>>((const R *)w.rho, g->deg64, n, w.part);
+        norm_partial_kernel<R, W><<<blocks, kThreads, 0, st>>>(src, g->deg64, n, w.part);
         block_sum_kernel<W><<<1, kThreads, 0, st>>>(w.part, blocks, w.sums);
-        finalize_kernel<R, W><<<grid, kThreads, 0, st>>>(cols, (const R *)w.rho, g->deg64, g->perm, n,
-                                                         w.sums, job.normalize);
+        finalize_kernel<R, W><<<grid, kThreads, 0, st>>>(cols, src, g->deg64, g->perm, n, w.sums,
+                                                         job.normalize);
     }
     return cudaGetLastError();
 }
 
 template <class S, class R>
-static cudaError_t tile_kernels_w(cpaa_graph *g, const TileJob &job, cudaStream_t st, int phase) {
+static cudaError_t tile_kernels_w(cpaa_graph *g, const TileJob &job, cudaStream_t st, int phase,
+                                  const void *final_src) {
     switch (job.width) {
-        case 1: return tile_kernels<S, R, 1>(g, job, st, phase);
-        case 2: return tile_kernels<S, R, 2>(g, job, st, phase);
-        case 4: return tile_kernels<S, R, 4>(g, job, st, phase);
-        case 8: return tile_kernels<S, R, 8>(g, job, st, phase);
-        case 16: return tile_kernels<S, R, 16>(g, job, st, phase);
+        case 1: return tile_kernels<S, R, 1>(g, job, st, phase, final_src);
+        case 2: return tile_kernels<S, R, 2>(g, job, st, phase, final_src);
+        case 4: return tile_kernels<S, R, 4>(g, job, st, phase, final_src);
+        case 8: return tile_kernels<S, R, 8>(g, job, st, phase, final_src);
+        case 16: return tile_kernels<S, R, 16>(g, job, st, phase, final_src);
     }
     return cudaErrorInvalidValue;
 }
 
-static cudaError_t tile_phase(cpaa_graph *g, const TileJob &job, cudaStream_t st, int phase) {
+static cudaError_t tile_phase(cpaa_graph *g, const TileJob &job, cudaStream_t st, int phase,
+                              const void *final_src = nullptr) {
     switch (job.precision) {
-        case CPAA_F64: return tile_kernels_w<double, double>(g, job, st, phase);
-        case CPAA_F32: return tile_kernels_w<float, float>(g, job, st, phase);
-        case CPAA_BF16: return tile_kernels_w<__nv_bfloat16, float>(g, job, st, phase);
+        case CPAA_F64: return tile_kernels_w<double, double>(g, job, st, phase, final_src);
+        case CPAA_F32: return tile_kernels_w<float, float>(g, job, st, phase, final_src);
+        case CPAA_BF16: return tile_kernels_w<__nv_bfloat16, float>(g, job, st, phase, final_src);
     }
     return cudaErrorInvalidValue;
 }
@@ -299,11 +305,12 @@ cpaa_status run_tile(cpaa_graph *g, const TileJob &job, cudaStream_t st, bool hi
         for (int b = 0; b < W; ++b) {
             if (k <= job.rounds[b]) {
                 sl.active |= 1u << b;
-                sl.ck[b] = ck[b][k];
+                sl.ck[b] = job.power ? job.c[b] : ck[b][k];
             }
             if (k == job.rounds[b] || (history_all_rounds && k <= job.rounds[b])) sl.reduce |= 1u << b;
         }
         sl.first = (k == 1) ? (1u << W) - 1u : 0u;
+        sl.power = job.power;
         sl.long_cnt = nullptr;
         sl.stream = st;
         CPAA_CUDA(launch_step(sl));
@@ -315,7 +322,7 @@ cpaa_status run_tile(cpaa_graph *g, const TileJob &job, cudaStream_t st, bool hi
         cudaEventDestroy(ev[0]);
         cudaEventDestroy(ev[1]);
     }
-    CPAA_CUDA(tile_phase(g, job, st, 1));
+    CPAA_CUDA(tile_phase(g, job, st, 1, job.power ? buf[maxM & 1] : nullptr));
     return CPAA_OK;
 }
 
@@ -335,8 +342,19 @@ void round_sums(int width, int b, int k, const std::vector<double> &h, double *s
 
 using namespace cpaa;
 
-extern "C" cpaa_status cpaa_solve(cpaa_graph *g, const double *p, double c, double tol, double *pi,
-                                  const cpaa_options *opt_in, cpaa_info *info) {
+// Rounds of the power method for an L1 bound: ||x_T - pi*||_1 <= c^T ||p - pi*||_1
+// <= 2 c^T (cP has L1 norm c), so the smallest T with 2 c^T < tol.
+static int power_rounds(double c, double tol, int max_rounds) {
+    double b = 2.0;
+    for (int T = 1; T <= max_rounds; ++T) {
+        b *= c;
+        if (b < tol) return T;
+    }
+    return -1;
+}
+
+static cpaa_status solve_one(cpaa_graph *g, const double *p, double c, double tol, double *pi,
+                             const cpaa_options *opt_in, cpaa_info *info, int power) {
     clear_error();
     cpaa_options opt;
     if (opt_in) opt = *opt_in; else cpaa_options_init(&opt);
@@ -347,6 +365,7 @@ extern "C" cpaa_status cpaa_solve(cpaa_graph *g, const double *p, double c, doub
     if (opt.fixed_rounds == 0 && !(tol > 0.0)) return fail(CPAA_EINVAL, "tol must be > 0");
     if (opt.precision != CPAA_F64 && opt.precision != CPAA_F32 && opt.precision != CPAA_BF16)
         return fail(CPAA_EINVAL, "unknown precision");
+    if (power && opt.precision == CPAA_BF16) return fail(CPAA_EINVAL, "the power method runs in FP64 or FP32");
     if (opt.normalize != 0 && opt.normalize != 1) return fail(CPAA_EINVAL, "normalize must be 0 or 1");
     const int max_rounds = opt.max_rounds > 0 ? opt.max_rounds : kDefaultMaxRounds;
     if (opt.fixed_rounds > max_rounds) return fail(CPAA_EINVAL, "fixed_rounds > max_rounds");
@@ -380,7 +399,7 @@ extern "C" cpaa_status cpaa_solve(cpaa_graph *g, const double *p, double c, doub
     cpaa_status result = CPAA_OK;
     int M = opt.fixed_rounds;
     if (M == 0) {
-        M = cpaa_rounds_needed(c, tol, kappa, opt.normalize, max_rounds);
+        M = power ? power_rounds(c, tol, max_rounds) : cpaa_rounds_needed(c, tol, kappa, opt.normalize, max_rounds);
         if (M < 0) {
             M = max_rounds;
             result = CPAA_ENOTCONV;
@@ -395,8 +414,9 @@ extern "C" cpaa_status cpaa_solve(cpaa_graph *g, const double *p, double c, doub
     job.p[0] = dp;
     job.pi[0] = dpi;
     job.c[0] = c;
-    job.c0half[0] = ck0[0] / 2.0;
+    job.c0half[0] = power ? 1.0 - c : ck0[0] / 2.0;
     job.rounds[0] = M;
+    job.power = power;
     float rounds_ms = 0.0f;
     // per-round sums every round only when the caller asked for the history;
     // otherwise just the last round's (for info)
@@ -418,7 +438,7 @@ extern "C" cpaa_status cpaa_solve(cpaa_graph *g, const double *p, double c, doub
         if (info) {
             info->rounds = M;
             info->kappa = kappa;
-            info->bound = cpaa_l1_bound(c, M, kappa, opt.normalize);
+            info->bound = power ? 2.0 * std::pow(c, (double)M) : cpaa_l1_bound(c, M, kappa, opt.normalize);
             if (M == 0) {
                 info->mass = info->l1 = sum_p;
             } else {
@@ -432,4 +452,14 @@ extern "C" cpaa_status cpaa_solve(cpaa_graph *g, const double *p, double c, doub
     }
     if (result == CPAA_ENOTCONV) fail(result, "the L1 bound needs more than max_rounds rounds");
     return result;
+}
+
+extern "C" cpaa_status cpaa_solve(cpaa_graph *g, const double *p, double c, double tol, double *pi,
+                                  const cpaa_options *opt, cpaa_info *info) {
+    return solve_one(g, p, c, tol, pi, opt, info, 0);
+}
+
+extern "C" cpaa_status cpaa_power_solve(cpaa_graph *g, const double *p, double c, double tol, double *pi,
+                                        const cpaa_options *opt, cpaa_info *info) {
+    return solve_one(g, p, c, tol, pi, opt, info, 1);
 }

@@ -27,6 +27,7 @@
 // row's entries in CSR order, slices are added in warp order; hub tiles use
 // shuffle trees over thread-strided sums and the tiles are added in tile
 // order), so a result never depends on scheduling.
+#include <algorithm>
 #include <cstring>
 
 #include "device_common.cuh"
@@ -66,6 +67,7 @@ struct StepParams {
     unsigned active;
     unsigned reduce;
     unsigned first;  // columns in their first round (y_1 = D^-1 P y_0... scaled: s / d)
+    int power;       // 1: power-method round y' = c s / d + q, ck[b] = c, q held in rho
 };
 
 // W consecutive values of one row, with the widest loads the row size allows.
@@ -186,6 +188,19 @@ __device__ __forceinline__ void row_finish(const StepParams<P, W> &p, int64_t r,
     using A = typename Prec<P>::A;
     using R = typename Prec<P>::R;
     S ys[W];
+    if (p.power) {
+        // power method (x' = c P x + (1 - c) p, scaled by D^-1): q = (1 - c) p / d
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            const A y = power_iterate<P>(s[b], inv, p.ck[b], o.rr[b]);
+            store_y(&ys[b], y);
+            const A T = y * d;
+            sT[b] += T;
+            sA[b] += (T < A(0) ? -T : T);
+        }
+        store_row<S, W>(p.y_io + r * W, ys, false);
+        return;
+    }
 #pragma unroll
     for (int b = 0; b < W; ++b) {
         const A y = new_iterate<P>(s[b], inv, o.y_old[b], (p.first >> b) & 1u);
@@ -454,6 +469,7 @@ static cudaError_t launch_typed(const StepLaunch &s) {
     p.active = s.active;
     p.reduce = s.reduce;
     p.first = s.first;
+    p.power = s.power;
     static int per_sm = 0, sms = 0;  // per instantiation, on the current device
     if (per_sm == 0) {
         int dev = 0;
@@ -462,7 +478,11 @@ static cudaError_t launch_typed(const StepLaunch &s) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cheb_step_kernel<P, W>, kThreads, 0);
         if (per_sm < 1) per_sm = 1;
     }
-    const int grid = per_sm * sms;
+    // a small graph needs fewer CTAs than fit: one per CTA item plus one per
+    // kWarps short chunks
+    const int64_t needed = (int64_t)g->num_hub_tiles + g->num_long_chunks +
+                           (g->num_chunks - g->num_long_chunks + kWarps - 1) / kWarps;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sms, needed));
     cheb_step_kernel<P, W><<<grid, kThreads, 0, s.stream>>>(p);
     return cudaGetLastError();
 }

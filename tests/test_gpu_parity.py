@@ -213,3 +213,31 @@ def test_batch_on_fresh_graph(pkg):
         ref = O.cpaa(rp, cx, P[b], 0.85, infos[b].rounds)
         assert np.abs(PI[b].cpu().numpy() - ref).sum() / np.abs(ref).sum() <= 1e-6
     G.close()
+
+
+@pytest.mark.parametrize("gi", [0, 3, 12, 13, 14, 16], ids=lambda i: GRAPHS[i].name)
+def test_power_method_matches_oracle(pkg, uploaded, gi):
+    """The power-method baseline on the same kernels against the oracle's power
+    method for the same rounds (FP64 L1 <= 1e-12), and its rigorous rounds."""
+    g, G = GRAPHS[gi], uploaded[gi]
+    rp, cx = g.numpy()
+    p = _p_variants(g.n)["ramp"]
+    pd = torch.as_tensor(p).cuda()
+    out = torch.empty_like(pd)
+    for T in (1, 2, 7, 30):
+        G.power_solve(pd, 0.85, 0.0, out, fixed_rounds=T, normalize=1)
+        torch.cuda.synchronize()
+        ref, _ = O.power(rp, cx, p, 0.85, rounds=T)
+        assert np.abs(out.cpu().numpy() - ref).sum() <= 1e-12, (g.name, T)
+    info = G.power_solve(pd, 0.85, 1e-8, out)
+    torch.cuda.synchronize()
+    T = next(t for t in range(1, 1000) if 2 * 0.85 ** t < 1e-8)
+    assert info.rounds == T
+    if g.n <= 2500:
+        truth = O.lapack_pagerank(rp, cx, p, 0.85)
+        assert np.abs(out.cpu().numpy() - truth).sum() <= 1e-8
+    out32 = torch.empty_like(pd)
+    G.power_solve(pd, 0.85, 1e-6, out32, precision=pkg.CPAA_F32)
+    torch.cuda.synchronize()
+    ref, _ = O.power(rp, cx, p, 0.85, rounds=next(t for t in range(1, 1000) if 2 * 0.85 ** t < 1e-6))
+    assert np.abs(out32.cpu().numpy() - ref).sum() / np.abs(ref).sum() <= 1e-6
