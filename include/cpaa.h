@@ -149,7 +149,8 @@ cpaa_status cpaa_solve(cpaa_graph *g, const double *p, double c, double tol, dou
  * ground truth).  It runs T rounds, the smallest with 2 c^T < tol (since
  * ||x_T - pi*||_1 <= c^T ||p - pi*||_1 <= 2 c^T), or opt->fixed_rounds.
  * Arguments, info (bound = 2 c^T) and errors as cpaa_solve; CPAA_F64 or
- * CPAA_F32 only. */
+ * CPAA_F32 only.  normalize = 1 returns x_T as it is (it sums to 1 up to
+ * rounding); normalize = 0 divides by its sum. */
 cpaa_status cpaa_power_solve(cpaa_graph *g, const double *p, double c, double tol, double *pi,
                              const cpaa_options *opt, cpaa_info *info);
 

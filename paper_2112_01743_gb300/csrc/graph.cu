@@ -66,7 +66,8 @@ __global__ void vertex_arrays_kernel(const int32_t *__restrict__ row_ptr,
 }
 
 // One warp per SELL chunk: lane l writes entry i of row n_hub + 32c + l at
-// chunk_off[c] + 32 i + l, relabelled; padding gets the sentinel n.
+// chunk_off[c] + 128 (i / 4) + 4 l + i % 4 (each lane's entries in groups of
+// four, one 16-byte load), relabelled; padding gets the sentinel n.
 __global__ void build_sell_kernel(const int32_t *__restrict__ row_ptr,
                                   const int32_t *__restrict__ col_idx,
                                   const int32_t *__restrict__ perm,
@@ -87,7 +88,8 @@ __global__ void build_sell_kernel(const int32_t *__restrict__ row_ptr,
         const int64_t off = chunk_off[c];
         const int len = chunk_len[c];
         for (int i = 0; i < len; ++i)
-            sell[off + (int64_t)i * kChunkRows + lane] = (i < d) ? inv_perm[col_idx[e0 + i]] : (int32_t)n;
+            sell[off + (int64_t)(i / kSellVec) * (kChunkRows * kSellVec) + lane * kSellVec + i % kSellVec] =
+                (i < d) ? inv_perm[col_idx[e0 + i]] : (int32_t)n;
     }
 }
 
@@ -168,7 +170,8 @@ static void host_layout(const int32_t *rp, int64_t n, HostLayout &L) {
     L.chunk_len.resize((size_t)nch);
     int64_t off = 0;
     for (int64_t c = 0; c < nch; ++c) {
-        const int len = deg(rest[(size_t)(c * kChunkRows)]);
+        // the longest row, rounded up to whole groups of kSellVec entries
+        const int len = (deg(rest[(size_t)(c * kChunkRows)]) + kSellVec - 1) / kSellVec * kSellVec;
         L.chunk_off[c] = off;
         L.chunk_len[c] = len;
         off += (int64_t)len * kChunkRows;

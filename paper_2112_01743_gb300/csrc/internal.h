@@ -24,9 +24,11 @@ namespace cpaa {
 //
 // Non-hub rows are held as SELL-C-sigma (sliced ELLPACK, C = kChunkRows = 32,
 // sigma = kSortWindow): chunk c holds new rows n_hub + 32c .. + 31, padded to
-// the chunk's longest row, column-major (entry i of lane l at
-// chunk_off[c] + 32 i + l); padding entries hold the sentinel column n, whose
-// iterate value is kept at zero.  One warp owns one chunk, one lane one row.
+// the chunk's longest row rounded up to a multiple of kSellVec, column-major
+// in groups of kSellVec entries per lane (entry i of lane l at
+// chunk_off[c] + 128 (i / 4) + 4 l + i % 4, so a warp reads 512 contiguous
+// bytes per load); padding entries hold the sentinel column n, whose iterate
+// value is kept at zero.  One warp owns one chunk, one lane one row.
 // Windows are multiples of 32 rows, so a chunk never straddles two windows
 // and its first row is its longest.
 //
@@ -39,6 +41,7 @@ namespace cpaa {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kChunkRows = 32;
+constexpr int kSellVec = 4;     // a lane's SELL entries are stored in groups of 4 (one 16-byte load)
 constexpr int kSortWindow = 1024;
 constexpr int kHubDegree = 2048;
 constexpr int kHubTileEntries = 2048;

@@ -220,7 +220,9 @@ static cudaError_t tile_kernels(cpaa_graph *g, const TileJob &job, cudaStream_t 
         cols.p[b] = job.p[bb];
         cols.pi[b] = job.pi[bb];
         cols.c0half[b] = job.c0half[bb];
-        cols.scale[b] = 1.0 - job.c[bb];
+        // normalize = 1: (1 - c) pibar for CPAA (Sec. 2.1); the power iterate
+        // x_T is already the estimate
+        cols.scale[b] = job.power ? 1.0 : 1.0 - job.c[bb];
     }
     const unsigned grid = (unsigned)std::min<int64_t>((n + kThreads - 1) / kThreads, 8192);
     if (phase == 0) {

@@ -323,34 +323,66 @@ __device__ __forceinline__ void hub_tile(const StepParams<P, W> &p, int4 t, type
     __syncthreads();  // s_w and s_last are reused by the CTA's next item
 }
 
-template <int W> struct Unroll { static constexpr int value = W >= 8 ? 1 : 8 / W; };
+template <int W> struct Unroll { static constexpr int value = W >= 4 ? 1 : 8 / (4 * W); };
 
-// Sum of entries [i0, i1) of the lane's row in chunk `col` (SELL layout).
+// Sum of entries [i0, i1) of the lane's row in a SELL chunk; i0 and i1 are
+// multiples of kSellVec.  `col` points at the chunk's lane group (chunk start
+// + kSellVec * lane); entries are added in CSR order.
 template <int P, int W>
 __device__ __forceinline__ void chunk_sum(const StepParams<P, W> &p, const int32_t *col, int i0, int i1,
                                           typename Prec<P>::A (&acc)[W]) {
     using A = typename Prec<P>::A;
-    constexpr int U = Unroll<W>::value;
+    constexpr int U = Unroll<W>::value;  // groups of four entries in flight per lane
+    constexpr int G = kChunkRows * kSellVec;
 #pragma unroll
     for (int b = 0; b < W; ++b) acc[b] = A(0);
-    int i = i0;
-    for (; i + U <= i1; i += U) {
-        int jj[U];
+    int q = i0 / kSellVec;
+    const int q1 = i1 / kSellVec;
+    if constexpr (W >= 8) {
+        // wide rows: one gathered row in registers at a time
+        for (; q < q1; ++q) {
+            const int4 j = ld_stream4(col + (int64_t)q * G);
+            const int jj[4] = {j.x, j.y, j.z, j.w};
 #pragma unroll
-        for (int k = 0; k < U; ++k) jj[k] = ld_stream(col + (int64_t)(i + k) * kChunkRows);
-        A x[U][W];
+            for (int e = 0; e < 4; ++e) {
+                A x[W];
+                gather_row<P, W>(p.y_src, jj[e], x);
 #pragma unroll
-        for (int k = 0; k < U; ++k) gather_row<P, W>(p.y_src, jj[k], x[k]);
+                for (int b = 0; b < W; ++b) acc[b] += x[b];
+            }
+        }
+        return;
+    }
+    for (; q + U <= q1; q += U) {
+        int4 jj[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) jj[k] = ld_stream4(col + (int64_t)(q + k) * G);
+        A x[U][4][W];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            gather_row<P, W>(p.y_src, jj[k].x, x[k][0]);
+            gather_row<P, W>(p.y_src, jj[k].y, x[k][1]);
+            gather_row<P, W>(p.y_src, jj[k].z, x[k][2]);
+            gather_row<P, W>(p.y_src, jj[k].w, x[k][3]);
+        }
 #pragma unroll
         for (int k = 0; k < U; ++k)
 #pragma unroll
-            for (int b = 0; b < W; ++b) acc[b] += x[k][b];
-    }
-    for (; i < i1; ++i) {
-        A x[W];
-        gather_row<P, W>(p.y_src, ld_stream(col + (int64_t)i * kChunkRows), x);
+            for (int e = 0; e < 4; ++e)
 #pragma unroll
-        for (int b = 0; b < W; ++b) acc[b] += x[b];
+                for (int b = 0; b < W; ++b) acc[b] += x[k][e][b];
+    }
+    for (; q < q1; ++q) {
+        const int4 j = ld_stream4(col + (int64_t)q * G);
+        A x[4][W];
+        gather_row<P, W>(p.y_src, j.x, x[0]);
+        gather_row<P, W>(p.y_src, j.y, x[1]);
+        gather_row<P, W>(p.y_src, j.z, x[2]);
+        gather_row<P, W>(p.y_src, j.w, x[3]);
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+#pragma unroll
+            for (int b = 0; b < W; ++b) acc[b] += x[e][b];
     }
 }
 
@@ -364,10 +396,11 @@ __device__ __forceinline__ void long_chunk(const StepParams<P, W> &p, int c, typ
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t off = p.chunk_off[c];
     const int len = p.chunk_len[c];
-    const int per = (len + kWarps - 1) / kWarps;
+    // slices of whole kSellVec groups
+    const int per = ((len + kWarps - 1) / kWarps + kSellVec - 1) / kSellVec * kSellVec;
     const int i0 = min(len, warp * per), i1 = min(len, i0 + per);
     A acc[W];
-    chunk_sum<P, W>(p, p.sell_col + off + lane, i0, i1, acc);
+    chunk_sum<P, W>(p, p.sell_col + off + kSellVec * lane, i0, i1, acc);
 #pragma unroll
     for (int b = 0; b < W; ++b) s_part[warp][b][lane] = acc[b];
     __syncthreads();
@@ -423,7 +456,7 @@ __global__ void __launch_bounds__(kThreads) cheb_step_kernel(const StepParams<P,
             if constexpr (kEarly) load_ops<P, W>(p, r, o);
         }
         A acc[W];
-        chunk_sum<P, W>(p, p.sell_col + off + lane, 0, len, acc);
+        chunk_sum<P, W>(p, p.sell_col + off + kSellVec * lane, 0, len, acc);
         if (live) {
             if constexpr (!kEarly) load_ops<P, W>(p, r, o);
             row_finish<P, W>(p, r, acc, inv, d, o, sT, sA);
