@@ -50,6 +50,9 @@ WORKLOADS = {
     "chung_lu_1M": dict(n=1 << 20, edges=16_000_000, gamma=2.1, seed=0, c=0.85, tol=1e-6,
                         desc="Chung-Lu n=2^20, 1.6e7 pair draws, gamma=2.1, seed 0, + ring; "
                              "c=0.85, uniform p, tol 1e-6 L1"),
+    "grid_4096": dict(rows=4096, cols=4096, frac=0.2, seed=0, c=0.85, tol=1e-6,
+                      desc="4096x4096 lattice, 20% of edges deleted (seed 0, spanning tree kept); "
+                           "c=0.85, uniform p, tol 1e-6 L1"),
 }
 
 PREC = {"f64": 0, "f32": 1, "bf16": 2}
@@ -173,7 +176,10 @@ def make_graph(wl, device):
     import cpaa_inputs as ci
     w = WORKLOADS[wl]
     t = time.time()
-    g = ci.chung_lu(w["n"], w["edges"], gamma=w["gamma"], seed=w["seed"], device=device)
+    if "rows" in w:
+        g = ci.grid_deleted(w["rows"], w["cols"], w["frac"], seed=w["seed"], device=device)
+    else:
+        g = ci.chung_lu(w["n"], w["edges"], gamma=w["gamma"], seed=w["seed"], device=device)
     return g, time.time() - t
 
 
@@ -247,6 +253,17 @@ def run_batch(pkg, args, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     t_batch = e0.elapsed_time(e1)
+    # the same batch under the a-posteriori stopping rule
+    PI2 = torch.empty_like(P)
+    G.solve_batch(B, P, cs, 1e-6, PI2, precision=pkg.CPAA_F32, stop_rule=pkg.CPAA_STOP_POSTERIORI)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    infos2 = G.solve_batch(B, P, cs, 1e-6, PI2, precision=pkg.CPAA_F32, stop_rule=pkg.CPAA_STOP_POSTERIORI)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_batch2 = e0.elapsed_time(e1)
+    d12 = float((PI2 - PI).abs().sum(dim=1).max().item())
+    del PI2
     # plain FP64 single-vector form on a sample of the same queries
     sample = list(range(0, B, 16))
     pi = torch.empty((n,), dtype=torch.float64, device="cuda")
@@ -261,6 +278,7 @@ def run_batch(pkg, args, stream):
     l1 = float((PI[sample[-1]] - pi).abs().sum().item())
     G.close()
     rounds = [i.rounds for i in infos]
+    rounds2 = [i.rounds for i in infos2]
     return {"workload": "Chung-Lu n=2^22, 6.4e7 pair draws, gamma=2.1, seed 0, + ring; 256 vectors "
                         "uniform over 1-16 seeds; c=0.85; tol 1e-6 L1",
             "n": n, "nnz": nnz, "B": B, "precision": "f32",
@@ -269,7 +287,12 @@ def run_batch(pkg, args, stream):
             "speedup_batched_f32_vs_single_f64": t_single / (t_batch / B),
             "effective_gteps": nnz * sum(rounds) / (t_batch * 1e-3) / 1e9,
             "rounds_min_max": [min(rounds), max(rounds)],
-            "l1_batched_f32_vs_single_f64_last_sample": l1}
+            "l1_batched_f32_vs_single_f64_last_sample": l1,
+            "posteriori": {"ms_per_query_batched_f32": t_batch2 / B,
+                           "speedup_vs_single_f64": t_single / (t_batch2 / B),
+                           "rounds_min_max": [min(rounds2), max(rounds2)],
+                           "rounds_mean": float(np.mean(rounds2)), "rigorous_rounds_mean": float(np.mean(rounds)),
+                           "max_l1_vs_rigorous": d12}}
 
 
 def run_small(pkg, args, stream):
@@ -367,8 +390,8 @@ def run_serving(pkg, args):
             out.append((gi, seeds, float(rng.choice([0.5, 0.85, 0.95]))))
         return out
 
-    def run(queries, rate):
-        S = pkg.Server(64 << 30)
+    def run(queries, rate, stop_rule=pkg.CPAA_STOP_RIGOROUS):
+        S = pkg.Server(64 << 30, stop_rule=stop_rule)
         ids = [S.add_graph(x, 16) for x in G]
         tickets = []
         lock = threading.Condition()
@@ -412,7 +435,9 @@ def run_serving(pkg, args):
         S.close()
         return len(queries) / (done["t_last"] - t0), st
 
-    sat_qps, sat_st = run(make(args.serve_queries // 4), None)
+    sat_queries = make(args.serve_queries // 4)
+    sat_qps, sat_st = run(sat_queries, None)
+    post_qps, post_st = run(sat_queries, None, pkg.CPAA_STOP_POSTERIORI)
     rate = 0.7 * sat_qps
     qps, st = run(make(args.serve_queries), rate)
     for x in G:
@@ -425,7 +450,9 @@ def run_serving(pkg, args):
             "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3, "mean_ms": st["mean_us"] / 1e3,
             "admit_p50_ms": st["admit_p50_us"] / 1e3, "saturated_p50_ms": sat_st["p50_us"] / 1e3,
             "saturated_p99_ms": sat_st["p99_us"] / 1e3, "completed": st["completed"],
-            "failed": st["failed"]}
+            "failed": st["failed"],
+            "posteriori_saturated_qps": post_qps, "posteriori_saturated_p50_ms": post_st["p50_us"] / 1e3,
+            "posteriori_saturated_p99_ms": post_st["p99_us"] / 1e3}
 
 
 def run_reference(args):

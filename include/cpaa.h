@@ -76,6 +76,25 @@ typedef enum { CPAA_F64 = 0, CPAA_F32 = 1, CPAA_BF16 = 2 } cpaa_precision;
 #define CPAA_TIME_ROUNDS 2u /* time the M round launches with CUDA events on the solve's
                                stream; the result is cpaa_info.rounds_ms */
 
+/* cpaa_options.stop_rule.  The paper runs a fixed M and bounds the truncation
+ * by ERR_M = 2 beta^(M+1) / (1 + beta) (Eq. 41), a bound on the neglected
+ * mass.  It becomes an L1 bound on pi through the size of the neglected terms
+ * T_k p (k > M):
+ *   RIGOROUS    ||T_k p||_1 <= kappa = sqrt(sum d) ||D^-1/2 p||_2 for every k
+ *               (||T_k(S)||_2 <= 1 for the symmetric S = D^-1/2 A D^-1/2),
+ *               so M is fixed before the rounds from ERR_M kappa < tol (plus
+ *               the normalisation term of the divide-by-sum form);
+ *   POSTERIORI  kappa is replaced by 2 max_{j<=M} ||T_j p||_1, measured by the
+ *               rounds' own sums; a vector stops after the first round M that
+ *               passes, or at the rigorous M if that comes first.  Not a
+ *               proof but an estimate (checked against exact solutions in the
+ *               tests).  On power-law graphs a one-seed vector's ||T_j p||_1
+ *               climbs to about 0.4 kappa, so it saves a round or two there;
+ *               for uniform p, 2 max ||T_j p||_1 exceeds kappa and the rigorous
+ *               M stands.  Every round then takes its sums (two small extra
+ *               kernels per round). */
+typedef enum { CPAA_STOP_RIGOROUS = 0, CPAA_STOP_POSTERIORI = 1 } cpaa_stop_rule;
+
 typedef struct {
     cpaa_precision precision; /* default CPAA_F64 */
     int normalize;            /* 0: pi = pibar / sum(pibar), last line of Algorithm 1 (default);
@@ -89,11 +108,13 @@ typedef struct {
                                  for k = 0..M (the mass view of Sec. 4.1); cpaa_solve only */
     int batch_width;          /* cpaa_solve_batch: vectors per tile, 1/2/4/8/16, or 0 to pick
                                  the widest whose gathered array fits in L2 (default 0) */
+    cpaa_stop_rule stop_rule; /* default CPAA_STOP_RIGOROUS; cpaa_solve and cpaa_solve_batch */
 } cpaa_options;
 
 typedef struct {
-    int rounds;       /* M that was run */
-    double bound;     /* rigorous L1 bound on ||pi - pi*||_1 after M rounds */
+    int rounds;       /* M that was run (accumulated terms c_1 .. c_M) */
+    double bound;     /* L1 bound on ||pi - pi*||_1 after M rounds by the stop rule that
+                         ended the solve: rigorous, or the a-posteriori estimate */
     double kappa;     /* sqrt(sum d) ||D^-1/2 p||_2 */
     double mass;      /* sum_u T_M[u]; equals sum p up to rounding (Sec. 4.1) */
     double l1;        /* sum_u |T_M[u]| */

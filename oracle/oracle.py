@@ -110,6 +110,27 @@ def rounds_needed(c, tol, kap, normalize=0, max_rounds=10000):
                                    int(max_rounds))
 
 
+def rounds_posteriori(c, tol, l1_hist, normalize=0, max_rounds=None):
+    """The a-posteriori stopping rule: the first M >= 1 with
+    l1_bound(c, M, 2 max_{j<=M} ||T_j p||_1) < tol, where l1_hist[j] is
+    ||T_j p||_1 (j = 0 .. len - 1) from ``cpaa(..., history=True)``; None if no
+    M within the history (or max_rounds) passes.
+
+    Eq. 41's ERR_M bounds the neglected coefficient mass; the L1 error of pi is
+    at most ERR_M times the size of the neglected T_k p.  The rigorous rule
+    bounds that size by kappa; this rule estimates it from the terms already
+    computed (twice their running maximum).  It is an estimate, not a proof,
+    which is why the tests check its result against the exact solution.
+    """
+    last = len(l1_hist) - 1 if max_rounds is None else min(max_rounds, len(l1_hist) - 1)
+    m = float(l1_hist[0])
+    for M in range(1, last + 1):
+        m = max(m, float(l1_hist[M]))
+        if l1_bound(c, M, 2.0 * m, normalize) < tol:
+            return M
+    return None
+
+
 # -- the method ---------------------------------------------------------------
 
 def cpaa(row_ptr, col_idx, p, c, M, normalize=0, nthreads=None, history=False):

@@ -15,7 +15,7 @@ __all__ = [
     "CPAA_OK", "CPAA_EINVAL", "CPAA_ENOMEM", "CPAA_ENOTCONV", "CPAA_ECUDA", "CPAA_ETIMEOUT",
     "CPAA_EBUSY", "CPAA_ECANCELLED", "CPAA_ENOTFOUND",
     "CPAA_F64", "CPAA_F32", "CPAA_BF16", "CPAA_GRAPH_DEVICE_INPUT", "CPAA_GRAPH_VALIDATE",
-    "CPAA_DEVICE_IO", "CPAA_TIME_ROUNDS",
+    "CPAA_DEVICE_IO", "CPAA_TIME_ROUNDS", "CPAA_STOP_RIGOROUS", "CPAA_STOP_POSTERIORI",
     "cpaa_options_init", "cpaa_graph_create", "cpaa_graph_destroy", "cpaa_graph_info",
     "cpaa_solve", "cpaa_solve_batch", "cpaa_rounds_needed", "cpaa_l1_bound",
     "cpaa_status_string", "cpaa_last_error", "cpaa_solve_fixed_noalloc", "cpaa_power_solve", "Graph",
@@ -32,6 +32,7 @@ CPAA_DEVICE_IO = 1
 CPAA_NOALLOC_MAX_N = 1300000
 CPAA_SERVER_MAX_SEEDS = 64
 CPAA_TIME_ROUNDS = 2
+CPAA_STOP_RIGOROUS, CPAA_STOP_POSTERIORI = 0, 1
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(HERE, "_build", "libcpaa.so")
@@ -56,7 +57,8 @@ class CpaaOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("normalize", ctypes.c_int),
                 ("fixed_rounds", ctypes.c_int), ("max_rounds", ctypes.c_int),
                 ("flags", ctypes.c_uint), ("stream", ctypes.c_void_p),
-                ("history", ctypes.POINTER(ctypes.c_double)), ("batch_width", ctypes.c_int)]
+                ("history", ctypes.POINTER(ctypes.c_double)), ("batch_width", ctypes.c_int),
+                ("stop_rule", ctypes.c_int)]
 
 
 class CpaaInfo(ctypes.Structure):
@@ -196,8 +198,9 @@ def cpaa_graph_info(g):
 
 
 def _options(precision, normalize, fixed_rounds, max_rounds, device_io, stream, history,
-             time_rounds=False):
+             time_rounds=False, stop_rule=CPAA_STOP_RIGOROUS):
     o = cpaa_options_init()
+    o.stop_rule = int(stop_rule)
     o.precision = int(precision)
     o.normalize = int(normalize)
     o.fixed_rounds = int(fixed_rounds)
@@ -220,13 +223,14 @@ def _stream_of(x, stream):
 
 
 def cpaa_solve(g, p, c, tol, pi, precision=CPAA_F64, normalize=0, fixed_rounds=0, max_rounds=0,
-               stream=None, history=None, raise_notconv=True, time_rounds=False):
+               stream=None, history=None, raise_notconv=True, time_rounds=False,
+               stop_rule=CPAA_STOP_RIGOROUS):
     """pi <- CPAA(p); p, pi FP64 length n (both host or both device)."""
     dev = _is_device(p)
     if dev != _is_device(pi):
         raise ValueError("p and pi must both be host or both be device buffers")
     o = _options(precision, normalize, fixed_rounds, max_rounds, dev, _stream_of(p, stream), history,
-                 time_rounds)
+                 time_rounds, stop_rule)
     info = CpaaInfo()
     st = lib().cpaa_solve(g, _addr(p), float(c), float(tol), _addr(pi), ctypes.byref(o), ctypes.byref(info))
     _check(st, raise_notconv)
@@ -234,13 +238,14 @@ def cpaa_solve(g, p, c, tol, pi, precision=CPAA_F64, normalize=0, fixed_rounds=0
 
 
 def cpaa_power_solve(g, p, c, tol, pi, precision=CPAA_F64, normalize=0, fixed_rounds=0, max_rounds=0,
-                     stream=None, history=None, raise_notconv=True, time_rounds=False):
+                     stream=None, history=None, raise_notconv=True, time_rounds=False,
+                     stop_rule=CPAA_STOP_RIGOROUS):
     """Power-method baseline (same layout and kernels): pi <- x_T."""
     dev = _is_device(p)
     if dev != _is_device(pi):
         raise ValueError("p and pi must both be host or both be device buffers")
     o = _options(precision, normalize, fixed_rounds, max_rounds, dev, _stream_of(p, stream), history,
-                 time_rounds)
+                 time_rounds, stop_rule)
     info = CpaaInfo()
     st = lib().cpaa_power_solve(g, _addr(p), float(c), float(tol), _addr(pi), ctypes.byref(o),
                                 ctypes.byref(info))
@@ -249,12 +254,14 @@ def cpaa_power_solve(g, p, c, tol, pi, precision=CPAA_F64, normalize=0, fixed_ro
 
 
 def cpaa_solve_batch(g, B, P, c, tol, PI, precision=CPAA_F32, normalize=0, fixed_rounds=0,
-                     max_rounds=0, stream=None, raise_notconv=True, batch_width=0):
+                     max_rounds=0, stream=None, raise_notconv=True, batch_width=0,
+                     stop_rule=CPAA_STOP_RIGOROUS):
     """Column b of P (n x B column-major, i.e. B vectors back to back) with
     damping c[b] -> column b of PI.  Returns a list of B info records."""
     dev = _is_device(P)
     cvec = np.ascontiguousarray(np.broadcast_to(np.asarray(c, dtype=np.float64), (int(B),)))
-    o = _options(precision, normalize, fixed_rounds, max_rounds, dev, _stream_of(P, stream), None)
+    o = _options(precision, normalize, fixed_rounds, max_rounds, dev, _stream_of(P, stream), None,
+                 False, stop_rule)
     o.batch_width = int(batch_width)
     infos = (CpaaInfo * int(B))()
     st = lib().cpaa_solve_batch(g, int(B), _addr(P), cvec.ctypes.data, float(tol), _addr(PI),
@@ -273,10 +280,12 @@ def cpaa_solve_fixed_noalloc(n, nnz, row_ptr, col_idx, p, c, rounds, pi, normali
     return _check(st)
 
 
-def cpaa_server_create(budget_bytes, precision=CPAA_F32, normalize=0, max_rounds=0):
+def cpaa_server_create(budget_bytes, precision=CPAA_F32, normalize=0, max_rounds=0,
+                       stop_rule=CPAA_STOP_RIGOROUS):
     o = cpaa_options_init()
     o.precision = int(precision)
     o.normalize = int(normalize)
+    o.stop_rule = int(stop_rule)
     if max_rounds:
         o.max_rounds = int(max_rounds)
     h = ctypes.c_void_p()
@@ -327,8 +336,9 @@ def cpaa_server_destroy(s):
 class Server:
     """Owning wrapper of a cpaa_server handle."""
 
-    def __init__(self, budget_bytes, precision=CPAA_F32, normalize=0, max_rounds=0):
-        self.handle = cpaa_server_create(budget_bytes, precision, normalize, max_rounds)
+    def __init__(self, budget_bytes, precision=CPAA_F32, normalize=0, max_rounds=0,
+                 stop_rule=CPAA_STOP_RIGOROUS):
+        self.handle = cpaa_server_create(budget_bytes, precision, normalize, max_rounds, stop_rule)
 
     def add_graph(self, graph, max_slots=0):
         return cpaa_server_add_graph(self.handle, graph.handle, max_slots)

@@ -77,6 +77,8 @@ extern "C" cpaa_status cpaa_solve_batch(cpaa_graph *g, int B, const double *P, c
     if (opt.precision != CPAA_F64 && opt.precision != CPAA_F32 && opt.precision != CPAA_BF16)
         return fail(CPAA_EINVAL, "unknown precision");
     if (opt.normalize != 0 && opt.normalize != 1) return fail(CPAA_EINVAL, "normalize must be 0 or 1");
+    if (opt.stop_rule != CPAA_STOP_RIGOROUS && opt.stop_rule != CPAA_STOP_POSTERIORI)
+        return fail(CPAA_EINVAL, "unknown stop_rule");
     const int max_rounds = opt.max_rounds > 0 ? opt.max_rounds : kDefaultMaxRounds;
     if (opt.fixed_rounds > max_rounds) return fail(CPAA_EINVAL, "fixed_rounds > max_rounds");
     int W = opt.batch_width;
@@ -112,7 +114,7 @@ extern "C" cpaa_status cpaa_solve_batch(cpaa_graph *g, int B, const double *P, c
     CPAA_CUDA(cudaStreamSynchronize(st));
     std::vector<double> kappa(B);
     std::vector<int> M(B);
-    cpaa_status result = CPAA_OK;
+    std::vector<char> notconv(B, 0);
     for (int b = 0; b < B; ++b) {
         if ((s = check_stats(&hs[3 * b], g->nnz, &kappa[b])) != CPAA_OK)
             return fail(s, "column " + std::to_string(b) + ": " + cpaa_last_error());
@@ -121,7 +123,7 @@ extern "C" cpaa_status cpaa_solve_batch(cpaa_graph *g, int B, const double *P, c
             M[b] = cpaa_rounds_needed(c[b], tol, kappa[b], opt.normalize, max_rounds);
             if (M[b] < 0) {
                 M[b] = max_rounds;
-                result = CPAA_ENOTCONV;
+                notconv[b] = 1;
             }
         }
     }
@@ -154,6 +156,8 @@ extern "C" cpaa_status cpaa_solve_batch(cpaa_graph *g, int B, const double *P, c
         job.width = tw;
         job.precision = opt.precision;
         job.normalize = opt.normalize;
+        job.posteriori = opt.stop_rule == CPAA_STOP_POSTERIORI && opt.fixed_rounds == 0;
+        job.tol = tol;
         for (int j = 0; j < tw; ++j) {
             const int b = order[t0 + j];
             std::vector<double> ck0;
@@ -163,12 +167,27 @@ extern "C" cpaa_status cpaa_solve_batch(cpaa_graph *g, int B, const double *P, c
             job.c[j] = c[b];
             job.c0half[j] = ck0[0] / 2.0;
             job.rounds[j] = M[b];
+            job.p_l1[j] = hs[3 * b];
         }
         if ((s = run_tile(g, job, st, false, nullptr)) != CPAA_OK) return s;
+        int sr[kMaxWidth];
+        bool by_post[kMaxWidth] = {};
+        if (job.posteriori) {
+            CPAA_CUDA(cudaMemcpyAsync(sr, w.stop_round, sizeof(int) * kMaxWidth, cudaMemcpyDeviceToHost, st));
+            CPAA_CUDA(cudaStreamSynchronize(st));
+            for (int j = 0; j < tw; ++j) {
+                const int b = order[t0 + j];
+                if (sr[j] >= 1 && sr[j] <= M[b]) {
+                    M[b] = sr[j];
+                    by_post[j] = true;
+                    notconv[b] = 0;
+                }
+            }
+        }
         if (info) {
             int maxM = 0;
             for (int j = 0; j < tw; ++j) maxM = std::max(maxM, job.rounds[j]);
-            std::vector<double> h((size_t)(maxM + 1) * 2 * tw * kRedSlots);
+            std::vector<double> h((size_t)(maxM + 1) * 2 * tw);
             CPAA_CUDA(cudaMemcpyAsync(h.data(), w.red, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st));
             CPAA_CUDA(cudaMemcpyAsync(w.h_sums, w.sums, sizeof(double) * tw, cudaMemcpyDeviceToHost, st));
             CPAA_CUDA(cudaStreamSynchronize(st));
@@ -177,7 +196,16 @@ extern "C" cpaa_status cpaa_solve_batch(cpaa_graph *g, int B, const double *P, c
                 cpaa_info &in = info[b];
                 in.rounds = M[b];
                 in.kappa = kappa[b];
-                in.bound = cpaa_l1_bound(c[b], M[b], kappa[b], opt.normalize);
+                if (by_post[j]) {
+                    double ml = hs[3 * b], t = 0, a = 0;
+                    for (int k = 1; k <= M[b]; ++k) {
+                        round_sums(tw, j, k, h, &t, &a);
+                        ml = std::max(ml, a);
+                    }
+                    in.bound = cpaa_l1_bound(c[b], M[b], 2.0 * ml, opt.normalize);
+                } else {
+                    in.bound = cpaa_l1_bound(c[b], M[b], kappa[b], opt.normalize);
+                }
                 round_sums(tw, j, M[b], h, &in.mass, &in.l1);
                 in.sum_pibar = w.h_sums[j];
                 in.rounds_ms = 0.0;
@@ -189,6 +217,7 @@ extern "C" cpaa_status cpaa_solve_batch(cpaa_graph *g, int B, const double *P, c
         CPAA_CUDA(cudaMemcpyAsync(PI, dPI, sizeof(double) * n * B, cudaMemcpyDeviceToHost, st));
         CPAA_CUDA(cudaStreamSynchronize(st));
     }
-    if (result == CPAA_ENOTCONV) fail(result, "the L1 bound of some column needs more than max_rounds rounds");
-    return result;
+    for (int b = 0; b < B; ++b)
+        if (notconv[b]) return fail(CPAA_ENOTCONV, "the L1 bound of some column needs more than max_rounds rounds");
+    return CPAA_OK;
 }

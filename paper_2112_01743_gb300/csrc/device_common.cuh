@@ -62,13 +62,15 @@ __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, 
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
-// The new iterate of one row from its gathered sum s (Sec. 4.1):
-// k = 1: y = s / d; k >= 2: y = 2 s / d - y_old; rounded to storage.
+// The new iterate of one row from its gathered sum s (Sec. 4.1), given
+// inv2 = 2 / d: k = 1: y = s / d; k >= 2: y = 2 s / d - y_old (one fused
+// multiply-add: 2 s (1/d) and s (2/d) are the same exact product); rounded to
+// storage.
 template <int P, class S = typename Prec<P>::S>
-__device__ __forceinline__ typename Prec<P>::A new_iterate(typename Prec<P>::A s, typename Prec<P>::A inv,
+__device__ __forceinline__ typename Prec<P>::A new_iterate(typename Prec<P>::A s, typename Prec<P>::A inv2,
                                                            typename Prec<P>::A y_old, int first) {
     using A = typename Prec<P>::A;
-    const A y = first ? mul_rn(s, inv) : fma_rn(add_rn(s, s), inv, -y_old);
+    const A y = first ? mul_rn(mul_rn(s, inv2), A(0.5)) : fma_rn(s, inv2, -y_old);
     return round_y(y, (const S *)nullptr);
 }
 

@@ -52,15 +52,18 @@ __global__ void validate_kernel(const int32_t *__restrict__ row_ptr,
 // Per-vertex arrays in the new order, and the inverse permutation.
 __global__ void vertex_arrays_kernel(const int32_t *__restrict__ row_ptr,
                                      const int32_t *__restrict__ perm, int64_t n, double *deg64,
-                                     double *inv64, float *deg32, float *inv32, int32_t *inv_perm) {
+                                     double *inv64, double *inv2_64, float *deg32, float *inv32,
+                                     float *inv2_32, int32_t *inv_perm) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
          r += (int64_t)gridDim.x * blockDim.x) {
         const int32_t u = perm[r];
         const int d = row_ptr[u + 1] - row_ptr[u];
         deg64[r] = (double)d;
         inv64[r] = 1.0 / (double)d;
+        inv2_64[r] = 2.0 / (double)d;
         deg32[r] = (float)d;
         inv32[r] = 1.0f / (float)d;
+        inv2_32[r] = 2.0f / (float)d;
         inv_perm[u] = (int32_t)r;
     }
 }
@@ -114,10 +117,12 @@ static void release(cpaa_graph *g) {
     cudaFree(w.y0); cudaFree(w.y1); cudaFree(w.rho); cudaFree(w.comp); cudaFree(w.red);
     cudaFree(w.long_part); cudaFree(w.part); cudaFree(w.sums); cudaFree(w.io);
     if (w.h_sums) cudaFreeHost(w.h_sums);
+    for (auto &rg : w.round_graphs) cudaGraphExecDestroy(rg.exec);
+    if (w.capture) cudaStreamDestroy(w.capture);
     cudaFree(g->perm); cudaFree(g->hub_row_ptr); cudaFree(g->hub_col); cudaFree(g->hub_tiles);
     cudaFree(g->long_cnt); cudaFree(g->sell_col); cudaFree(g->chunk_off);
-    cudaFree(g->chunk_len); cudaFree(g->chunk_order); cudaFree(g->deg64); cudaFree(g->inv_deg64);
-    cudaFree(g->deg32); cudaFree(g->inv_deg32);
+    cudaFree(g->chunk_len); cudaFree(g->chunk_order); cudaFree(g->chunk_desc); cudaFree(g->deg64); cudaFree(g->inv_deg64);
+    cudaFree(g->deg32); cudaFree(g->inv_deg32); cudaFree(g->inv2_deg64); cudaFree(g->inv2_deg32);
     delete g;
 }
 
@@ -130,15 +135,22 @@ struct HostLayout {
     std::vector<int64_t> chunk_off;
     std::vector<int32_t> chunk_len;
     std::vector<int32_t> chunk_order;
+    std::vector<int4> chunk_desc;
     std::vector<int4> hub_tiles;
     int64_t sell_entries = 0;
 };
 
-static void host_layout(const int32_t *rp, int64_t n, HostLayout &L) {
+static int hub_degree(int64_t nnz) {
+    return (int)std::min<int64_t>(kHubDegree, std::max<int64_t>(kMinHubDegree, nnz / 4096));
+}
+
+static int hub_tile_entries(int hub_deg) { return std::min(kMaxHubTile, std::max(kMinHubTile, 2 * hub_deg)); }
+
+static void host_layout(const int32_t *rp, int64_t n, int hub_deg, int tile, HostLayout &L) {
     auto deg = [&](int32_t u) { return rp[u + 1] - rp[u]; };
     std::vector<int32_t> hubs, rest;
     rest.reserve((size_t)n);
-    for (int64_t u = 0; u < n; ++u) (deg((int32_t)u) > kHubDegree ? hubs : rest).push_back((int32_t)u);
+    for (int64_t u = 0; u < n; ++u) (deg((int32_t)u) > hub_deg ? hubs : rest).push_back((int32_t)u);
     std::stable_sort(hubs.begin(), hubs.end(), [&](int32_t a, int32_t b) { return deg(a) > deg(b); });
     const int64_t nrest = (int64_t)rest.size();
     const int64_t nwin = (nrest + kSortWindow - 1) / kSortWindow;
@@ -161,7 +173,7 @@ static void host_layout(const int32_t *rp, int64_t n, HostLayout &L) {
     for (int h = 0; h < L.n_hub; ++h) {
         const int d = deg(hubs[h]);
         L.hub_row_ptr[h + 1] = L.hub_row_ptr[h] + d;
-        const int nt = (d + kHubTileEntries - 1) / kHubTileEntries;
+        const int nt = (d + tile - 1) / tile;
         for (int j = 0; j < nt; ++j) L.hub_tiles.push_back(make_int4(h, j, slot, h + 1));
         slot += nt;
     }
@@ -181,6 +193,13 @@ static void host_layout(const int32_t *rp, int64_t n, HostLayout &L) {
     std::iota(L.chunk_order.begin(), L.chunk_order.end(), 0);
     std::stable_sort(L.chunk_order.begin(), L.chunk_order.end(),
                      [&](int32_t a, int32_t b) { return L.chunk_len[a] > L.chunk_len[b]; });
+    // one 16-byte descriptor per chunk in processing order: the round kernel
+    // finds a chunk's row, offset and length with a single load
+    L.chunk_desc.resize((size_t)nch);
+    for (int64_t i = 0; i < nch; ++i) {
+        const int32_t c = L.chunk_order[(size_t)i];
+        L.chunk_desc[(size_t)i] = make_int4(c, (int)(L.chunk_off[c] / (kChunkRows * kSellVec)), L.chunk_len[c], 0);
+    }
 }
 
 }  // namespace cpaa
@@ -257,7 +276,9 @@ extern "C" cpaa_status cpaa_graph_create(int64_t n, int64_t nnz, const int32_t *
         }
 
         HostLayout L;
-        host_layout(hrp.data(), n, L);
+        g->hub_degree = hub_degree(nnz);
+        g->hub_tile = hub_tile_entries(g->hub_degree);
+        host_layout(hrp.data(), n, g->hub_degree, g->hub_tile, L);
         g->n_hub = L.n_hub;
         g->hub_nnz = L.hub_row_ptr.back();
         g->num_hub_tiles = (int)L.hub_tiles.size();
@@ -275,8 +296,11 @@ extern "C" cpaa_status cpaa_graph_create(int64_t n, int64_t nnz, const int32_t *
         ALLOC(g->inv_deg64, sizeof(double) * n);
         ALLOC(g->deg32, sizeof(float) * n);
         ALLOC(g->inv_deg32, sizeof(float) * n);
+        ALLOC(g->inv2_deg64, sizeof(double) * n);
+        ALLOC(g->inv2_deg32, sizeof(float) * n);
         vertex_arrays_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 8192), 256>>>(
-            d_rp, g->perm, n, g->deg64, g->inv_deg64, g->deg32, g->inv_deg32, d_inv);
+            d_rp, g->perm, n, g->deg64, g->inv_deg64, g->inv2_deg64, g->deg32, g->inv_deg32, g->inv2_deg32,
+            d_inv);
         CK(cudaGetLastError());
 
         ALLOC(g->hub_row_ptr, sizeof(int32_t) * (L.n_hub + 1));
@@ -300,11 +324,14 @@ extern "C" cpaa_status cpaa_graph_create(int64_t n, int64_t nnz, const int32_t *
         ALLOC(g->chunk_off, sizeof(int64_t) * nch);
         ALLOC(g->chunk_len, sizeof(int32_t) * nch);
         ALLOC(g->chunk_order, sizeof(int32_t) * nch);
+        ALLOC(g->chunk_desc, sizeof(int4) * nch);
         ALLOC(g->sell_col, sizeof(int32_t) * std::max<int64_t>(4, g->sell_entries));
         if (g->num_chunks > 0) {
             CK(cudaMemcpy(g->chunk_off, L.chunk_off.data(), sizeof(int64_t) * g->num_chunks, cudaMemcpyHostToDevice));
             CK(cudaMemcpy(g->chunk_len, L.chunk_len.data(), sizeof(int32_t) * g->num_chunks, cudaMemcpyHostToDevice));
             CK(cudaMemcpy(g->chunk_order, L.chunk_order.data(), sizeof(int32_t) * g->num_chunks,
+                          cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(g->chunk_desc, L.chunk_desc.data(), sizeof(int4) * g->num_chunks,
                           cudaMemcpyHostToDevice));
             build_sell_kernel<<<(unsigned)std::min<int64_t>(((int64_t)g->num_chunks * 32 + 255) / 256, 16384), 256>>>(
                 d_rp, d_ci, g->perm, d_inv, n, L.n_hub, g->num_chunks, g->chunk_off, g->chunk_len, g->sell_col);

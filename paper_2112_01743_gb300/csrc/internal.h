@@ -16,7 +16,7 @@ namespace cpaa {
 // Layout of the graph on the device.
 //
 // Vertices are relabelled once, at cpaa_graph_create:
-//   new ids [0, n_hub)  hub rows (degree > kHubDegree), by decreasing degree;
+//   new ids [0, n_hub)  hub rows (degree > hub_degree(nnz)), by decreasing degree;
 //   new ids [n_hub, n)  every other row, in windows of kSortWindow rows of the
 //                       original order, each window sorted by decreasing degree.
 // Every per-vertex vector (degrees, iterates, accumulator) is stored in the new
@@ -32,22 +32,46 @@ namespace cpaa {
 // Windows are multiples of 32 rows, so a chunk never straddles two windows
 // and its first row is its longest.
 //
-// Hub rows stay CSR (relabelled columns).  Their entries are cut into tiles of
-// kHubTileEntries; one CTA sums one tile, and the CTA that takes the last
-// ticket of a row adds the tile partials in tile order and writes the row (an
-// atomic counter, no waiting).  Hub tile encoding (int4):
+// The hub threshold is kHubDegree on large graphs.  A small graph lowers it
+// (nnz / 4096, at least kMinHubDegree): its round is short, and a SELL chunk
+// whose first rows are long would otherwise set the round's length by one
+// lane's serial gathers (and carry the padding of its shorter rows).  A hub
+// tile holds twice the hub threshold, within [kMinHubTile, kMaxHubTile]
+// entries: long tiles on large graphs (fewer barriers and tickets per entry),
+// short ones on small graphs (more CTAs on a row).
+//
+// Hub rows stay CSR (relabelled columns).  Their entries are cut into tiles;
+// one CTA sums one tile, and the CTA that takes the last ticket of a row adds
+// the tile partials in tile order and writes the row (an atomic counter, no
+// waiting).  Hub tile encoding (int4):
 //   {row, tile, slot, hub + 1}   slot = partial-sum index of tile 0 of the row
+//
+// Defaults of the thresholds: timed on the 2^24-vertex Chung-Lu graph (single
+// FP32 vector) against hub thresholds of 1024 to 16384, tiles of 1024 to 16384
+// entries and long-chunk thresholds of 32 to 128, and on the 10^4-vertex one.
 // ---------------------------------------------------------------------------
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kChunkRows = 32;
 constexpr int kSellVec = 4;     // a lane's SELL entries are stored in groups of 4 (one 16-byte load)
 constexpr int kSortWindow = 1024;
-constexpr int kHubDegree = 2048;
-constexpr int kHubTileEntries = 2048;
-constexpr int kLongChunk = 64;  // SELL chunks longer than this get a whole CTA
-constexpr int kRedSlots = 256;  // atomic slots per reduced scalar and round
-constexpr int kRedQ = 2;       // reduced scalars per round: sum T, sum |T|
+// Tuning constants (compile-time; the defaults were picked by timing the
+// round on the 2^24-vertex Chung-Lu graph).
+#ifndef CPAA_HUB_DEGREE
+#define CPAA_HUB_DEGREE 4096
+#endif
+#ifndef CPAA_MAX_HUB_TILE
+#define CPAA_MAX_HUB_TILE 8192
+#endif
+#ifndef CPAA_LONG_CHUNK
+#define CPAA_LONG_CHUNK 32
+#endif
+constexpr int kHubDegree = CPAA_HUB_DEGREE;       // hub rows: degree above this (the cap)
+constexpr int kMinHubDegree = 64;
+constexpr int kMaxHubTile = CPAA_MAX_HUB_TILE;    // entries of a hub tile (the cap)
+constexpr int kMinHubTile = 2048;
+constexpr int kLongChunk = CPAA_LONG_CHUNK;       // SELL chunks longer than this get a whole CTA
+constexpr int kSumBlocks = 256; // CTAs of the first level of the per-round item sums
 constexpr int kDefaultMaxRounds = 2000;
 
 constexpr int kPrepBlocks = 1024;  // CTAs of the fixed-order reductions
@@ -62,8 +86,15 @@ struct Workspace {
     void *rho = nullptr;       // accumulator D^-1 pibar, [n x W]
     void *comp = nullptr;      // Kahan compensation (FP32 paths), [n x W]
     size_t rho_bytes = 0;
-    double *red = nullptr;     // per-round sums [(M+1)][2][W][kRedSlots]
+    double *red = nullptr;     // per-round sums [(M+1)][2][W]: sum T, sum |T| per column
     size_t red_bytes = 0;
+    double *ipart = nullptr;   // item partial sums [(n_hub + num_chunks)][2][W]
+    size_t ipart_bytes = 0;
+    double *ipart2 = nullptr;  // first-level sums [kSumBlocks][2][W]
+    // a-posteriori stopping rule (CPAA_STOP_POSTERIORI): per column
+    double *maxl1 = nullptr;   // running max_j ||T_j p||_1 [kMaxWidth]
+    unsigned *stop = nullptr;  // stopped columns
+    int *stop_round = nullptr; // [kMaxWidth]
     void *long_part = nullptr; // hub tile partials [num_hub_tiles x W]
     size_t long_part_bytes = 0;
     double *part = nullptr;    // per-CTA partials of the fixed-order reductions
@@ -71,6 +102,14 @@ struct Workspace {
     double *h_sums = nullptr;  // pinned host copy of sums
     double *io = nullptr;      // device staging of host p / pi
     size_t io_bytes = 0;
+    // Round sequences captured as CUDA graphs (solve.cu), keyed by every
+    // value the launches take; replayed by later solves with the same key.
+    struct RoundGraph {
+        std::vector<uint64_t> key;
+        cudaGraphExec_t exec = nullptr;
+    };
+    std::vector<RoundGraph> round_graphs;
+    cudaStream_t capture = nullptr;  // private stream the captures run on
 };
 
 // One tile of up to kMaxWidth vectors for run_tile (solve.cu).
@@ -84,6 +123,23 @@ struct TileJob {
     double c0half[kMaxWidth] = {};   // power method: 1 - c (the accumulator slot holds q)
     int rounds[kMaxWidth] = {};
     int power = 0;                    // 1: power-method rounds instead of Chebyshev ones
+    int posteriori = 0;               // 1: columns may stop early by the a-posteriori rule
+    double tol = 0;                   // its tolerance
+    double p_l1[kMaxWidth] = {};      // ||p||_1 = ||T_0 p||_1 of each column (that rule's start)
+};
+
+// The a-posteriori stopping rule for one round (solve.cu): after round k,
+// column b stops when ERR_k(c_b) * 2 max_{j<=k} ||T_j p||_1 (plus the
+// normalisation term of the divide-by-sum form) falls below tol.
+struct StopArgs {
+    unsigned decide = 0;            // columns that test the rule this round
+    int k[kMaxWidth] = {};          // each column's round number
+    double err[kMaxWidth] = {};     // ERR_k of each column at that round (Eq. 41)
+    double tol[kMaxWidth] = {};     // each column's tolerance
+    int normalize = 0;
+    double *maxl1 = nullptr;        // [W] running max of ||T_j p||_1, j <= k
+    unsigned *stop = nullptr;       // stopped columns (bit mask)
+    int *stop_round = nullptr;      // [W] the round a column stopped after
 };
 
 }  // namespace cpaa
@@ -108,12 +164,17 @@ struct cpaa_graph {
     int64_t *chunk_off = nullptr;    // [num_chunks]
     int32_t *chunk_len = nullptr;    // [num_chunks]
     int32_t *chunk_order = nullptr;  // chunk ids, longest first
+    int4 *chunk_desc = nullptr;      // [num_chunks] in chunk_order: {chunk, offset / 128, length, 0}
+    int hub_degree = cpaa::kHubDegree;  // rows above this degree are hub rows
+    int hub_tile = cpaa::kMaxHubTile;   // entries of a hub tile
     int num_long_chunks = 0;         // leading chunk_order entries longer than kLongChunk
     // per-vertex, new order
     double *deg64 = nullptr;         // d_u
     double *inv_deg64 = nullptr;     // 1 / d_u
+    double *inv2_deg64 = nullptr;    // 2 / d_u (the recurrence's factor)
     float *deg32 = nullptr;
     float *inv_deg32 = nullptr;
+    float *inv2_deg32 = nullptr;
     int64_t device_bytes = 0;
     int tuned_width[3] = {0, 0, 0};  // batch tile width picked by the autotuner, per precision
     cpaa::Workspace ws;
@@ -136,28 +197,36 @@ void clear_error();
 cpaa_status dev_alloc(cpaa_graph *g, void **p, size_t bytes);
 void dev_free(cpaa_graph *g, void **p, size_t bytes);
 
+// ERR_M = 2 beta^(M+1) / (1 + beta) (Eq. 41), the expression cpaa_l1_bound uses.
+double err_bound(double c, int M);
+
 // Host-side coefficient table c_0..c_M (Sec. 2.2, Proposition 1).
 void cheb_coeffs(double c, int M, std::vector<double> &ck);
 
 // Round launcher (step.cu): one round for a tile of `width` vectors.
 struct StepLaunch {
-    const cpaa_graph *g;
-    int precision;
-    int width;          // 1, 2, 4, 8 or 16
-    const void *y_src;  // gathered iterates y_{k-1}, [(n+1) x width]
-    void *y_io;         // in: y_{k-2} (k >= 2); out: y_k
-    void *rho;          // [n x width]
-    void *comp;         // [n x width]
-    void *long_part;    // hub tile partials [num_hub_tiles x width]
-    double *red;        // this round's [2][width][kRedSlots]
-    double ck[kMaxWidth];
-    unsigned active;    // columns that still accumulate
-    unsigned reduce;    // columns whose sums are reduced this round
-    unsigned first;     // columns in their first round (k == 1)
-    int power;          // 1: power-method round (ck[b] = c, rho holds q = (1-c) p / d)
-    int *long_cnt;      // hub ticket counters [n_hub], all zero; NULL = the graph's own
-    cudaStream_t stream;
+    const cpaa_graph *g = nullptr;
+    int precision = CPAA_F64;
+    int width = 1;                  // 1, 2, 4, 8 or 16
+    const void *y_src = nullptr;    // gathered iterates y_{k-1}, [(n+1) x width]
+    void *y_io = nullptr;           // in: y_{k-2} (k >= 2); out: y_k
+    void *rho = nullptr;            // [n x width]
+    void *comp = nullptr;           // [n x width]
+    void *long_part = nullptr;      // hub tile partials [num_hub_tiles x width]
+    double *ipart = nullptr;        // item partial sums (reducing rounds)
+    double *ipart2 = nullptr;       // first-level sums [kSumBlocks][2][width]
+    double *red = nullptr;          // this round's sums [2][width]
+    const unsigned *stop = nullptr; // stopped columns (a-posteriori rule), or NULL
+    StopArgs sa;                    // the rule's test after this round (sa.decide == 0: none)
+    double ck[kMaxWidth] = {};
+    unsigned active = 0;            // columns that still accumulate
+    unsigned reduce = 0;            // nonzero: take this round's sums
+    unsigned first = 0;             // columns in their first round (k == 1)
+    int power = 0;                  // 1: power-method round (ck[b] = c, rho holds q = (1-c) p / d)
+    int *long_cnt = nullptr;        // hub ticket counters [n_hub], all zero; NULL = the graph's own
+    cudaStream_t stream = nullptr;
 };
+void prepare_step(int precision, int width);
 cudaError_t launch_step(const StepLaunch &s);
 
 // Solve pieces (solve.cu), shared by cpaa_solve and cpaa_solve_batch.

@@ -17,6 +17,15 @@
 // At most kInFlight rounds per graph are queued ahead of the device, so new
 // queries join quickly.  Each column's arithmetic is the same whatever the
 // other columns hold, so a result is bit-identical alone and in a mix.
+//
+// With the a-posteriori stopping rule every round also takes its per-column
+// sums and tests the rule on the device (step.cu); a column that passes stops
+// accumulating at once.  After each round a one-warp kernel writes the stop
+// state to mapped host memory, and the scheduler, which reads it when the
+// round's event completes (a lag of at most kInFlight rounds), finalises the
+// column.
+// The rule's decision uses only that column's sums, so it too is the same
+// alone and in a mix.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -43,10 +52,19 @@ __device__ __forceinline__ double sget(const double *p) { return *p; }
 __device__ __forceinline__ double sget(const float *p) { return (double)*p; }
 __device__ __forceinline__ double sget(const __nv_bfloat16 *p) { return (double)__bfloat162float(*p); }
 
+// Stop state of a graph's columns under the a-posteriori rule (device, and
+// pinned host copies of it).
+struct DevStop {
+    unsigned stop;                // stopped columns
+    int round[kMaxWidth];         // the round a column stopped after (-1: running)
+    double maxl1[kMaxWidth];      // running max of ||T_j p||_1
+};
+
 struct SeedArgs {
     int count;
     int col;
     double c0half;
+    double l1;                    // ||p||_1, the rule's starting max
     int32_t r[CPAA_SERVER_MAX_SEEDS];  // new ids
     double w[CPAA_SERVER_MAX_SEEDS];
 };
@@ -63,9 +81,23 @@ __global__ void slot_zero_kernel(S *y0, R *rho, R *comp, int64_t n, int b) {
     }
 }
 
+// Copy the stop state into mapped host memory (read by the host once an
+// event after this kernel has completed).
+__global__ void copy_stop_kernel(const DevStop *__restrict__ src, DevStop *dst) {
+    const unsigned *s = reinterpret_cast<const unsigned *>(src);
+    unsigned *d = reinterpret_cast<unsigned *>(dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(DevStop) / 4); i += blockDim.x) d[i] = s[i];
+}
+
 template <class S, class R, int W>
-__global__ void slot_seed_kernel(const SeedArgs a, const double *__restrict__ inv64, S *y0, R *rho) {
+__global__ void slot_seed_kernel(const SeedArgs a, const double *__restrict__ inv64, S *y0, R *rho,
+                                 DevStop *ds) {
     const int i = threadIdx.x;
+    if (i == 0 && ds) {  // the column starts running under the a-posteriori rule
+        ds->stop &= ~(1u << a.col);
+        ds->round[a.col] = -1;
+        ds->maxl1[a.col] = a.l1;
+    }
     if (i < a.count) {
         const int64_t u = a.r[i];
         sput(y0 + u * W + a.col, __dmul_rn(a.w[i], inv64[u]));
@@ -127,6 +159,8 @@ struct Request {
     double c = 0, tol = 0, kappa = 0;
     int M = 0;
     bool notconv = false;
+    bool by_posteriori = false;  // stopped by the a-posteriori rule at round M
+    double maxl1 = 0;            // that rule's running max at the stop
     enum State { PENDING, RUNNING, DONE, CANCELLED } state = PENDING;
     bool cancel = false;
     bool collecting = false;  // cpaa_server_wait is copying the result out
@@ -145,6 +179,7 @@ struct Slot {
     SlotState st = FREE;
     std::vector<double> ck;
     cudaEvent_t done = nullptr;
+    int64_t g_admit = 0;         // the graph's round count when the query was admitted
 };
 
 struct GraphState {
@@ -161,8 +196,18 @@ struct GraphState {
     std::vector<double> deg;        // caller order
     std::vector<Slot> slots;
     std::deque<ReqP> pending;
-    int64_t G = 0;  // rounds launched
+    int64_t G = 0;       // rounds launched
+    int64_t G_seen = 0;  // rounds whose completion the scheduler has processed
     cudaEvent_t ring[kInFlight] = {};
+    // a-posteriori rule (NULL otherwise)
+    double *ipart = nullptr, *ipart2 = nullptr;
+    DevStop *dstop = nullptr;
+    // mapped host memory, written by copy_stop_kernel (no copy engine: a
+    // per-round copy would queue behind large result copies)
+    DevStop *h_ring = nullptr;  // [kInFlight]: stop state after round r at r % kInFlight
+    DevStop *h_slot = nullptr;  // [W]: stop state at each slot's finalisation
+    DevStop *d_ring = nullptr;  // device addresses of the same memory
+    DevStop *d_slot = nullptr;
 };
 
 struct Completion {
@@ -181,6 +226,7 @@ using namespace cpaa::srv;
 struct cpaa_server {
     size_t budget = 0, used = 0;
     int prec = CPAA_F32, normalize = 0, max_rounds = kDefaultMaxRounds;
+    int posteriori = 0;  // stop rule CPAA_STOP_POSTERIORI
     int device = 0;
     std::vector<std::unique_ptr<GraphState>> graphs;
     std::mutex mu;
@@ -202,11 +248,14 @@ namespace srv {
 static size_t vbytes(int prec) { return prec == CPAA_F64 ? 8 : prec == CPAA_F32 ? 4 : 2; }
 static size_t rbytes(int prec) { return prec == CPAA_F64 ? 8 : 4; }
 
-static size_t graph_bytes(const cpaa_graph *g, int prec, int W) {
+static size_t graph_bytes(const cpaa_graph *g, int prec, int W, int posteriori) {
     const size_t n = (size_t)g->n;
-    return 2 * (n + 1) * W * vbytes(prec) + 2 * n * W * rbytes(prec) + n * W * 8 +
-           (size_t)std::max(1, g->num_hub_tiles) * W * 8 + (size_t)std::max(1, g->n_hub) * 4 +
-           (size_t)kPrepBlocks * 8 + (size_t)W * 8 + 2 * kRedSlots * 8 * (size_t)W;
+    size_t b = 2 * (n + 1) * W * vbytes(prec) + 2 * n * W * rbytes(prec) + n * W * 8 +
+               (size_t)std::max(1, g->num_hub_tiles) * W * 8 + (size_t)std::max(1, g->n_hub) * 4 +
+               (size_t)kPrepBlocks * 8 + (size_t)W * 8 + 2 * 8 * (size_t)W;
+    if (posteriori)  // per-round item sums
+        b += 2 * 8 * (size_t)W * ((size_t)g->n_hub + g->num_chunks + kSumBlocks) + sizeof(DevStop);
+    return b;
 }
 
 template <class S, class R, int W>
@@ -216,7 +265,8 @@ static void launch_slot_prep(GraphState &gs, int b, const SeedArgs &a) {
     R *comp = std::is_same<R, float>::value ? (R *)gs.comp : nullptr;
     S *y0 = (S *)gs.y[gs.G & 1];  // the buffer the next round gathers from
     slot_zero_kernel<S, R, W><<<grid, 256, 0, gs.stream>>>(y0, (R *)gs.rho, comp, n, b);
-    slot_seed_kernel<S, R, W><<<1, CPAA_SERVER_MAX_SEEDS, 0, gs.stream>>>(a, gs.g->inv_deg64, y0, (R *)gs.rho);
+    slot_seed_kernel<S, R, W><<<1, CPAA_SERVER_MAX_SEEDS, 0, gs.stream>>>(a, gs.g->inv_deg64, y0, (R *)gs.rho,
+                                                                         gs.dstop);
 }
 
 template <class R, int W>
@@ -262,6 +312,49 @@ static void slot_prep(cpaa_server *s, GraphState &gs, int b, const SeedArgs &a) 
 static void slot_final(cpaa_server *s, GraphState &gs, int b, double c) {
     if (s->prec == CPAA_F64) slot_final_w<double>(gs, b, s->normalize, c);
     else slot_final_w<float>(gs, b, s->normalize, c);
+    // the column's stop state as of its finalisation (read by the completion thread)
+    if (gs.dstop) copy_stop_kernel<<<1, 64, 0, gs.stream>>>(gs.dstop, gs.d_slot + b);
+}
+
+// Queue a LIVE slot's finalisation and hand it to the completion thread
+// (caller does not hold s->mu).
+static void finish_slots(cpaa_server *s, GraphState &gs, const std::vector<int> &cols) {
+    if (cols.empty()) return;
+    std::vector<Completion> done;
+    for (int b : cols) {
+        Slot &slot = gs.slots[b];
+        slot_final(s, gs, b, slot.req->c);
+        cudaEventRecord(slot.done, gs.stream);
+        done.push_back({&gs, b, slot.req, false});
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (auto &c : done) {
+        gs.slots[c.slot].st = FINISHING;
+        s->comps.push_back(c);
+    }
+    s->cv_comp.notify_one();
+}
+
+// Rounds that completed since the last pass: under the a-posteriori rule, the
+// columns they stopped are finalised now.  A view counts for a slot only if it
+// was taken after the slot's query was admitted (its prep reset the column).
+static void process_completed_rounds(cpaa_server *s, GraphState &gs) {
+    std::vector<int> stopped;
+    while (gs.G_seen < gs.G) {
+        const int64_t r = gs.G_seen + 1;
+        if (cudaEventQuery(gs.ring[r % kInFlight]) != cudaSuccess) break;
+        if (gs.h_ring) {
+            const DevStop &v = gs.h_ring[r % kInFlight];
+            for (int b = 0; b < gs.W; ++b) {
+                const Slot &sl = gs.slots[b];
+                if (sl.st == LIVE && (v.stop >> b & 1u) && r > sl.g_admit &&
+                    std::find(stopped.begin(), stopped.end(), b) == stopped.end())
+                    stopped.push_back(b);
+            }
+        }
+        gs.G_seen = r;
+    }
+    finish_slots(s, gs, stopped);
 }
 
 static double us_since(clk::time_point a, clk::time_point b) {
@@ -270,9 +363,10 @@ static double us_since(clk::time_point a, clk::time_point b) {
 
 // One scheduling pass over a graph; true if anything was launched.
 static bool step_graph(cpaa_server *s, GraphState &gs) {
-    // at most kInFlight rounds queued: launch G+1 waits for launch G+1-kInFlight
-    if (gs.G + 1 > kInFlight && cudaEventQuery(gs.ring[(gs.G + 1) % kInFlight]) == cudaErrorNotReady)
-        return false;
+    process_completed_rounds(s, gs);
+    // at most kInFlight rounds queued: launch G+1 waits until round G+1-kInFlight
+    // has completed and been processed (its ring entry is then free)
+    if (gs.G + 1 > kInFlight && gs.G_seen < gs.G + 1 - kInFlight) return false;
     std::vector<std::pair<int, SeedArgs>> admitted;
     unsigned live = 0;
     {
@@ -309,6 +403,7 @@ static bool step_graph(cpaa_server *s, GraphState &gs) {
                 sl.req = r;
                 sl.k = 0;
                 sl.st = LIVE;
+                sl.g_admit = gs.G;
                 cheb_coeffs(r->c, r->M, sl.ck);
                 r->state = Request::RUNNING;
                 r->t_admit = now;
@@ -365,27 +460,37 @@ static bool step_graph(cpaa_server *s, GraphState &gs) {
         sl.ck[b] = gs.slots[b].ck[k];
         if (k == 1) sl.first |= 1u << b;
     }
+    if (gs.dstop) {
+        // every round takes its sums and tests the a-posteriori rule
+        sl.ipart = gs.ipart;
+        sl.ipart2 = gs.ipart2;
+        sl.reduce = live;
+        sl.stop = &gs.dstop->stop;
+        sl.sa.decide = live;
+        for (int b = 0; b < gs.W; ++b) {
+            if (!(live >> b & 1u)) continue;
+            const Slot &slot = gs.slots[b];
+            sl.sa.k[b] = slot.k + 1;
+            sl.sa.err[b] = err_bound(slot.req->c, slot.k + 1);
+            sl.sa.tol[b] = slot.req->tol;
+        }
+        sl.sa.normalize = s->normalize;
+        sl.sa.maxl1 = gs.dstop->maxl1;
+        sl.sa.stop = &gs.dstop->stop;
+        sl.sa.stop_round = gs.dstop->round;
+    }
     if (launch_step(sl) != cudaSuccess) return false;
-    ++gs.G;
+    const int64_t Gn = gs.G + 1;
+    if (gs.dstop)
+        copy_stop_kernel<<<1, 64, 0, gs.stream>>>(gs.dstop, gs.d_ring + Gn % kInFlight);
+    gs.G = Gn;
     cudaEventRecord(gs.ring[gs.G % kInFlight], gs.stream);
-    std::vector<Completion> done;
+    std::vector<int> due;
     for (int b = 0; b < gs.W; ++b) {
         if (!(live >> b & 1u)) continue;
-        Slot &slot = gs.slots[b];
-        if (++slot.k == slot.req->M) {
-            slot_final(s, gs, b, slot.req->c);
-            cudaEventRecord(slot.done, gs.stream);
-            done.push_back({&gs, b, slot.req, false});
-        }
+        if (++gs.slots[b].k == gs.slots[b].req->M) due.push_back(b);
     }
-    if (!done.empty()) {
-        std::lock_guard<std::mutex> lk(s->mu);
-        for (auto &c : done) {
-            gs.slots[c.slot].st = FINISHING;
-            s->comps.push_back(c);
-        }
-        s->cv_comp.notify_one();
-    }
+    finish_slots(s, gs, due);
     return true;
 }
 
@@ -453,6 +558,15 @@ static void completion_main(cpaa_server *s) {
         std::lock_guard<std::mutex> lk(s->mu);
         const auto now = clk::now();
         c.req->t_done = now;
+        if (e == cudaSuccess && gs.h_slot) {
+            const DevStop &v = gs.h_slot[c.slot];
+            if ((v.stop >> c.slot & 1u) && v.round[c.slot] >= 1 && v.round[c.slot] <= c.req->M) {
+                c.req->M = v.round[c.slot];
+                c.req->by_posteriori = true;
+                c.req->maxl1 = v.maxl1[c.slot];
+                c.req->notconv = false;
+            }
+        }
         if (e == cudaSuccess) {
             c.req->state = Request::DONE;
             c.req->gs = &gs;
@@ -486,6 +600,9 @@ static void release_slot(cpaa_server *s, Request &r) {
 static void free_graph_state(GraphState &gs) {
     cudaFree(gs.y[0]); cudaFree(gs.y[1]); cudaFree(gs.rho); cudaFree(gs.comp); cudaFree(gs.long_part);
     cudaFree(gs.long_cnt); cudaFree(gs.red); cudaFree(gs.result); cudaFree(gs.part); cudaFree(gs.sums);
+    cudaFree(gs.ipart); cudaFree(gs.ipart2); cudaFree(gs.dstop);
+    if (gs.h_ring) cudaFreeHost(gs.h_ring);
+    if (gs.h_slot) cudaFreeHost(gs.h_slot);
     for (auto &e : gs.ring) if (e) cudaEventDestroy(e);
     for (auto &sl : gs.slots) if (sl.done) cudaEventDestroy(sl.done);
     if (gs.stream) cudaStreamDestroy(gs.stream);
@@ -515,7 +632,10 @@ extern "C" cpaa_status cpaa_server_create(size_t device_mem_budget, const cpaa_o
     if (o.precision != CPAA_F64 && o.precision != CPAA_F32 && o.precision != CPAA_BF16)
         return fail(CPAA_EINVAL, "unknown precision");
     if (o.normalize != 0 && o.normalize != 1) return fail(CPAA_EINVAL, "normalize must be 0 or 1");
+    if (o.stop_rule != CPAA_STOP_RIGOROUS && o.stop_rule != CPAA_STOP_POSTERIORI)
+        return fail(CPAA_EINVAL, "unknown stop_rule");
     cpaa_server *s = new cpaa_server();
+    s->posteriori = o.stop_rule == CPAA_STOP_POSTERIORI;
     s->budget = device_mem_budget;
     s->prec = o.precision;
     s->normalize = o.normalize;
@@ -540,7 +660,7 @@ extern "C" cpaa_status cpaa_server_add_graph(cpaa_server *s, cpaa_graph *g, int 
     while (W & (W - 1)) --W;
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        while (W >= 1 && s->used + graph_bytes(g, s->prec, W) > s->budget) W /= 2;
+        while (W >= 1 && s->used + graph_bytes(g, s->prec, W, s->posteriori) > s->budget) W /= 2;
         if (W < 1) return fail(CPAA_ENOMEM, "device memory budget too small for one slot of this graph");
     }
     auto gs = std::make_unique<GraphState>();
@@ -568,13 +688,23 @@ extern "C" cpaa_status cpaa_server_add_graph(cpaa_server *s, cpaa_graph *g, int 
         SALLOC(gs->comp, rb);
         SALLOC(gs->long_part, (size_t)std::max(1, g->num_hub_tiles) * W * 8);
         SALLOC(gs->long_cnt, (size_t)std::max(1, g->n_hub) * 4);
-        SALLOC(gs->red, 2 * kRedSlots * 8 * (size_t)W);
+        SALLOC(gs->red, 2 * 8 * (size_t)W);
         SALLOC(gs->result, (size_t)n * W * 8);
         SALLOC(gs->part, (size_t)kPrepBlocks * 8);
         SALLOC(gs->sums, (size_t)W * 8);
         SCK(cudaMemsetAsync(gs->y[0], 0, vb, gs->stream));
         SCK(cudaMemsetAsync(gs->y[1], 0, vb, gs->stream));
         SCK(cudaMemsetAsync(gs->long_cnt, 0, (size_t)std::max(1, g->n_hub) * 4, gs->stream));
+        if (s->posteriori) {
+            SALLOC(gs->ipart, 2 * 8 * (size_t)W * ((size_t)g->n_hub + g->num_chunks));
+            SALLOC(gs->ipart2, 2 * 8 * (size_t)W * kSumBlocks);
+            SALLOC(gs->dstop, sizeof(DevStop));
+            SCK(cudaMemsetAsync(gs->dstop, 0, sizeof(DevStop), gs->stream));
+            SCK(cudaHostAlloc((void **)&gs->h_ring, sizeof(DevStop) * kInFlight, cudaHostAllocMapped));
+            SCK(cudaHostAlloc((void **)&gs->h_slot, sizeof(DevStop) * W, cudaHostAllocMapped));
+            SCK(cudaHostGetDevicePointer((void **)&gs->d_ring, gs->h_ring, 0));
+            SCK(cudaHostGetDevicePointer((void **)&gs->d_slot, gs->h_slot, 0));
+        }
         for (auto &e : gs->ring) SCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         gs->slots.resize(W);
         for (auto &sl : gs->slots) SCK(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
@@ -590,7 +720,7 @@ extern "C" cpaa_status cpaa_server_add_graph(cpaa_server *s, cpaa_graph *g, int 
             gs->deg[perm[r]] = deg[r];
         }
         SCK(cudaStreamSynchronize(gs->stream));
-        gs->bytes = graph_bytes(g, s->prec, W);
+        gs->bytes = graph_bytes(g, s->prec, W, s->posteriori);
         std::lock_guard<std::mutex> lk(s->mu);
         gs->id = (int)s->graphs.size();
         s->used += gs->bytes;
@@ -639,6 +769,7 @@ extern "C" cpaa_status cpaa_server_submit(cpaa_server *s, int graph_id, int nsee
         q += w * w / gs->deg[v];
     }
     if (!(std::fabs(sumw - 1.0) <= 1e-9)) return fail(CPAA_EINVAL, "weights must sum to 1");
+    r->seeds.l1 = sumw;
     r->kappa = std::sqrt((double)gs->g->nnz) * std::sqrt(q);
     r->M = cpaa_rounds_needed(c, tol, r->kappa, s->normalize, s->max_rounds);
     if (r->M < 0) {
@@ -701,7 +832,8 @@ extern "C" cpaa_status cpaa_server_wait(cpaa_server *s, uint64_t ticket, double 
     if (info) {
         info->rounds = r->M;
         info->kappa = r->kappa;
-        info->bound = cpaa_l1_bound(r->c, r->M, r->kappa, s->normalize);
+        info->bound = r->by_posteriori ? cpaa_l1_bound(r->c, r->M, 2.0 * r->maxl1, s->normalize)
+                                       : cpaa_l1_bound(r->c, r->M, r->kappa, s->normalize);
         info->mass = info->l1 = info->sum_pibar = std::numeric_limits<double>::quiet_NaN();  // not reduced when serving
         info->rounds_ms = 0.0;
     }

@@ -153,7 +153,23 @@ cpaa_status ensure_reduction_buffers(cpaa_graph *g) {
     return CPAA_OK;
 }
 
+static cpaa_status ensure_workspace_buffers(cpaa_graph *g, int prec, int width, int max_rounds);
+
+// Sizes the workspace; captured round graphs refer to its buffers, so they
+// are dropped when any buffer moves.
 cpaa_status ensure_workspace(cpaa_graph *g, int prec, int width, int max_rounds) {
+    Workspace &w = g->ws;
+    const void *before[] = {w.y0, w.y1, w.rho, w.comp, w.red, w.long_part, w.ipart, w.ipart2, w.maxl1};
+    const cpaa_status st = ensure_workspace_buffers(g, prec, width, max_rounds);
+    const void *after[] = {w.y0, w.y1, w.rho, w.comp, w.red, w.long_part, w.ipart, w.ipart2, w.maxl1};
+    if (std::memcmp(before, after, sizeof before) != 0) {
+        for (auto &rg : w.round_graphs) cudaGraphExecDestroy(rg.exec);
+        w.round_graphs.clear();
+    }
+    return st;
+}
+
+static cpaa_status ensure_workspace_buffers(cpaa_graph *g, int prec, int width, int max_rounds) {
     Workspace &w = g->ws;
     const int64_t n = g->n;
     cpaa_status st;
@@ -175,12 +191,26 @@ cpaa_status ensure_workspace(cpaa_graph *g, int prec, int width, int max_rounds)
         if ((st = dev_alloc(g, &w.comp, rb)) != CPAA_OK) return st;
         w.rho_bytes = rb;
     }
-    const size_t red = sizeof(double) * 2 * kRedSlots * (size_t)width * (max_rounds + 1);
+    const size_t red = sizeof(double) * 2 * (size_t)width * (max_rounds + 1);
     if (w.red_bytes < red) {
         dev_free(g, (void **)&w.red, w.red_bytes);
         w.red_bytes = 0;
         if ((st = dev_alloc(g, (void **)&w.red, red)) != CPAA_OK) return st;
         w.red_bytes = red;
+    }
+    const size_t ip = sizeof(double) * 2 * (size_t)width * ((size_t)g->n_hub + g->num_chunks);
+    if (w.ipart_bytes < ip) {
+        dev_free(g, (void **)&w.ipart, w.ipart_bytes);
+        w.ipart_bytes = 0;
+        if ((st = dev_alloc(g, (void **)&w.ipart, ip)) != CPAA_OK) return st;
+        w.ipart_bytes = ip;
+    }
+    if (!w.ipart2) {
+        if ((st = dev_alloc(g, (void **)&w.ipart2, sizeof(double) * 2 * kMaxWidth * kSumBlocks)) != CPAA_OK)
+            return st;
+        if ((st = dev_alloc(g, (void **)&w.maxl1, sizeof(double) * kMaxWidth)) != CPAA_OK) return st;
+        if ((st = dev_alloc(g, (void **)&w.stop, sizeof(unsigned))) != CPAA_OK) return st;
+        if ((st = dev_alloc(g, (void **)&w.stop_round, sizeof(int) * kMaxWidth)) != CPAA_OK) return st;
     }
     const size_t lp = sizeof(double) * std::max(1, g->num_hub_tiles) * (size_t)width;
     if (w.long_part_bytes < lp) {
@@ -265,30 +295,13 @@ static cudaError_t tile_phase(cpaa_graph *g, const TileJob &job, cudaStream_t st
     return cudaErrorInvalidValue;
 }
 
-// Prep, the rounds and the finalisation of one tile (workspace must be sized).
-// rounds_ms (if not NULL) receives the device time of the round launches.
-cpaa_status run_tile(cpaa_graph *g, const TileJob &job, cudaStream_t st, bool history_all_rounds,
-                     float *rounds_ms) {
+// The M round launches of a tile on stream st.
+static cudaError_t launch_rounds(cpaa_graph *g, const TileJob &job, bool history_all_rounds, int maxM,
+                                 cudaStream_t st) {
     Workspace &w = g->ws;
-    const int64_t n = g->n;
     const int W = job.width;
-    int maxM = 0;
-    for (int b = 0; b < W; ++b) maxM = std::max(maxM, job.rounds[b]);
-    const size_t vb = store_bytes(job.precision) * (size_t)W;
-    CPAA_CUDA(cudaMemsetAsync(w.red, 0, sizeof(double) * 2 * kRedSlots * W * (size_t)(maxM + 1), st));
-    CPAA_CUDA(cudaMemsetAsync(g->long_cnt, 0, sizeof(int) * std::max(1, g->n_hub), st));
-    CPAA_CUDA(cudaMemsetAsync((char *)w.y0 + vb * n, 0, vb, st));  // sentinel row n
-    CPAA_CUDA(cudaMemsetAsync((char *)w.y1 + vb * n, 0, vb, st));
-    CPAA_CUDA(tile_phase(g, job, st, 0));
-
     std::vector<std::vector<double>> ck(W);
     for (int b = 0; b < W; ++b) cheb_coeffs(job.c[b], job.rounds[b], ck[b]);
-    cudaEvent_t ev[2] = {nullptr, nullptr};
-    if (rounds_ms) {
-        CPAA_CUDA(cudaEventCreate(&ev[0]));
-        CPAA_CUDA(cudaEventCreate(&ev[1]));
-        CPAA_CUDA(cudaEventRecord(ev[0], st));
-    }
     void *buf[2] = {w.y0, w.y1};
     for (int k = 1; k <= maxM; ++k) {
         StepLaunch sl;
@@ -300,7 +313,9 @@ cpaa_status run_tile(cpaa_graph *g, const TileJob &job, cudaStream_t st, bool hi
         sl.rho = w.rho;
         sl.comp = w.comp;
         sl.long_part = w.long_part;
-        sl.red = w.red + (size_t)k * 2 * W * kRedSlots;
+        sl.ipart = w.ipart;
+        sl.ipart2 = w.ipart2;
+        sl.red = w.red + (size_t)k * 2 * W;
         sl.active = 0;
         sl.reduce = 0;
         for (int b = 0; b < kMaxWidth; ++b) sl.ck[b] = 0.0;
@@ -311,12 +326,122 @@ cpaa_status run_tile(cpaa_graph *g, const TileJob &job, cudaStream_t st, bool hi
             }
             if (k == job.rounds[b] || (history_all_rounds && k <= job.rounds[b])) sl.reduce |= 1u << b;
         }
+        if (job.posteriori) {
+            // every round takes its sums; columns still within their
+            // rigorous M test the a-posteriori rule after it
+            sl.stop = w.stop;
+            sl.sa.decide = sl.active;
+            for (int b = 0; b < W; ++b) {
+                sl.sa.k[b] = k;
+                sl.sa.err[b] = err_bound(job.c[b], k);
+                sl.sa.tol[b] = job.tol;
+            }
+            sl.sa.normalize = job.normalize;
+            sl.sa.maxl1 = w.maxl1;
+            sl.sa.stop = w.stop;
+            sl.sa.stop_round = w.stop_round;
+            sl.reduce |= sl.active;
+        }
         sl.first = (k == 1) ? (1u << W) - 1u : 0u;
         sl.power = job.power;
         sl.long_cnt = nullptr;
         sl.stream = st;
-        CPAA_CUDA(launch_step(sl));
+        const cudaError_t e = launch_step(sl);
+        if (e != cudaSuccess) return e;
     }
+    return cudaSuccess;
+}
+
+constexpr size_t kMaxRoundGraphs = 8;
+
+// The round sequence of a tile as an instantiated CUDA graph: found in the
+// graph's cache, or captured on the private stream and added to it.  The key
+// holds everything the launches read (buffers, widths, coefficients' inputs,
+// masks), so a replay issues exactly the launches launch_rounds would.
+static cpaa_status round_graph(cpaa_graph *g, const TileJob &job, bool history_all_rounds, int maxM,
+                               cudaGraphExec_t *out) {
+    Workspace &w = g->ws;
+    uint64_t tolb;
+    std::memcpy(&tolb, &job.tol, sizeof tolb);
+    std::vector<uint64_t> key = {(uint64_t)job.precision, (uint64_t)job.width, (uint64_t)job.power,
+                                 (uint64_t)history_all_rounds, (uint64_t)maxM, (uint64_t)job.posteriori,
+                                 job.posteriori ? tolb : 0, (uint64_t)job.normalize,
+                                 (uint64_t)(uintptr_t)w.y0, (uint64_t)(uintptr_t)w.y1,
+                                 (uint64_t)(uintptr_t)w.rho, (uint64_t)(uintptr_t)w.comp,
+                                 (uint64_t)(uintptr_t)w.long_part, (uint64_t)(uintptr_t)w.red,
+                                 (uint64_t)(uintptr_t)w.ipart, (uint64_t)(uintptr_t)w.maxl1};
+    for (int b = 0; b < job.width; ++b) {
+        uint64_t cb;
+        std::memcpy(&cb, &job.c[b], sizeof cb);
+        key.push_back(cb);
+        key.push_back((uint64_t)job.rounds[b]);
+    }
+    for (auto &rg : w.round_graphs)
+        if (rg.key == key) {
+            *out = rg.exec;
+            return CPAA_OK;
+        }
+    if (!w.capture) CPAA_CUDA(cudaStreamCreateWithFlags(&w.capture, cudaStreamNonBlocking));
+    prepare_step(job.precision, job.width);
+    CPAA_CUDA(cudaStreamBeginCapture(w.capture, cudaStreamCaptureModeThreadLocal));
+    const cudaError_t le = launch_rounds(g, job, history_all_rounds, maxM, w.capture);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(w.capture, &graph);
+    if (le != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(le, "round launch during capture");
+    }
+    CPAA_CUDA(ce);
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CPAA_CUDA(ie);
+    if (w.round_graphs.size() >= kMaxRoundGraphs) {
+        cudaGraphExecDestroy(w.round_graphs.front().exec);
+        w.round_graphs.erase(w.round_graphs.begin());
+    }
+    w.round_graphs.push_back({std::move(key), exec});
+    *out = exec;
+    return CPAA_OK;
+}
+
+// Prep, the rounds and the finalisation of one tile (workspace must be sized).
+// rounds_ms (if not NULL) receives the device time of the round launches.
+cpaa_status run_tile(cpaa_graph *g, const TileJob &job, cudaStream_t st, bool history_all_rounds,
+                     float *rounds_ms) {
+    Workspace &w = g->ws;
+    const int64_t n = g->n;
+    const int W = job.width;
+    int maxM = 0;
+    for (int b = 0; b < W; ++b) maxM = std::max(maxM, job.rounds[b]);
+    const size_t vb = store_bytes(job.precision) * (size_t)W;
+    CPAA_CUDA(cudaMemsetAsync(w.red, 0, sizeof(double) * 2 * W * (size_t)(maxM + 1), st));
+    if (job.posteriori) {
+        // the running max of ||T_j p||_1 starts at j = 0 (||p||_1); no column
+        // has stopped
+        CPAA_CUDA(cudaMemcpyAsync(w.maxl1, job.p_l1, sizeof(double) * W, cudaMemcpyHostToDevice, st));
+        CPAA_CUDA(cudaMemsetAsync(w.stop, 0, sizeof(unsigned), st));
+        CPAA_CUDA(cudaMemsetAsync(w.stop_round, 0xff, sizeof(int) * kMaxWidth, st));
+        // the copy reads the caller's job, which ends with this call
+        CPAA_CUDA(cudaStreamSynchronize(st));
+    }
+    CPAA_CUDA(cudaMemsetAsync(g->long_cnt, 0, sizeof(int) * std::max(1, g->n_hub), st));
+    CPAA_CUDA(cudaMemsetAsync((char *)w.y0 + vb * n, 0, vb, st));  // sentinel row n
+    CPAA_CUDA(cudaMemsetAsync((char *)w.y1 + vb * n, 0, vb, st));
+    CPAA_CUDA(tile_phase(g, job, st, 0));
+
+    cudaGraphExec_t exec = nullptr;
+    if (maxM > 0) {
+        cpaa_status s = round_graph(g, job, history_all_rounds, maxM, &exec);
+        if (s != CPAA_OK) return s;
+    }
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (rounds_ms) {
+        CPAA_CUDA(cudaEventCreate(&ev[0]));
+        CPAA_CUDA(cudaEventCreate(&ev[1]));
+        CPAA_CUDA(cudaEventRecord(ev[0], st));
+    }
+    if (exec) CPAA_CUDA(cudaGraphLaunch(exec, st));
     if (rounds_ms) {
         CPAA_CUDA(cudaEventRecord(ev[1], st));
         CPAA_CUDA(cudaEventSynchronize(ev[1]));
@@ -324,6 +449,7 @@ cpaa_status run_tile(cpaa_graph *g, const TileJob &job, cudaStream_t st, bool hi
         cudaEventDestroy(ev[0]);
         cudaEventDestroy(ev[1]);
     }
+    void *buf[2] = {w.y0, w.y1};
     CPAA_CUDA(tile_phase(g, job, st, 1, job.power ? buf[maxM & 1] : nullptr));
     return CPAA_OK;
 }
@@ -331,13 +457,8 @@ cpaa_status run_tile(cpaa_graph *g, const TileJob &job, cudaStream_t st, bool hi
 // Sums of column b (of a tile of `width`) in round k from the host copy h of
 // the reduction slots.
 void round_sums(int width, int b, int k, const std::vector<double> &h, double *sumT, double *sumA) {
-    double a = 0, c = 0;
-    for (int i = 0; i < kRedSlots; ++i) {
-        a += h[(((size_t)k * 2 + 0) * width + b) * kRedSlots + i];
-        c += h[(((size_t)k * 2 + 1) * width + b) * kRedSlots + i];
-    }
-    *sumT = a;
-    *sumA = c;
+    *sumT = h[((size_t)k * 2 + 0) * width + b];
+    *sumA = h[((size_t)k * 2 + 1) * width + b];
 }
 
 }  // namespace cpaa
@@ -369,6 +490,10 @@ static cpaa_status solve_one(cpaa_graph *g, const double *p, double c, double to
         return fail(CPAA_EINVAL, "unknown precision");
     if (power && opt.precision == CPAA_BF16) return fail(CPAA_EINVAL, "the power method runs in FP64 or FP32");
     if (opt.normalize != 0 && opt.normalize != 1) return fail(CPAA_EINVAL, "normalize must be 0 or 1");
+    if (opt.stop_rule != CPAA_STOP_RIGOROUS && opt.stop_rule != CPAA_STOP_POSTERIORI)
+        return fail(CPAA_EINVAL, "unknown stop_rule");
+    if (power && opt.stop_rule != CPAA_STOP_RIGOROUS)
+        return fail(CPAA_EINVAL, "the power method has its own stopping rule (2 c^T < tol)");
     const int max_rounds = opt.max_rounds > 0 ? opt.max_rounds : kDefaultMaxRounds;
     if (opt.fixed_rounds > max_rounds) return fail(CPAA_EINVAL, "fixed_rounds > max_rounds");
     const bool host_io = (opt.flags & CPAA_DEVICE_IO) == 0;
@@ -419,6 +544,10 @@ static cpaa_status solve_one(cpaa_graph *g, const double *p, double c, double to
     job.c0half[0] = power ? 1.0 - c : ck0[0] / 2.0;
     job.rounds[0] = M;
     job.power = power;
+    // the a-posteriori rule may stop the rounds before the rigorous M
+    job.posteriori = opt.stop_rule == CPAA_STOP_POSTERIORI && opt.fixed_rounds == 0 && M > 0;
+    job.tol = tol;
+    job.p_l1[0] = sum_p;
     float rounds_ms = 0.0f;
     // per-round sums every round only when the caller asked for the history;
     // otherwise just the last round's (for info)
@@ -427,8 +556,19 @@ static cpaa_status solve_one(cpaa_graph *g, const double *p, double c, double to
         return s;
     if (host_io) CPAA_CUDA(cudaMemcpyAsync(pi, dpi, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
 
+    bool by_posteriori = false;
+    if (job.posteriori) {
+        int sr = -1;
+        CPAA_CUDA(cudaMemcpyAsync(&sr, w.stop_round, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CPAA_CUDA(cudaStreamSynchronize(st));
+        if (sr >= 1 && sr <= M) {
+            M = sr;
+            by_posteriori = true;
+            result = CPAA_OK;  // the estimate passed within max_rounds
+        }
+    }
     if (info || opt.history) {
-        std::vector<double> h((size_t)(M + 1) * 2 * kRedSlots);
+        std::vector<double> h((size_t)(M + 1) * 2);
         CPAA_CUDA(cudaMemcpyAsync(h.data(), w.red, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st));
         CPAA_CUDA(cudaMemcpyAsync(w.h_sums + 3, w.sums, sizeof(double), cudaMemcpyDeviceToHost, st));
         CPAA_CUDA(cudaStreamSynchronize(st));
@@ -440,7 +580,18 @@ static cpaa_status solve_one(cpaa_graph *g, const double *p, double c, double to
         if (info) {
             info->rounds = M;
             info->kappa = kappa;
-            info->bound = power ? 2.0 * std::pow(c, (double)M) : cpaa_l1_bound(c, M, kappa, opt.normalize);
+            if (power) {
+                info->bound = 2.0 * std::pow(c, (double)M);
+            } else if (by_posteriori) {
+                double ml = sum_p, t = 0, a = 0;
+                for (int k = 1; k <= M; ++k) {
+                    round_sums(1, 0, k, h, &t, &a);
+                    ml = std::max(ml, a);
+                }
+                info->bound = cpaa_l1_bound(c, M, 2.0 * ml, opt.normalize);
+            } else {
+                info->bound = cpaa_l1_bound(c, M, kappa, opt.normalize);
+            }
             if (M == 0) {
                 info->mass = info->l1 = sum_p;
             } else {

@@ -56,6 +56,11 @@ void cheb_coeffs(double c, int M, std::vector<double> &ck) {
     for (int k = 1; k <= M; ++k) ck[k] = ck[k - 1] * beta;
 }
 
+double err_bound(double c, int M) {
+    const double beta = (1.0 - std::sqrt(1.0 - c * c)) / c;
+    return 2.0 * std::pow(beta, (double)(M + 1)) / (1.0 + beta);
+}
+
 }  // namespace cpaa
 
 extern "C" {
@@ -93,8 +98,7 @@ void cpaa_options_init(cpaa_options *opt) {
 // by the sum instead (Algorithm 1) rescales by 1 / (1 - ERR_M), since every
 // T_k(P) keeps e^T p = 1; that adds at most (1 + E kappa) E / (1 - E).
 double cpaa_l1_bound(double c, int M, double kappa, int normalize) {
-    const double beta = (1.0 - std::sqrt(1.0 - c * c)) / c;
-    const double E = 2.0 * std::pow(beta, (double)(M + 1)) / (1.0 + beta);
+    const double E = cpaa::err_bound(c, M);
     if (normalize == 1) return E * kappa;
     return E * kappa + (1.0 + E * kappa) * E / (1.0 - E);
 }

@@ -16,14 +16,20 @@
 //
 // Layout: vector b of a tile is column b of a row-major [(n+1) x W] array
 // (row n is the padding sentinel, kept at zero).  Column b accumulates while
-// bit b of `active` is set; its per-round sums (the mass view of Sec. 4.1,
-// sum_u T_k[u] and sum_u |T_k[u]|) are reduced when bit b of `reduce` is set.
+// bit b of `active` is set and bit b of *stop is clear.
+//
+// Per-round sums (the mass view of Sec. 4.1: sum_u T_k[u] and sum_u |T_k[u]|)
+// are taken in rounds whose `reduce` mask is not zero.  Every work item (a hub
+// row, a SELL chunk) writes its own partial sums to a slot of its own (a
+// chunk's 32 rows by a fixed shuffle tree), and two small kernels add the
+// slots in a fixed order; so the sums, and the stopping decision taken from
+// them, are the same bits for a vector alone and in any tile.
 //
 // Work split (internal.h): a persistent grid.  CTAs first take the hub tiles
 // (one tile of a hub row each) and the long SELL chunks (more than kLongChunk
 // entries per row, split over the CTA's warps) round-robin; then every warp
 // takes short SELL chunks, one lane per row, round-robin from the
-// longest-first order.  Every sum runs in a fixed order (a lane adds its
+// longest-first order (chunk descriptors are stored in that order).  Every sum runs in a fixed order (a lane adds its
 // row's entries in CSR order, slices are added in warp order; hub tiles use
 // shuffle trees over thread-strided sums and the tiles are added in tile
 // order), so a result never depends on scheduling.
@@ -42,27 +48,27 @@ struct StepParams {
     // hub rows
     const int4 *hub_tiles;
     int num_hub_tiles;
+    int hub_tile;  // entries per hub tile
     const int32_t *hub_row_ptr;
     const int32_t *hub_col;
     A *long_part;  // [num_hub_tiles][W]
     int *long_cnt;
     // SELL chunks
     const int32_t *sell_col;
-    const int64_t *chunk_off;
-    const int32_t *chunk_len;
-    const int32_t *chunk_order;
+    const int4 *chunk_desc;  // {chunk, offset / 128, length, 0}, longest first
     int num_chunks;
-    int num_long_chunks;  // chunk_order[0, num_long_chunks) take one CTA each
+    int num_long_chunks;  // chunk_desc[0, num_long_chunks) take one CTA each
     int n_hub;
     int64_t n;
     // vectors (new order)
     const A *deg;
-    const A *inv_deg;
+    const A *inv_deg;  // 2 / d for Chebyshev rounds, 1 / d for power-method rounds
     const S *y_src;  // [(n+1) x W]
     S *y_io;         // [(n+1) x W]
     R *rho;          // [n x W]
     R *comp;         // [n x W]
-    double *red;     // this round's [2][W][kRedSlots]
+    double *ipart;   // item partial sums [(n_hub + num_chunks)][2][W] (reducing rounds)
+    const unsigned *stop;  // columns stopped by the a-posteriori rule, or NULL
     A ck[W];
     unsigned active;
     unsigned reduce;
@@ -182,8 +188,8 @@ template <int P, int W>
 __device__ __forceinline__ void row_finish(const StepParams<P, W> &p, int64_t r,
                                            const typename Prec<P>::A (&s)[W],
                                            typename Prec<P>::A inv, typename Prec<P>::A d,
-                                           RowOps<P, W> &o, typename Prec<P>::A (&sT)[W],
-                                           typename Prec<P>::A (&sA)[W]) {
+                                           RowOps<P, W> &o, typename Prec<P>::A (&tT)[W],
+                                           typename Prec<P>::A (&tA)[W], unsigned active) {
     using S = typename Prec<P>::S;
     using A = typename Prec<P>::A;
     using R = typename Prec<P>::R;
@@ -195,8 +201,8 @@ __device__ __forceinline__ void row_finish(const StepParams<P, W> &p, int64_t r,
             const A y = power_iterate<P>(s[b], inv, p.ck[b], o.rr[b]);
             store_y(&ys[b], y);
             const A T = y * d;
-            sT[b] += T;
-            sA[b] += (T < A(0) ? -T : T);
+            tT[b] = T;
+            tA[b] = (T < A(0) ? -T : T);
         }
         store_row<S, W>(p.y_io + r * W, ys, false);
         return;
@@ -205,35 +211,32 @@ __device__ __forceinline__ void row_finish(const StepParams<P, W> &p, int64_t r,
     for (int b = 0; b < W; ++b) {
         const A y = new_iterate<P>(s[b], inv, o.y_old[b], (p.first >> b) & 1u);
         store_y(&ys[b], y);
-        if (p.active >> b & 1u) accumulate<P>(o.rr[b], o.cmp[b], p.ck[b], y);
+        if (active >> b & 1u) accumulate<P>(o.rr[b], o.cmp[b], p.ck[b], y);
         const A T = y * d;
-        sT[b] += T;
-        sA[b] += (T < A(0) ? -T : T);
+        tT[b] = T;
+        tA[b] = (T < A(0) ? -T : T);
     }
     store_row<S, W>(p.y_io + r * W, ys, false);
     store_row<R, W>(p.rho + r * W, o.rr, true);
     if constexpr (Prec<P>::kKahan) store_row<R, W>(p.comp + r * W, o.cmp, true);
 }
 
-// Add the per-thread sums of the columns in `reduce` to this round's slots:
-// a shuffle tree per warp, then one atomic per warp and column (no barrier, so
-// a warp that runs out of work never waits for the others).
+// A chunk's partial sums: the 32 rows' T and |T| added by a fixed shuffle
+// tree, written by lane 0 to item slot `item` (all W columns).
 template <class A, int W>
-__device__ __forceinline__ void warp_reduce_add(const A (&sT)[W], const A (&sA)[W], unsigned reduce,
-                                                double *red) {
-    const int l = threadIdx.x & 31;
-    const int slot = (int)((blockIdx.x * (unsigned)kWarps + (threadIdx.x >> 5)) % kRedSlots);
+__device__ __forceinline__ void warp_item_sums(A (&tT)[W], A (&tA)[W], double *ipart, int64_t item) {
 #pragma unroll
-    for (int b = 0; b < W; ++b) {
-        if (!(reduce >> b & 1u)) continue;  // uniform over the grid
-        double a = (double)sT[b], c = (double)sA[b];
+    for (int b = 0; b < W; ++b)
         for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_xor_sync(0xffffffffu, a, o);
-            c += __shfl_xor_sync(0xffffffffu, c, o);
+            tT[b] += __shfl_xor_sync(0xffffffffu, tT[b], o);
+            tA[b] += __shfl_xor_sync(0xffffffffu, tA[b], o);
         }
-        if (l == 0) {
-            atomicAdd(red + (0 * W + b) * kRedSlots + slot, a);
-            atomicAdd(red + (1 * W + b) * kRedSlots + slot, c);
+    if ((threadIdx.x & 31) == 0) {
+        double *d = ipart + item * 2 * W;
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            d[b] = (double)tT[b];
+            d[W + b] = (double)tA[b];
         }
     }
 }
@@ -260,21 +263,20 @@ __device__ __forceinline__ void cta_sum_w(A (&v)[W], A (&s_w)[kWarps][W]) {
         }
 }
 
-// One hub tile (kHubTileEntries entries of a hub row) by one CTA.  The CTA
+// One hub tile (p.hub_tile entries of a hub row) by one CTA.  The CTA
 // that takes the row's last ticket adds the tile partials in tile order and
 // writes the row (an atomic ticket: no CTA waits for another).
 template <int P, int W>
-__device__ __forceinline__ void hub_tile(const StepParams<P, W> &p, int4 t, typename Prec<P>::A (&sT)[W],
-                                         typename Prec<P>::A (&sA)[W]) {
+__device__ __forceinline__ void hub_tile(const StepParams<P, W> &p, int4 t, unsigned active) {
     using A = typename Prec<P>::A;
     __shared__ A s_w[kWarps][W];
     __shared__ int s_last;
     const int tid = threadIdx.x;
     const int h = t.x, j = t.y, slot = t.z, hub = t.w - 1;
     const int e0 = p.hub_row_ptr[h], e1 = p.hub_row_ptr[h + 1];
-    const int nt = (e1 - e0 + kHubTileEntries - 1) / kHubTileEntries;
-    const int c0 = e0 + j * kHubTileEntries;
-    const int c1 = min(c0 + kHubTileEntries, e1);
+    const int nt = (e1 - e0 + p.hub_tile - 1) / p.hub_tile;
+    const int c0 = e0 + j * p.hub_tile;
+    const int c1 = min(c0 + p.hub_tile, e1);
     const int a0 = c0 & ~3;
     const int nvec = (c1 - a0 + 3) >> 2;
     A acc[W];
@@ -316,14 +318,30 @@ __device__ __forceinline__ void hub_tile(const StepParams<P, W> &p, int4 t, type
         if (tid == 0) {
             RowOps<P, W> o;
             load_ops<P, W>(p, h, o);
-            row_finish<P, W>(p, h, part, p.inv_deg[h], p.deg[h], o, sT, sA);
+            A tT[W], tA[W];
+            row_finish<P, W>(p, h, part, p.inv_deg[h], p.deg[h], o, tT, tA, active);
+            if (p.reduce) {
+                double *d = p.ipart + (int64_t)h * 2 * W;
+#pragma unroll
+                for (int b = 0; b < W; ++b) {
+                    d[b] = (double)tT[b];
+                    d[W + b] = (double)tA[b];
+                }
+            }
             p.long_cnt[hub] = 0;  // ready for the next round
         }
     }
     __syncthreads();  // s_w and s_last are reused by the CTA's next item
 }
 
-template <int W> struct Unroll { static constexpr int value = W >= 4 ? 1 : 8 / (4 * W); };
+// Groups of kSellVec entries a lane gathers at once in a short chunk (single
+// vector); wider tiles bring W values per gathered row and take fewer groups.
+#ifndef CPAA_SELL_GROUPS
+#define CPAA_SELL_GROUPS 2
+#endif
+template <int W> struct Unroll {
+    static constexpr int value = W >= 4 ? 1 : (CPAA_SELL_GROUPS / W > 0 ? CPAA_SELL_GROUPS / W : 1);
+};
 
 // Sum of entries [i0, i1) of the lane's row in a SELL chunk; i0 and i1 are
 // multiples of kSellVec.  `col` points at the chunk's lane group (chunk start
@@ -351,51 +369,51 @@ __device__ __forceinline__ void chunk_sum(const StepParams<P, W> &p, const int32
                 for (int b = 0; b < W; ++b) acc[b] += x[b];
             }
         }
-        return;
-    }
-    for (; q + U <= q1; q += U) {
-        int4 jj[U];
+    } else {
+        for (; q + U <= q1; q += U) {
+            int4 jj[U];
 #pragma unroll
-        for (int k = 0; k < U; ++k) jj[k] = ld_stream4(col + (int64_t)(q + k) * G);
-        A x[U][4][W];
+            for (int k = 0; k < U; ++k) jj[k] = ld_stream4(col + (int64_t)(q + k) * G);
+            A x[U][4][W];
 #pragma unroll
-        for (int k = 0; k < U; ++k) {
-            gather_row<P, W>(p.y_src, jj[k].x, x[k][0]);
-            gather_row<P, W>(p.y_src, jj[k].y, x[k][1]);
-            gather_row<P, W>(p.y_src, jj[k].z, x[k][2]);
-            gather_row<P, W>(p.y_src, jj[k].w, x[k][3]);
+            for (int k = 0; k < U; ++k) {
+                gather_row<P, W>(p.y_src, jj[k].x, x[k][0]);
+                gather_row<P, W>(p.y_src, jj[k].y, x[k][1]);
+                gather_row<P, W>(p.y_src, jj[k].z, x[k][2]);
+                gather_row<P, W>(p.y_src, jj[k].w, x[k][3]);
+            }
+#pragma unroll
+            for (int k = 0; k < U; ++k)
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+#pragma unroll
+                    for (int b = 0; b < W; ++b) acc[b] += x[k][e][b];
         }
-#pragma unroll
-        for (int k = 0; k < U; ++k)
+        for (; q < q1; ++q) {
+            const int4 j = ld_stream4(col + (int64_t)q * G);
+            A x[4][W];
+            gather_row<P, W>(p.y_src, j.x, x[0]);
+            gather_row<P, W>(p.y_src, j.y, x[1]);
+            gather_row<P, W>(p.y_src, j.z, x[2]);
+            gather_row<P, W>(p.y_src, j.w, x[3]);
 #pragma unroll
             for (int e = 0; e < 4; ++e)
 #pragma unroll
-                for (int b = 0; b < W; ++b) acc[b] += x[k][e][b];
-    }
-    for (; q < q1; ++q) {
-        const int4 j = ld_stream4(col + (int64_t)q * G);
-        A x[4][W];
-        gather_row<P, W>(p.y_src, j.x, x[0]);
-        gather_row<P, W>(p.y_src, j.y, x[1]);
-        gather_row<P, W>(p.y_src, j.z, x[2]);
-        gather_row<P, W>(p.y_src, j.w, x[3]);
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-#pragma unroll
-            for (int b = 0; b < W; ++b) acc[b] += x[e][b];
+                for (int b = 0; b < W; ++b) acc[b] += x[e][b];
+        }
     }
 }
 
 // A long chunk by one CTA: warp w sums slice w of the entries of all 32
 // rows; the slices are added in warp order and warp 0 finishes the rows.
 template <int P, int W>
-__device__ __forceinline__ void long_chunk(const StepParams<P, W> &p, int c, typename Prec<P>::A (&sT)[W],
-                                           typename Prec<P>::A (&sA)[W]) {
+__device__ __forceinline__ void long_chunk(const StepParams<P, W> &p, int4 dsc, unsigned active) {
     using A = typename Prec<P>::A;
     __shared__ A s_part[kWarps][W][kChunkRows];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t off = p.chunk_off[c];
-    const int len = p.chunk_len[c];
+    const int c = dsc.x;
+    const int64_t off = (int64_t)dsc.y * (kChunkRows * kSellVec);
+    const int len = dsc.z;
     // slices of whole kSellVec groups
     const int per = ((len + kWarps - 1) / kWarps + kSellVec - 1) / kSellVec * kSellVec;
     const int i0 = min(len, warp * per), i1 = min(len, i0 + per);
@@ -412,11 +430,16 @@ __device__ __forceinline__ void long_chunk(const StepParams<P, W> &p, int c, typ
             s[b] = s_part[0][b][lane];
             for (int q = 1; q < kWarps; ++q) s[b] += s_part[q][b][lane];
         }
+        A tT[W], tA[W];
+#pragma unroll
+        for (int b = 0; b < W; ++b) tT[b] = tA[b] = A(0);
         if (r < p.n) {
             RowOps<P, W> o;
             load_ops<P, W>(p, r, o);
-            row_finish<P, W>(p, r, s, ld_once(p.inv_deg + r), ld_once(p.deg + r), o, sT, sA);
+            row_finish<P, W>(p, r, s, ld_once(p.inv_deg + r), p.reduce ? ld_once(p.deg + r) : A(0), o, tT, tA,
+                             active);
         }
+        if (p.reduce) warp_item_sums<A, W>(tT, tA, p.ipart, p.n_hub + c);
     }
     __syncthreads();  // s_part is reused by the CTA's next item
 }
@@ -428,21 +451,23 @@ __device__ __forceinline__ void long_chunk(const StepParams<P, W> &p, int c, typ
 template <int P, int W>
 __global__ void __launch_bounds__(kThreads) cheb_step_kernel(const StepParams<P, W> p) {
     using A = typename Prec<P>::A;
-    A sT[W], sA[W];
-#pragma unroll
-    for (int b = 0; b < W; ++b) sT[b] = sA[b] = A(0);
+    // columns stopped by the a-posteriori rule no longer accumulate; once
+    // every column has stopped the remaining rounds do nothing
+    const unsigned active = p.stop ? (p.active & ~*p.stop) : p.active;
+    if (p.stop && active == 0) return;
     const int n_cta_items = p.num_hub_tiles + p.num_long_chunks;
     for (int it = blockIdx.x; it < n_cta_items; it += gridDim.x) {
-        if (it < p.num_hub_tiles) hub_tile<P, W>(p, p.hub_tiles[it], sT, sA);
-        else long_chunk<P, W>(p, p.chunk_order[it - p.num_hub_tiles], sT, sA);
+        if (it < p.num_hub_tiles) hub_tile<P, W>(p, p.hub_tiles[it], active);
+        else long_chunk<P, W>(p, ld_stream4(&p.chunk_desc[it - p.num_hub_tiles].x), active);
     }
     const int lane = threadIdx.x & 31;
     const int nwarps = (int)gridDim.x * kWarps;
     for (int idx = p.num_long_chunks + (int)blockIdx.x * kWarps + (int)(threadIdx.x >> 5); idx < p.num_chunks;
          idx += nwarps) {
-        const int c = p.chunk_order[idx];
-        const int64_t off = p.chunk_off[c];
-        const int len = p.chunk_len[c];
+        const int4 dsc = ld_stream4(&p.chunk_desc[idx].x);
+        const int c = dsc.x;
+        const int64_t off = (int64_t)dsc.y * (kChunkRows * kSellVec);
+        const int len = dsc.z;
         const int64_t r = p.n_hub + (int64_t)c * kChunkRows + lane;
         const bool live = r < p.n;
         // for narrow tiles the row's own operands are fetched before the gather
@@ -452,17 +477,96 @@ __global__ void __launch_bounds__(kThreads) cheb_step_kernel(const StepParams<P,
         RowOps<P, W> o;
         if (live) {
             inv = ld_once(p.inv_deg + r);
-            d = ld_once(p.deg + r);
+            if (p.reduce) d = ld_once(p.deg + r);  // only the round's sums need d
             if constexpr (kEarly) load_ops<P, W>(p, r, o);
         }
         A acc[W];
         chunk_sum<P, W>(p, p.sell_col + off + kSellVec * lane, 0, len, acc);
+        A tT[W], tA[W];
+#pragma unroll
+        for (int b = 0; b < W; ++b) tT[b] = tA[b] = A(0);
         if (live) {
             if constexpr (!kEarly) load_ops<P, W>(p, r, o);
-            row_finish<P, W>(p, r, acc, inv, d, o, sT, sA);
+            row_finish<P, W>(p, r, acc, inv, d, o, tT, tA, active);
         }
+        if (p.reduce) warp_item_sums<A, W>(tT, tA, p.ipart, p.n_hub + c);
     }
-    warp_reduce_add<A, W>(sT, sA, p.reduce, p.red);
+}
+
+// Per-round sums, level 1: CTA j adds item slots [j per, (j+1) per) -- thread
+// t every kThreads-th slot, then a fixed shuffle tree and the warps in order.
+template <int W>
+__global__ void __launch_bounds__(kThreads) item_sum_kernel(const double *__restrict__ ipart, int64_t items,
+                                                            int64_t per, double *out) {
+    __shared__ double s_w[kWarps][2 * W];
+    double v[2 * W];
+#pragma unroll
+    for (int q = 0; q < 2 * W; ++q) v[q] = 0.0;
+    const int64_t i0 = (int64_t)blockIdx.x * per;
+    const int64_t i1 = min(items, i0 + per);
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += kThreads)
+#pragma unroll
+        for (int q = 0; q < 2 * W; ++q) v[q] = __dadd_rn(v[q], ipart[i * 2 * W + q]);
+#pragma unroll
+    for (int q = 0; q < 2 * W; ++q)
+        for (int o = 16; o > 0; o >>= 1) v[q] = __dadd_rn(v[q], __shfl_xor_sync(0xffffffffu, v[q], o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 2 * W; ++q) s_w[warp][q] = v[q];
+    __syncthreads();
+    if (threadIdx.x < 2 * W) {
+        double t = s_w[0][threadIdx.x];
+        for (int w = 1; w < kWarps; ++w) t = __dadd_rn(t, s_w[w][threadIdx.x]);
+        out[(int64_t)blockIdx.x * 2 * W + threadIdx.x] = t;
+    }
+}
+
+// Level 2 (one CTA): the level-1 sums in block order give the round's
+// sum T and sum |T| per column; then the a-posteriori rule's test.
+template <int W>
+__global__ void item_final_kernel(const double *__restrict__ part, int nblk, double *red, const StopArgs a) {
+    const int t = threadIdx.x;
+    __shared__ double s_l1[W];
+    if (t < 2 * W) {
+        double v = 0.0;
+        for (int j = 0; j < nblk; ++j) v = __dadd_rn(v, part[j * 2 * W + t]);
+        red[t] = v;
+        if (t >= W) s_l1[t - W] = v;
+    }
+    __syncthreads();
+    if (t == 0 && a.decide) {
+        unsigned stop = *a.stop;
+        for (int b = 0; b < W; ++b) {
+            if (!(a.decide >> b & 1u) || (stop >> b & 1u)) continue;
+            const double m = a.maxl1[b] < s_l1[b] ? s_l1[b] : a.maxl1[b];
+            a.maxl1[b] = m;
+            const double E = a.err[b];
+            const double EK = __dmul_rn(E, __dmul_rn(2.0, m));
+            const double bound =
+                a.normalize ? EK : __dadd_rn(EK, __ddiv_rn(__dmul_rn(__dadd_rn(1.0, EK), E), __dsub_rn(1.0, E)));
+            if (bound < a.tol[b]) {
+                stop |= 1u << b;
+                a.stop_round[b] = a.k[b];
+            }
+        }
+        *a.stop = stop;
+    }
+}
+
+// CTAs of cheb_step_kernel<P, W> resident on the whole GPU at once (per
+// instantiation, on the current device; computed on first use).
+template <int P, int W>
+static int resident_ctas() {
+    static int per_sm = 0, sms = 0;
+    if (per_sm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cheb_step_kernel<P, W>, kThreads, 0);
+        if (per_sm < 1) per_sm = 1;
+    }
+    return per_sm * sms;
 }
 
 template <int P, int W>
@@ -474,49 +578,50 @@ static cudaError_t launch_typed(const StepLaunch &s) {
     StepParams<P, W> p;
     p.hub_tiles = g->hub_tiles;
     p.num_hub_tiles = g->num_hub_tiles;
+    p.hub_tile = g->hub_tile;
     p.hub_row_ptr = g->hub_row_ptr;
     p.hub_col = g->hub_col;
     p.long_part = reinterpret_cast<A *>(s.long_part);
     p.long_cnt = s.long_cnt ? s.long_cnt : g->long_cnt;
     p.sell_col = g->sell_col;
-    p.chunk_off = g->chunk_off;
-    p.chunk_len = g->chunk_len;
-    p.chunk_order = g->chunk_order;
+    p.chunk_desc = g->chunk_desc;
     p.num_chunks = g->num_chunks;
     p.num_long_chunks = g->num_long_chunks;
     p.n_hub = g->n_hub;
     p.n = g->n;
     if constexpr (P == CPAA_F64) {
         p.deg = g->deg64;
-        p.inv_deg = g->inv_deg64;
+        p.inv_deg = s.power ? g->inv_deg64 : g->inv2_deg64;
     } else {
         p.deg = g->deg32;
-        p.inv_deg = g->inv_deg32;
+        p.inv_deg = s.power ? g->inv_deg32 : g->inv2_deg32;
     }
     p.y_src = static_cast<const S *>(s.y_src);
     p.y_io = static_cast<S *>(s.y_io);
     p.rho = static_cast<R *>(s.rho);
     p.comp = static_cast<R *>(s.comp);
-    p.red = s.red;
+    p.ipart = s.ipart;
+    p.stop = s.stop;
     for (int b = 0; b < W; ++b) p.ck[b] = (A)s.ck[b];
     p.active = s.active;
     p.reduce = s.reduce;
     p.first = s.first;
     p.power = s.power;
-    static int per_sm = 0, sms = 0;  // per instantiation, on the current device
-    if (per_sm == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cheb_step_kernel<P, W>, kThreads, 0);
-        if (per_sm < 1) per_sm = 1;
-    }
     // a small graph needs fewer CTAs than fit: one per CTA item plus one per
     // kWarps short chunks
     const int64_t needed = (int64_t)g->num_hub_tiles + g->num_long_chunks +
                            (g->num_chunks - g->num_long_chunks + kWarps - 1) / kWarps;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sms, needed));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(resident_ctas<P, W>(), needed));
     cheb_step_kernel<P, W><<<grid, kThreads, 0, s.stream>>>(p);
+    if (s.reduce) {
+        // slots: hub rows, then chunks; the split into blocks depends on the
+        // graph alone, so the sums are the same bits for every tile width
+        const int64_t items = (int64_t)g->n_hub + g->num_chunks;
+        const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>(kSumBlocks, (items + kThreads - 1) / kThreads));
+        const int64_t per = (items + nblk - 1) / nblk;
+        item_sum_kernel<W><<<nblk, kThreads, 0, s.stream>>>(s.ipart, items, per, s.ipart2);
+        item_final_kernel<W><<<1, 64, 0, s.stream>>>(s.ipart2, nblk, s.red, s.sa);
+    }
     return cudaGetLastError();
 }
 
@@ -530,6 +635,27 @@ static cudaError_t launch_w(const StepLaunch &s) {
         case 16: return launch_typed<P, 16>(s);
     }
     return cudaErrorInvalidValue;
+}
+
+template <int P>
+static void prepare_w(int width) {
+    switch (width) {
+        case 1: resident_ctas<P, 1>(); break;
+        case 2: resident_ctas<P, 2>(); break;
+        case 4: resident_ctas<P, 4>(); break;
+        case 8: resident_ctas<P, 8>(); break;
+        case 16: resident_ctas<P, 16>(); break;
+    }
+}
+
+// Runs the one-time occupancy queries of a round kernel, so that a later
+// launch issues no other CUDA call (as a stream capture wants).
+void prepare_step(int precision, int width) {
+    switch (precision) {
+        case CPAA_F64: prepare_w<CPAA_F64>(width); break;
+        case CPAA_F32: prepare_w<CPAA_F32>(width); break;
+        case CPAA_BF16: prepare_w<CPAA_BF16>(width); break;
+    }
 }
 
 cudaError_t launch_step(const StepLaunch &s) {

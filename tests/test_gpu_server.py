@@ -142,3 +142,50 @@ def test_admission_needs_memory(pkg):
     assert e.value.status == pkg.CPAA_ENOMEM
     S.close()
     G.close()
+
+
+def test_posteriori_rule_alone_equals_in_mix(pkg):
+    """Serving under the a-posteriori stopping rule: a query stops at the round
+    the oracle's own sums give, no later than the rigorous M, within tol of the
+    exact solution, and with the same bits alone and in a mix."""
+    graphs = [ci.chung_lu(5000, 40000, seed=31), ci.chung_lu(60000, 600000, seed=32)]
+    G = [upload(pkg, g) for g in graphs]
+    S = pkg.Server(2 << 30, stop_rule=pkg.CPAA_STOP_POSTERIORI)
+    ids = [S.add_graph(x, 8) for x in G]
+    try:
+        n = graphs[1].n
+        rp, cx = graphs[1].numpy()
+        seeds = np.array([59990], dtype=np.int32)  # a low-degree seed: kappa = 390
+        p = np.zeros(n)
+        p[seeds] = 1.0
+        truth, _ = O.power(rp, cx, p, 0.85, tol=1e-11)
+        alone = np.empty(n)
+        st, info = S.wait(S.submit(ids[1], seeds, None, 0.85, 1e-6), alone, timeout_us=120_000_000)
+        assert st == pkg.CPAA_OK
+        k = O.kappa(rp, p)
+        M1 = O.rounds_needed(0.85, 1e-6, k)
+        _, _, l1 = O.cpaa(rp, cx, p, 0.85, M1, history=True)
+        M2 = O.rounds_posteriori(0.85, 1e-6, l1)
+        assert M2 is not None and M2 < M1  # 33 against 34 on this graph
+        assert info.rounds == M2
+        assert info.bound < 1e-6
+        ref = O.cpaa(rp, cx, p, 0.85, info.rounds)
+        assert np.abs(alone - ref).sum() / np.abs(ref).sum() <= 1e-6
+        assert np.abs(alone - truth).sum() <= 2e-6
+        mix = _queries(graphs, 60, seed=9)
+        tickets, tq = [], None
+        for i, (g2, sd, w, c, tol) in enumerate(mix):
+            tickets.append(S.submit(ids[g2], sd, w, c, tol))
+            if i == 30:
+                tq = S.submit(ids[1], seeds, None, 0.85, 1e-6)
+        in_mix = np.empty(n)
+        st2, info2 = S.wait(tq, in_mix, timeout_us=120_000_000)
+        assert st2 == pkg.CPAA_OK and info2.rounds == info.rounds
+        assert np.array_equal(alone, in_mix)
+        for t in tickets:
+            st3, _ = S.wait(t, None, timeout_us=120_000_000)
+            assert st3 == pkg.CPAA_OK
+    finally:
+        S.close()
+        for x in G:
+            x.close()

@@ -179,6 +179,51 @@ def test_l1_bound_holds(c):
                 assert err <= O.l1_bound(c, M, k, norm) * (1 + 1e-9) + 1e-15
 
 
+@pytest.mark.parametrize("c", CS)
+def test_posteriori_rule_against_exact_solution(c):
+    """The a-posteriori rule (kappa replaced by twice the running max of
+    ||T_j p||_1) is an estimate: pin its M against the exact solution from
+    LAPACK on uniform, single-seed and few-seed vectors, and check that it
+    never asks for more rounds than the rigorous rule when 2 max ||T_j p|| <=
+    kappa (so it can only shorten such solves)."""
+    margins = []
+    for gseed, (n, m) in enumerate(((600, 4000), (1500, 9000))):
+        g = ci.chung_lu(n, m, seed=40 + gseed)
+        rp, cx = g.numpy()
+        ps = [np.full(n, 1.0 / n)]
+        for s0 in ((n - 1,), (n // 2,), (3, 100, n - 7)):
+            e = np.zeros(n); e[list(s0)] = 1.0 / len(s0)
+            ps.append(e)
+        for p in ps:
+            ref = O.lapack_pagerank(rp, cx, p, c)
+            k = O.kappa(rp, p)
+            for tol in (1e-4, 1e-6, 1e-9):
+                for norm in (0, 1):
+                    M1 = O.rounds_needed(c, tol, k, norm)
+                    _, _, l1 = O.cpaa(rp, cx, p, c, M1, normalize=norm, history=True)
+                    M2 = O.rounds_posteriori(c, tol, l1, norm)
+                    if 2 * l1.max() <= k:
+                        assert M2 is not None and M2 <= M1
+                    M = M1 if M2 is None else min(M1, M2)
+                    err = np.abs(O.cpaa(rp, cx, p, c, M, normalize=norm) - ref).sum()
+                    assert err <= tol, (n, tol, norm, M, err)
+                    margins.append(err / tol)
+    assert max(margins) < 1.0
+
+
+def test_posteriori_rule_hand_case():
+    """Hand case: with ||T_j p||_1 = 1 for every j the estimate is 2, so the
+    rule's M is the first with l1_bound(c, M, 2) < tol."""
+    c, tol = 0.85, 1e-6
+    hist = np.ones(200)
+    want = next(M for M in range(1, 200) if O.l1_bound(c, M, 2.0) < tol)
+    assert O.rounds_posteriori(c, tol, hist) == want
+    # a larger term later raises the estimate from that round on
+    hist2 = hist.copy(); hist2[want - 1] = 50.0
+    assert O.rounds_posteriori(c, tol, hist2) > want
+    assert O.rounds_posteriori(c, tol, hist[:want]) is None
+
+
 # -- closed forms ------------------------------------------------------------------
 
 @pytest.mark.parametrize("L", [1, 2, 5, 50])
