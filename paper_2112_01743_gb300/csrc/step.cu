@@ -183,13 +183,13 @@ __device__ __forceinline__ void load_ops(const StepParams<P, W> &p, int64_t r, R
     }
 }
 
-// Row epilogue: new iterates, accumulation, reduction terms.
+// Row epilogue: new iterates and accumulation; yv receives the new iterates
+// (as stored) for the round's sums.
 template <int P, int W>
 __device__ __forceinline__ void row_finish(const StepParams<P, W> &p, int64_t r,
                                            const typename Prec<P>::A (&s)[W],
-                                           typename Prec<P>::A inv, typename Prec<P>::A d,
-                                           RowOps<P, W> &o, typename Prec<P>::A (&tT)[W],
-                                           typename Prec<P>::A (&tA)[W], unsigned active) {
+                                           typename Prec<P>::A inv, RowOps<P, W> &o,
+                                           typename Prec<P>::A (&yv)[W], unsigned active) {
     using S = typename Prec<P>::S;
     using A = typename Prec<P>::A;
     using R = typename Prec<P>::R;
@@ -200,9 +200,7 @@ __device__ __forceinline__ void row_finish(const StepParams<P, W> &p, int64_t r,
         for (int b = 0; b < W; ++b) {
             const A y = power_iterate<P>(s[b], inv, p.ck[b], o.rr[b]);
             store_y(&ys[b], y);
-            const A T = y * d;
-            tT[b] = T;
-            tA[b] = (T < A(0) ? -T : T);
+            yv[b] = y;
         }
         store_row<S, W>(p.y_io + r * W, ys, false);
         return;
@@ -212,13 +210,24 @@ __device__ __forceinline__ void row_finish(const StepParams<P, W> &p, int64_t r,
         const A y = new_iterate<P>(s[b], inv, o.y_old[b], (p.first >> b) & 1u);
         store_y(&ys[b], y);
         if (active >> b & 1u) accumulate<P>(o.rr[b], o.cmp[b], p.ck[b], y);
-        const A T = y * d;
-        tT[b] = T;
-        tA[b] = (T < A(0) ? -T : T);
+        yv[b] = y;
     }
     store_row<S, W>(p.y_io + r * W, ys, false);
     store_row<R, W>(p.rho + r * W, o.rr, true);
     if constexpr (Prec<P>::kKahan) store_row<R, W>(p.comp + r * W, o.cmp, true);
+}
+
+// A row's terms of the round's sums: T = d y and |T| (only in rounds that take
+// sums; the others skip this arithmetic, which matters on GB300's slow FP64
+// pipe).
+template <class A, int W>
+__device__ __forceinline__ void row_terms(const A (&yv)[W], A d, A (&tT)[W], A (&tA)[W]) {
+#pragma unroll
+    for (int b = 0; b < W; ++b) {
+        const A T = yv[b] * d;
+        tT[b] = T;
+        tA[b] = (T < A(0) ? -T : T);
+    }
 }
 
 // A chunk's partial sums: the 32 rows' T and |T| added by a fixed shuffle
@@ -318,9 +327,10 @@ __device__ __forceinline__ void hub_tile(const StepParams<P, W> &p, int4 t, unsi
         if (tid == 0) {
             RowOps<P, W> o;
             load_ops<P, W>(p, h, o);
-            A tT[W], tA[W];
-            row_finish<P, W>(p, h, part, p.inv_deg[h], p.deg[h], o, tT, tA, active);
+            A yv[W], tT[W], tA[W];
+            row_finish<P, W>(p, h, part, p.inv_deg[h], o, yv, active);
             if (p.reduce) {
+                row_terms<A, W>(yv, p.deg[h], tT, tA);
                 double *d = p.ipart + (int64_t)h * 2 * W;
 #pragma unroll
                 for (int b = 0; b < W; ++b) {
@@ -430,16 +440,19 @@ __device__ __forceinline__ void long_chunk(const StepParams<P, W> &p, int4 dsc, 
             s[b] = s_part[0][b][lane];
             for (int q = 1; q < kWarps; ++q) s[b] += s_part[q][b][lane];
         }
-        A tT[W], tA[W];
+        A yv[W];
 #pragma unroll
-        for (int b = 0; b < W; ++b) tT[b] = tA[b] = A(0);
+        for (int b = 0; b < W; ++b) yv[b] = A(0);
         if (r < p.n) {
             RowOps<P, W> o;
             load_ops<P, W>(p, r, o);
-            row_finish<P, W>(p, r, s, ld_once(p.inv_deg + r), p.reduce ? ld_once(p.deg + r) : A(0), o, tT, tA,
-                             active);
+            row_finish<P, W>(p, r, s, ld_once(p.inv_deg + r), o, yv, active);
         }
-        if (p.reduce) warp_item_sums<A, W>(tT, tA, p.ipart, p.n_hub + c);
+        if (p.reduce) {
+            A tT[W], tA[W];
+            row_terms<A, W>(yv, r < p.n ? ld_once(p.deg + r) : A(0), tT, tA);
+            warp_item_sums<A, W>(tT, tA, p.ipart, p.n_hub + c);
+        }
     }
     __syncthreads();  // s_part is reused by the CTA's next item
 }
@@ -482,14 +495,18 @@ __global__ void __launch_bounds__(kThreads) cheb_step_kernel(const StepParams<P,
         }
         A acc[W];
         chunk_sum<P, W>(p, p.sell_col + off + kSellVec * lane, 0, len, acc);
-        A tT[W], tA[W];
+        A yv[W];
 #pragma unroll
-        for (int b = 0; b < W; ++b) tT[b] = tA[b] = A(0);
+        for (int b = 0; b < W; ++b) yv[b] = A(0);
         if (live) {
             if constexpr (!kEarly) load_ops<P, W>(p, r, o);
-            row_finish<P, W>(p, r, acc, inv, d, o, tT, tA, active);
+            row_finish<P, W>(p, r, acc, inv, o, yv, active);
         }
-        if (p.reduce) warp_item_sums<A, W>(tT, tA, p.ipart, p.n_hub + c);
+        if (p.reduce) {
+            A tT[W], tA[W];
+            row_terms<A, W>(yv, d, tT, tA);
+            warp_item_sums<A, W>(tT, tA, p.ipart, p.n_hub + c);
+        }
     }
 }
 
