@@ -50,6 +50,10 @@ WORKLOADS = {
     "chung_lu_1M": dict(n=1 << 20, edges=16_000_000, gamma=2.1, seed=0, c=0.85, tol=1e-6,
                         desc="Chung-Lu n=2^20, 1.6e7 pair draws, gamma=2.1, seed 0, + ring; "
                              "c=0.85, uniform p, tol 1e-6 L1"),
+    "chung_lu_16M_shuffled": dict(n=1 << 24, edges=256_000_000, gamma=2.1, seed=0, c=0.85, tol=1e-6,
+                                  shuffle=1,
+                                  desc="Chung-Lu n=2^24 as chung_lu_16M, vertex ids randomly permuted "
+                                       "(seed 1); c=0.85, uniform p, tol 1e-6 L1"),
     "grid_4096": dict(rows=4096, cols=4096, frac=0.2, seed=0, c=0.85, tol=1e-6,
                       desc="4096x4096 lattice, 20% of edges deleted (seed 0, spanning tree kept); "
                            "c=0.85, uniform p, tol 1e-6 L1"),
@@ -180,6 +184,8 @@ def make_graph(wl, device):
         g = ci.grid_deleted(w["rows"], w["cols"], w["frac"], seed=w["seed"], device=device)
     else:
         g = ci.chung_lu(w["n"], w["edges"], gamma=w["gamma"], seed=w["seed"], device=device)
+        if w.get("shuffle"):
+            g = ci.shuffled(g, seed=w["shuffle"])
     return g, time.time() - t
 
 
@@ -395,7 +401,7 @@ def run_serving(pkg, args):
         ids = [S.add_graph(x, 16) for x in G]
         tickets = []
         lock = threading.Condition()
-        done = {"n": 0, "t_last": 0.0}
+        done = {"n": 0, "t_last": 0.0, "entries": 0}
 
         def consumer():
             i = 0
@@ -404,7 +410,8 @@ def run_serving(pkg, args):
                     while i >= len(tickets):
                         lock.wait()
                     t = tickets[i]
-                S.wait(t, None)
+                _, info = S.wait(t, None)
+                done["entries"] += G[queries[i][0]].nnz * info.rounds
                 i += 1
                 done["n"] = i
                 done["t_last"] = time.perf_counter()
@@ -433,6 +440,7 @@ def run_serving(pkg, args):
         th.join()
         st = S.stats()
         S.close()
+        st["effective_gteps"] = done["entries"] / (done["t_last"] - t0) / 1e9
         return len(queries) / (done["t_last"] - t0), st
 
     sat_queries = make(args.serve_queries // 4)
@@ -449,7 +457,8 @@ def run_serving(pkg, args):
             "saturated_qps": sat_qps, "poisson_rate_qps": rate, "achieved_qps": qps,
             "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3, "mean_ms": st["mean_us"] / 1e3,
             "admit_p50_ms": st["admit_p50_us"] / 1e3, "saturated_p50_ms": sat_st["p50_us"] / 1e3,
-            "saturated_p99_ms": sat_st["p99_us"] / 1e3, "completed": st["completed"],
+            "saturated_p99_ms": sat_st["p99_us"] / 1e3,
+            "saturated_effective_gteps": sat_st["effective_gteps"], "completed": st["completed"],
             "failed": st["failed"],
             "posteriori_saturated_qps": post_qps, "posteriori_saturated_p50_ms": post_st["p50_us"] / 1e3,
             "posteriori_saturated_p99_ms": post_st["p99_us"] / 1e3}

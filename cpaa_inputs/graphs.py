@@ -148,6 +148,34 @@ def grid_deleted(rows, cols, frac=0.2, seed=0, device="cpu"):
                                      % (R, C, frac, seed))
 
 
+def shuffled(g, seed=0):
+    """The same graph with its vertex ids permuted by a seeded random
+    permutation (rows re-sorted, columns ascending): a stand-in for inputs whose
+    ids carry no degree or locality order."""
+    n = g.n
+    dev = g.row_ptr.device
+    vid = rng.arange(0, n, dev)
+    order = torch.argsort(rng.u53(seed, 9, vid))      # new id -> old id
+    new_of = torch.empty_like(order)
+    new_of[order] = vid                                # old id -> new id
+    rp = g.row_ptr.to(torch.int64)
+    deg = rp[1:] - rp[:-1]
+    rows = torch.repeat_interleave(vid, deg)
+    a = new_of[rows]
+    b = new_of[g.col_idx.to(torch.int64)]
+    del rows
+    keys = a * n + b
+    del a, b
+    keys, _ = torch.sort(keys)
+    r = keys // n
+    counts = torch.bincount(r, minlength=n)
+    del r
+    row_ptr = torch.zeros(n + 1, dtype=torch.int64, device=dev)
+    row_ptr[1:] = torch.cumsum(counts, 0)
+    col_idx = (keys % n).to(torch.int32)
+    return Csr(n, row_ptr.to(torch.int32), col_idx, g.name + "_shuffled(%d)" % seed)
+
+
 # -- small graphs with known structure (test fixtures) ------------------------
 
 def star(L, device="cpu"):

@@ -148,10 +148,24 @@ static int hub_tile_entries(int hub_deg) { return std::min(kMaxHubTile, std::max
 
 static void host_layout(const int32_t *rp, int64_t n, int hub_deg, int tile, HostLayout &L) {
     auto deg = [&](int32_t u) { return rp[u + 1] - rp[u]; };
-    std::vector<int32_t> hubs, rest;
+    // heavy rows (degree at least kHeavyFactor times the mean, and at least 64) follow the
+    // hubs as one block sorted by degree: in an undirected graph a vertex is
+    // gathered once per edge, so these are the hottest gather targets, and
+    // placing them together keeps their iterate values in few cache lines
+    // whatever order the caller's ids have
+    const int64_t nnz = rp[n];
+    const int heavy = (int)std::max<int64_t>(64, kHeavyFactor * nnz / std::max<int64_t>(1, n));
+    std::vector<int32_t> hubs, heavy_rows, rest;
     rest.reserve((size_t)n);
-    for (int64_t u = 0; u < n; ++u) (deg((int32_t)u) > hub_deg ? hubs : rest).push_back((int32_t)u);
+    for (int64_t u = 0; u < n; ++u) {
+        const int d = deg((int32_t)u);
+        (d > hub_deg ? hubs : d >= heavy ? heavy_rows : rest).push_back((int32_t)u);
+    }
     std::stable_sort(hubs.begin(), hubs.end(), [&](int32_t a, int32_t b) { return deg(a) > deg(b); });
+    std::stable_sort(heavy_rows.begin(), heavy_rows.end(), [&](int32_t a, int32_t b) { return deg(a) > deg(b); });
+    // the heavy block leads the SELL part; the window sort below keeps it first
+    // (its rows are the longest of any window they share with light rows)
+    rest.insert(rest.begin(), heavy_rows.begin(), heavy_rows.end());
     const int64_t nrest = (int64_t)rest.size();
     const int64_t nwin = (nrest + kSortWindow - 1) / kSortWindow;
     const int nth = (int)std::max<int64_t>(1, std::min<int64_t>(16, nwin / 64));

@@ -17,8 +17,10 @@ namespace cpaa {
 //
 // Vertices are relabelled once, at cpaa_graph_create:
 //   new ids [0, n_hub)  hub rows (degree > hub_degree(nnz)), by decreasing degree;
-//   new ids [n_hub, n)  every other row, in windows of kSortWindow rows of the
-//                       original order, each window sorted by decreasing degree.
+//   new ids [n_hub, n)  heavy rows (degree at least 64 and kHeavyFactor times the mean)
+//                       by decreasing degree, then every other row in the
+//                       original order; cut into windows of kSortWindow rows,
+//                       each window sorted by decreasing degree.
 // Every per-vertex vector (degrees, iterates, accumulator) is stored in the new
 // order; the solve gathers p through the permutation and scatters pi back.
 //
@@ -54,7 +56,14 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kChunkRows = 32;
 constexpr int kSellVec = 4;     // a lane's SELL entries are stored in groups of 4 (one 16-byte load)
-constexpr int kSortWindow = 1024;
+#ifndef CPAA_SORT_WINDOW
+#define CPAA_SORT_WINDOW 1024
+#endif
+constexpr int kSortWindow = CPAA_SORT_WINDOW;  // sigma of SELL-C-sigma (a multiple of 32)
+#ifndef CPAA_HEAVY_FACTOR
+#define CPAA_HEAVY_FACTOR 8
+#endif
+constexpr int kHeavyFactor = CPAA_HEAVY_FACTOR;  // heavy rows: degree >= this times the mean (and >= 64)
 // Tuning constants (compile-time; the defaults were picked by timing the
 // round on the 2^24-vertex Chung-Lu graph).
 #ifndef CPAA_HUB_DEGREE

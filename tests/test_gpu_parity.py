@@ -241,3 +241,28 @@ def test_power_method_matches_oracle(pkg, uploaded, gi):
     torch.cuda.synchronize()
     ref, _ = O.power(rp, cx, p, 0.85, rounds=next(t for t in range(1, 1000) if 2 * 0.85 ** t < 1e-6))
     assert np.abs(out32.cpu().numpy() - ref).sum() / np.abs(ref).sum() <= 1e-6
+
+
+def test_round_graph_cache_across_keys_and_workspace_growth(pkg):
+    """The captured round sequences are keyed by every launch value: alternating
+    round counts, dampings and precisions, and a batch that grows the workspace
+    in between, all give the oracle's result."""
+    g = ci.chung_lu(20000, 150000, seed=41)
+    G = upload(pkg, g)
+    rp, cx = g.numpy()
+    p = _p_variants(g.n)["ramp"]
+    seq = [(10, 0.85, "F64"), (20, 0.85, "F64"), (10, 0.5, "F64"), (10, 0.85, "F32"), (10, 0.85, "F64")]
+    for i, (M, c, prec) in enumerate(seq):
+        if i == 3:  # grow the workspace (wider tile, more rounds) between solves
+            P = ci.seed_dense(g.n, ci.seed_vectors(g.n, 16, seed=2))
+            Pd = torch.as_tensor(P).cuda()
+            PI = torch.empty_like(Pd)
+            G.solve_batch(16, Pd, np.full(16, 0.85), 0.0, PI, fixed_rounds=40, precision=pkg.CPAA_F32,
+                          batch_width=16)
+            torch.cuda.synchronize()
+        pi, info = solve(pkg, G, p, c, fixed_rounds=M, precision=getattr(pkg, "CPAA_" + prec))
+        ref = O.cpaa(rp, cx, p, c, M)
+        err = np.abs(pi - ref).sum()
+        assert info.rounds == M
+        assert err <= (1e-12 if prec == "F64" else 1e-6 * np.abs(ref).sum()), (i, err)
+    G.close()
