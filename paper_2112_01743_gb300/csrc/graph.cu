@@ -148,13 +148,13 @@ static int hub_tile_entries(int hub_deg) { return std::min(kMaxHubTile, std::max
 
 static void host_layout(const int32_t *rp, int64_t n, int hub_deg, int tile, HostLayout &L) {
     auto deg = [&](int32_t u) { return rp[u + 1] - rp[u]; };
-    // heavy rows (degree at least kHeavyFactor times the mean, and at least 64) follow the
+    // heavy rows (degree at least kHeavyFactor times the mean, and at least kHeavyMin) follow the
     // hubs as one block sorted by degree: in an undirected graph a vertex is
     // gathered once per edge, so these are the hottest gather targets, and
     // placing them together keeps their iterate values in few cache lines
     // whatever order the caller's ids have
     const int64_t nnz = rp[n];
-    const int heavy = (int)std::max<int64_t>(64, kHeavyFactor * nnz / std::max<int64_t>(1, n));
+    const int heavy = (int)std::max<int64_t>(kHeavyMin, kHeavyFactor * nnz / std::max<int64_t>(1, n));
     std::vector<int32_t> hubs, heavy_rows, rest;
     rest.reserve((size_t)n);
     for (int64_t u = 0; u < n; ++u) {

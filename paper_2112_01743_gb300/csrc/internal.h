@@ -17,7 +17,7 @@ namespace cpaa {
 //
 // Vertices are relabelled once, at cpaa_graph_create:
 //   new ids [0, n_hub)  hub rows (degree > hub_degree(nnz)), by decreasing degree;
-//   new ids [n_hub, n)  heavy rows (degree at least 64 and kHeavyFactor times the mean)
+//   new ids [n_hub, n)  heavy rows (degree at least kHeavyMin and kHeavyFactor times the mean)
 //                       by decreasing degree, then every other row in the
 //                       original order; cut into windows of kSortWindow rows,
 //                       each window sorted by decreasing degree.
@@ -61,9 +61,13 @@ constexpr int kSellVec = 4;     // a lane's SELL entries are stored in groups of
 #endif
 constexpr int kSortWindow = CPAA_SORT_WINDOW;  // sigma of SELL-C-sigma (a multiple of 32)
 #ifndef CPAA_HEAVY_FACTOR
-#define CPAA_HEAVY_FACTOR 8
+#define CPAA_HEAVY_FACTOR 2
 #endif
-constexpr int kHeavyFactor = CPAA_HEAVY_FACTOR;  // heavy rows: degree >= this times the mean (and >= 64)
+#ifndef CPAA_HEAVY_MIN
+#define CPAA_HEAVY_MIN 64
+#endif
+constexpr int kHeavyFactor = CPAA_HEAVY_FACTOR;  // heavy rows: degree >= this times the mean
+constexpr int kHeavyMin = CPAA_HEAVY_MIN;        // ... and >= this
 // Tuning constants (compile-time; the defaults were picked by timing the
 // round on the 2^24-vertex Chung-Lu graph).
 #ifndef CPAA_HUB_DEGREE
