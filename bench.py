@@ -59,8 +59,8 @@ WORKLOADS = {
                            "c=0.85, uniform p, tol 1e-6 L1"),
 }
 
-PREC = {"f64": 0, "f32": 1, "bf16": 2}
-VB = {"f64": 8, "f32": 4, "bf16": 2}
+PREC = {"f64": 0, "f32": 1, "bf16": 2, "df64": 3}
+VB = {"f64": 8, "f32": 4, "bf16": 2, "df64": 8}
 
 
 def alg_bytes_per_round(n, nnz, prec):
@@ -70,8 +70,8 @@ def alg_bytes_per_round(n, nnz, prec):
     read-modify-write (2 vr n) and, for the FP32/BF16 forms, the Kahan
     compensation read-modify-write (8 n)."""
     vb = VB[prec]
-    vr = 8 if prec == "f64" else 4
-    kahan = 0 if prec == "f64" else 8
+    vr = 8 if prec in ("f64", "df64") else 4
+    kahan = 0 if prec in ("f64", "df64") else 8
     return 4 * nnz + 4 * (n + 1) + 4 * n + 3 * vb * n + 2 * vr * n + kahan * n
 
 
@@ -345,7 +345,8 @@ def run_grid(pkg, args, stream):
     out = {}
     res = {}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for name, prec in (("f64", pkg.CPAA_F64), ("f32", pkg.CPAA_F32), ("bf16", pkg.CPAA_BF16)):
+    for name, prec in (("f64", pkg.CPAA_F64), ("f32", pkg.CPAA_F32), ("bf16", pkg.CPAA_BF16),
+                       ("df64", pkg.CPAA_DF64)):
         pi = torch.empty_like(p)
         for _ in range(3):
             G.solve(p, 0.85, 1e-6, pi, precision=prec)
@@ -361,7 +362,7 @@ def run_grid(pkg, args, stream):
                      "gteps": nnz * infos[0].rounds / (ms * 1e-3) / 1e9,
                      "hbm_frac_of_measured": alg_bytes_per_round(n, nnz, name) / (rms * 1e-3) / 1e9
                      / measured_peak_gbs()[0]}
-    for name in ("f32", "bf16"):
+    for name in ("f32", "bf16", "df64"):
         out[name]["l1_vs_f64"] = float((res[name] - res["f64"]).abs().sum().item())
     G.close()
     return {"workload": "4096x4096 lattice, 20% of edges deleted (seed 0, spanning tree kept); "
@@ -584,6 +585,21 @@ def run_ours(args):
                "fp64_adds_per_round": nnz,
                "speedup_of_%s" % prec: ms64 / (ms_total / args.steps),
                "l1_%s_vs_f64" % prec: l1}
+        # the double-float form (FP64-class accuracy on the FP32 pipes)
+        pdf = torch.empty_like(p)
+        for _ in range(3):
+            G.solve(p, wl["c"], wl["tol"], pdf, precision=PREC["df64"])
+        torch.cuda.synchronize()
+        e0.record(stream)
+        infdf = [G.solve(p, wl["c"], wl["tol"], pdf, precision=PREC["df64"], time_rounds=True)
+                 for _ in range(args.steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msdf = e0.elapsed_time(e1) / args.steps
+        rdf = sum(i.rounds_ms for i in infdf) / sum(i.rounds for i in infdf)
+        f64["df64"] = {"ms_per_solve": msdf, "round_ms": rdf,
+                       "hbm_frac_of_measured": alg_bytes_per_round(n, nnz, "df64") / (rdf * 1e-3) / 1e9 / peak,
+                       "l1_vs_f64": float((pdf - pi).abs().sum().item())}
 
     # ---- the paper's comparison: power method (SPI) on the same kernels, same L1 bound
     power = None

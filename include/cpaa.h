@@ -62,9 +62,13 @@ typedef enum {
 /* Number format of the iterate vectors.  F64: FP64 storage and arithmetic.
  * F32: FP32 storage and arithmetic, Kahan-compensated FP32 accumulator.
  * BF16: bfloat16 storage, FP32 arithmetic, Kahan-compensated FP32
- * accumulator.  The coefficients c_k, the stopping rule and every output
- * stay FP64 on all three. */
-typedef enum { CPAA_F64 = 0, CPAA_F32 = 1, CPAA_BF16 = 2 } cpaa_precision;
+ * accumulator.  DF64: double-float -- every value is an unevaluated sum of
+ * two FP32 numbers (about 48 significant bits, FP32 exponent range), with
+ * error-free FP32 transformations for the arithmetic: FP64-class accuracy on
+ * the FP32 pipes of a GPU whose FP64 rate is low (cpaa_solve and
+ * cpaa_solve_batch; not the power method or the server).  The coefficients
+ * c_k, the stopping rule and every output stay FP64 on all four. */
+typedef enum { CPAA_F64 = 0, CPAA_F32 = 1, CPAA_BF16 = 2, CPAA_DF64 = 3 } cpaa_precision;
 
 /* cpaa_graph_create flags */
 #define CPAA_GRAPH_DEVICE_INPUT 1u /* row_ptr / col_idx are device pointers */

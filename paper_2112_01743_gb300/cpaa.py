@@ -14,7 +14,7 @@ __all__ = [
     "CpaaError", "CpaaOptions", "CpaaInfo", "lib", "library_path",
     "CPAA_OK", "CPAA_EINVAL", "CPAA_ENOMEM", "CPAA_ENOTCONV", "CPAA_ECUDA", "CPAA_ETIMEOUT",
     "CPAA_EBUSY", "CPAA_ECANCELLED", "CPAA_ENOTFOUND",
-    "CPAA_F64", "CPAA_F32", "CPAA_BF16", "CPAA_GRAPH_DEVICE_INPUT", "CPAA_GRAPH_VALIDATE",
+    "CPAA_F64", "CPAA_F32", "CPAA_BF16", "CPAA_DF64", "CPAA_GRAPH_DEVICE_INPUT", "CPAA_GRAPH_VALIDATE",
     "CPAA_DEVICE_IO", "CPAA_TIME_ROUNDS", "CPAA_STOP_RIGOROUS", "CPAA_STOP_POSTERIORI",
     "cpaa_options_init", "cpaa_graph_create", "cpaa_graph_destroy", "cpaa_graph_info",
     "cpaa_solve", "cpaa_solve_batch", "cpaa_rounds_needed", "cpaa_l1_bound",
@@ -26,7 +26,7 @@ __all__ = [
 
 CPAA_OK, CPAA_EINVAL, CPAA_ENOMEM, CPAA_ENOTCONV, CPAA_ECUDA = 0, 1, 2, 3, 4
 CPAA_ETIMEOUT, CPAA_EBUSY, CPAA_ECANCELLED, CPAA_ENOTFOUND = 5, 6, 7, 8
-CPAA_F64, CPAA_F32, CPAA_BF16 = 0, 1, 2
+CPAA_F64, CPAA_F32, CPAA_BF16, CPAA_DF64 = 0, 1, 2, 3
 CPAA_GRAPH_DEVICE_INPUT, CPAA_GRAPH_VALIDATE = 1, 2
 CPAA_DEVICE_IO = 1
 CPAA_NOALLOC_MAX_N = 1300000

@@ -74,7 +74,8 @@ extern "C" cpaa_status cpaa_solve_batch(cpaa_graph *g, int B, const double *P, c
         if (!(c[b] > 0.0 && c[b] < 1.0)) return fail(CPAA_EINVAL, "damping c[" + std::to_string(b) + "] must lie in (0, 1)");
     if (opt.fixed_rounds < 0) return fail(CPAA_EINVAL, "fixed_rounds < 0");
     if (opt.fixed_rounds == 0 && !(tol > 0.0)) return fail(CPAA_EINVAL, "tol must be > 0");
-    if (opt.precision != CPAA_F64 && opt.precision != CPAA_F32 && opt.precision != CPAA_BF16)
+    if (opt.precision != CPAA_F64 && opt.precision != CPAA_F32 && opt.precision != CPAA_BF16 &&
+        opt.precision != CPAA_DF64)
         return fail(CPAA_EINVAL, "unknown precision");
     if (opt.normalize != 0 && opt.normalize != 1) return fail(CPAA_EINVAL, "normalize must be 0 or 1");
     if (opt.stop_rule != CPAA_STOP_RIGOROUS && opt.stop_rule != CPAA_STOP_POSTERIORI)

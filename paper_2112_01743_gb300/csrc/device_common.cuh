@@ -27,6 +27,59 @@ template <> struct Prec<CPAA_BF16> {
     using R = float;
     static constexpr bool kKahan = true;
 };
+template <> struct Prec<CPAA_DF64> {
+    using S = df;
+    using A = df;
+    using R = df;
+    static constexpr bool kKahan = false;  // the pair already carries the low bits
+};
+
+// ---------------------------------------------------------------------------
+// Double-float arithmetic on the FP32 pipes.  The building blocks are the
+// classical error-free transformations: Knuth's two-sum (s + e = a + b
+// exactly), Dekker's fast two-sum (the same when |a| >= |b|) and the product
+// a b = p + e with e from one fused multiply-add.  A double-float sum adds the
+// high and the low parts with two-sums and renormalises twice, which keeps
+// about 2^-47 relative accuracy even under cancellation (the recurrence
+// subtracts y_{k-1}); a product drops only the lo x lo term.  Every step is an
+// explicitly rounded intrinsic, so the compiler cannot contract or reorder it.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+    float s, e, t, f;
+    two_sum(a.hi, b.hi, s, e);
+    two_sum(a.lo, b.lo, t, f);
+    e = __fadd_rn(e, t);
+    fast_two_sum(s, e, s, e);
+    e = __fadd_rn(e, f);
+    fast_two_sum(s, e, s, e);
+    return df(s, e);
+}
+__device__ __forceinline__ df df_mul(df a, df b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    float s;
+    fast_two_sum(p, e, s, e);
+    return df(s, e);
+}
+__device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
+__device__ __forceinline__ df operator+(df a, df b) { return df_add(a, b); }
+__device__ __forceinline__ df &operator+=(df &a, df b) { return a = df_add(a, b); }
+__device__ __forceinline__ df operator*(df a, df b) { return df_mul(a, b); }
+__device__ __forceinline__ bool operator<(df a, df b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ double to_double(df v) { return __dadd_rn((double)v.hi, (double)v.lo); }
+__device__ __forceinline__ double to_double(double v) { return v; }
+__device__ __forceinline__ double to_double(float v) { return (double)v; }
+// ---------------------------------------------------------------------------
 
 // Gathered iterate: ld.global.nc, allocating in L1 (hub values repeat).
 __device__ __forceinline__ double load_y(const double *p) { return __ldg(p); }
@@ -34,10 +87,13 @@ __device__ __forceinline__ float load_y(const float *p) { return __ldg(p); }
 __device__ __forceinline__ float load_y(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
 
 __device__ __forceinline__ double to_acc(double v) { return v; }
+__device__ __forceinline__ df to_acc(df v) { return v; }
 __device__ __forceinline__ float to_acc(float v) { return v; }
 __device__ __forceinline__ float to_acc(__nv_bfloat16 v) { return __bfloat162float(v); }
 
 __device__ __forceinline__ void store_y(double *p, double v) { *p = v; }
+__device__ __forceinline__ void store_y(df *p, df v) { *p = v; }
+__device__ __forceinline__ df round_y(df v, const df *) { return v; }
 __device__ __forceinline__ void store_y(float *p, float v) { *p = v; }
 __device__ __forceinline__ void store_y(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 __device__ __forceinline__ double round_y(double v, const double *) { return v; }
@@ -50,6 +106,10 @@ __device__ __forceinline__ float round_y(float v, const __nv_bfloat16 *) {
 __device__ __forceinline__ int ld_stream(const int32_t *p) { return __ldcs(p); }
 __device__ __forceinline__ int4 ld_stream4(const int32_t *p) { return __ldcs(reinterpret_cast<const int4 *>(p)); }
 template <class T> __device__ __forceinline__ T ld_once(const T *p) { return __ldcs(p); }
+__device__ __forceinline__ df ld_once(const df *p) {
+    const float2 v = __ldcs(reinterpret_cast<const float2 *>(p));
+    return df(v.x, v.y);
+}
 template <class T> __device__ __forceinline__ void st_once(T *p, T v) { __stcs(p, v); }
 
 // Explicitly rounded arithmetic (no contraction differences between kernels).
@@ -60,6 +120,10 @@ __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, 
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ df add_rn(df a, df b) { return df_add(a, b); }
+__device__ __forceinline__ df sub_rn(df a, df b) { return df_add(a, -b); }
+__device__ __forceinline__ df mul_rn(df a, df b) { return df_mul(a, b); }
+__device__ __forceinline__ df fma_rn(df a, df b, df c) { return df_add(df_mul(a, b), c); }
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
 // The new iterate of one row from its gathered sum s (Sec. 4.1), given

@@ -90,6 +90,15 @@ constexpr int kDefaultMaxRounds = 2000;
 constexpr int kPrepBlocks = 1024;  // CTAs of the fixed-order reductions
 constexpr int kMaxWidth = 16;      // widest tile of vectors a round kernel takes
 
+// A double-float value: hi + lo, |lo| <= ulp(hi) / 2 (CPAA_DF64).  The
+// arithmetic is in device_common.cuh.
+struct df {
+    float hi, lo;
+    df() = default;
+    __host__ __device__ explicit df(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
+    __host__ __device__ df(float h, float l) : hi(h), lo(l) {}
+};
+
 // Workspace of the solves, grown on demand and reused (one solve per graph at
 // a time).  Vectors of a tile of W columns are row-major [rows x W].
 struct Workspace {
@@ -185,11 +194,13 @@ struct cpaa_graph {
     double *deg64 = nullptr;         // d_u
     double *inv_deg64 = nullptr;     // 1 / d_u
     double *inv2_deg64 = nullptr;    // 2 / d_u (the recurrence's factor)
+    cpaa::df *deg_df = nullptr;      // d_u and 2 / d_u as double-floats (CPAA_DF64)
+    cpaa::df *inv2_deg_df = nullptr;
     float *deg32 = nullptr;
     float *inv_deg32 = nullptr;
     float *inv2_deg32 = nullptr;
     int64_t device_bytes = 0;
-    int tuned_width[3] = {0, 0, 0};  // batch tile width picked by the autotuner, per precision
+    int tuned_width[4] = {0, 0, 0, 0};  // batch tile width picked by the autotuner, per precision
     cpaa::Workspace ws;
 };
 

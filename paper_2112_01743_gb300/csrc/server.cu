@@ -630,7 +630,7 @@ extern "C" cpaa_status cpaa_server_create(size_t device_mem_budget, const cpaa_o
         o.precision = CPAA_F32;
     }
     if (o.precision != CPAA_F64 && o.precision != CPAA_F32 && o.precision != CPAA_BF16)
-        return fail(CPAA_EINVAL, "unknown precision");
+        return fail(CPAA_EINVAL, "the server runs in FP64, FP32 or BF16");
     if (o.normalize != 0 && o.normalize != 1) return fail(CPAA_EINVAL, "normalize must be 0 or 1");
     if (o.stop_rule != CPAA_STOP_RIGOROUS && o.stop_rule != CPAA_STOP_POSTERIORI)
         return fail(CPAA_EINVAL, "unknown stop_rule");

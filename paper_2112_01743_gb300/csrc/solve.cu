@@ -27,6 +27,8 @@ __device__ __forceinline__ void put(__nv_bfloat16 *p, double v) { *p = __double2
 __device__ __forceinline__ double get(const double *p) { return *p; }
 __device__ __forceinline__ double get(const float *p) { return (double)*p; }
 __device__ __forceinline__ double get(const __nv_bfloat16 *p) { return (double)__bfloat162float(*p); }
+__device__ __forceinline__ void put(df *p, double v) { *p = df(v); }
+__device__ __forceinline__ double get(const df *p) { return __dadd_rn((double)p->hi, (double)p->lo); }
 
 // Fixed-shape CTA sum of NQ values per thread into out[0..NQ).
 template <int NQ>
@@ -135,7 +137,7 @@ __global__ void __launch_bounds__(kThreads) finalize_kernel(const TileCols cols,
     }
 }
 
-static size_t store_bytes(int prec) { return prec == CPAA_F64 ? 8 : prec == CPAA_F32 ? 4 : 2; }
+static size_t store_bytes(int prec) { return prec == CPAA_F64 || prec == CPAA_DF64 ? 8 : prec == CPAA_F32 ? 4 : 2; }
 
 int stats_blocks(int64_t n) { return (int)std::min<int64_t>((n + kThreads - 1) / kThreads, kPrepBlocks); }
 
@@ -291,6 +293,7 @@ static cudaError_t tile_phase(cpaa_graph *g, const TileJob &job, cudaStream_t st
         case CPAA_F64: return tile_kernels_w<double, double>(g, job, st, phase, final_src);
         case CPAA_F32: return tile_kernels_w<float, float>(g, job, st, phase, final_src);
         case CPAA_BF16: return tile_kernels_w<__nv_bfloat16, float>(g, job, st, phase, final_src);
+        case CPAA_DF64: return tile_kernels_w<df, df>(g, job, st, phase, final_src);
     }
     return cudaErrorInvalidValue;
 }
@@ -486,9 +489,11 @@ static cpaa_status solve_one(cpaa_graph *g, const double *p, double c, double to
     if (!(c > 0.0 && c < 1.0)) return fail(CPAA_EINVAL, "damping c must lie in (0, 1)");
     if (opt.fixed_rounds < 0) return fail(CPAA_EINVAL, "fixed_rounds < 0");
     if (opt.fixed_rounds == 0 && !(tol > 0.0)) return fail(CPAA_EINVAL, "tol must be > 0");
-    if (opt.precision != CPAA_F64 && opt.precision != CPAA_F32 && opt.precision != CPAA_BF16)
+    if (opt.precision != CPAA_F64 && opt.precision != CPAA_F32 && opt.precision != CPAA_BF16 &&
+        opt.precision != CPAA_DF64)
         return fail(CPAA_EINVAL, "unknown precision");
-    if (power && opt.precision == CPAA_BF16) return fail(CPAA_EINVAL, "the power method runs in FP64 or FP32");
+    if (power && opt.precision != CPAA_F64 && opt.precision != CPAA_F32)
+        return fail(CPAA_EINVAL, "the power method runs in FP64 or FP32");
     if (opt.normalize != 0 && opt.normalize != 1) return fail(CPAA_EINVAL, "normalize must be 0 or 1");
     if (opt.stop_rule != CPAA_STOP_RIGOROUS && opt.stop_rule != CPAA_STOP_POSTERIORI)
         return fail(CPAA_EINVAL, "unknown stop_rule");

@@ -141,6 +141,20 @@ __device__ __forceinline__ void store_row(T *p, const T (&v)[W], bool stream) {
     }
 }
 
+// Warp shuffle and L2-coherent load of an arithmetic value (a double-float
+// moves as its two halves).
+__device__ __forceinline__ float shfl_xor(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double shfl_xor(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ df shfl_xor(df v, int o) {
+    return df(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+}
+__device__ __forceinline__ float ld_cg(const float *p) { return __ldcg(p); }
+__device__ __forceinline__ double ld_cg(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ df ld_cg(const df *p) {
+    const float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+    return df(v.x, v.y);
+}
+
 // Gathered neighbour row j: W values in arithmetic precision.
 template <int P, int W>
 __device__ __forceinline__ void gather_row(const typename Prec<P>::S *y, int j,
@@ -237,15 +251,15 @@ __device__ __forceinline__ void warp_item_sums(A (&tT)[W], A (&tA)[W], double *i
 #pragma unroll
     for (int b = 0; b < W; ++b)
         for (int o = 16; o > 0; o >>= 1) {
-            tT[b] += __shfl_xor_sync(0xffffffffu, tT[b], o);
-            tA[b] += __shfl_xor_sync(0xffffffffu, tA[b], o);
+            tT[b] += shfl_xor(tT[b], o);
+            tA[b] += shfl_xor(tA[b], o);
         }
     if ((threadIdx.x & 31) == 0) {
         double *d = ipart + item * 2 * W;
 #pragma unroll
         for (int b = 0; b < W; ++b) {
-            d[b] = (double)tT[b];
-            d[W + b] = (double)tA[b];
+            d[b] = to_double(tT[b]);
+            d[W + b] = to_double(tA[b]);
         }
     }
 }
@@ -258,7 +272,7 @@ __device__ __forceinline__ void cta_sum_w(A (&v)[W], A (&s_w)[kWarps][W]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int b = 0; b < W; ++b)
-        for (int o = 16; o > 0; o >>= 1) v[b] += __shfl_xor_sync(0xffffffffu, v[b], o);
+        for (int o = 16; o > 0; o >>= 1) v[b] += shfl_xor(v[b], o);
     if (lane == 0)
 #pragma unroll
         for (int b = 0; b < W; ++b) s_w[warp][b] = v[b];
@@ -321,7 +335,7 @@ __device__ __forceinline__ void hub_tile(const StepParams<P, W> &p, int4 t, unsi
         for (int b = 0; b < W; ++b) part[b] = A(0);
         for (int c = tid; c < nt; c += kThreads)
 #pragma unroll
-            for (int b = 0; b < W; ++b) part[b] += __ldcg(p.long_part + (int64_t)(slot + c) * W + b);
+            for (int b = 0; b < W; ++b) part[b] += ld_cg(p.long_part + (int64_t)(slot + c) * W + b);
         __syncthreads();  // s_w is free again
         cta_sum_w<A, W>(part, s_w);
         if (tid == 0) {
@@ -334,8 +348,8 @@ __device__ __forceinline__ void hub_tile(const StepParams<P, W> &p, int4 t, unsi
                 double *d = p.ipart + (int64_t)h * 2 * W;
 #pragma unroll
                 for (int b = 0; b < W; ++b) {
-                    d[b] = (double)tT[b];
-                    d[W + b] = (double)tA[b];
+                    d[b] = to_double(tT[b]);
+                    d[W + b] = to_double(tA[b]);
                 }
             }
             p.long_cnt[hub] = 0;  // ready for the next round
@@ -486,7 +500,7 @@ __global__ void __launch_bounds__(kThreads) cheb_step_kernel(const StepParams<P,
         // for narrow tiles the row's own operands are fetched before the gather
         // so that their latency overlaps it
         constexpr bool kEarly = W <= 4;
-        A inv = 0, d = 0;
+        A inv = A(0), d = A(0);
         RowOps<P, W> o;
         if (live) {
             inv = ld_once(p.inv_deg + r);
@@ -609,6 +623,9 @@ static cudaError_t launch_typed(const StepLaunch &s) {
     if constexpr (P == CPAA_F64) {
         p.deg = g->deg64;
         p.inv_deg = s.power ? g->inv_deg64 : g->inv2_deg64;
+    } else if constexpr (P == CPAA_DF64) {
+        p.deg = g->deg_df;
+        p.inv_deg = g->inv2_deg_df;  // no power-method rounds in this format
     } else {
         p.deg = g->deg32;
         p.inv_deg = s.power ? g->inv_deg32 : g->inv2_deg32;
@@ -672,6 +689,7 @@ void prepare_step(int precision, int width) {
         case CPAA_F64: prepare_w<CPAA_F64>(width); break;
         case CPAA_F32: prepare_w<CPAA_F32>(width); break;
         case CPAA_BF16: prepare_w<CPAA_BF16>(width); break;
+        case CPAA_DF64: prepare_w<CPAA_DF64>(width); break;
     }
 }
 
@@ -680,6 +698,7 @@ cudaError_t launch_step(const StepLaunch &s) {
         case CPAA_F64: return launch_w<CPAA_F64>(s);
         case CPAA_F32: return launch_w<CPAA_F32>(s);
         case CPAA_BF16: return launch_w<CPAA_BF16>(s);
+        case CPAA_DF64: return launch_w<CPAA_DF64>(s);
     }
     return cudaErrorInvalidValue;
 }

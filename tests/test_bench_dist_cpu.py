@@ -50,6 +50,7 @@ def test_alg_bytes_formula():
     n, nnz = 10, 100
     assert bench.alg_bytes_per_round(n, nnz, "f64") == 4 * nnz + 4 * (n + 1) + 4 * n + 24 * n + 16 * n
     assert bench.alg_bytes_per_round(n, nnz, "f32") == 4 * nnz + 4 * (n + 1) + 4 * n + 12 * n + 8 * n + 8 * n
+    assert bench.alg_bytes_per_round(n, nnz, "df64") == bench.alg_bytes_per_round(n, nnz, "f64")
 
 
 def test_reference_arm_json_line():

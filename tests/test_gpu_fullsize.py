@@ -71,15 +71,18 @@ def test_config_16M_f64_and_f32(pkg, big_chung_lu):
     p = torch.full((n,), 1.0 / n, dtype=torch.float64, device="cuda")
     pi64, i64 = _solve(pkg, G, p, 0.85, 1e-6, precision=pkg.CPAA_F64)
     pi32, i32 = _solve(pkg, G, p, 0.85, 1e-6, precision=pkg.CPAA_F32)
-    assert i64.rounds == i32.rounds
+    pidf, idf = _solve(pkg, G, p, 0.85, 1e-6, precision=pkg.CPAA_DF64)
+    assert i64.rounds == i32.rounds == idf.rounds
     hp = np.full(n, 1.0 / n)
     assert i64.rounds == O.rounds_needed(0.85, 1e-6, O.kappa(rp, hp))
     ref = O.cpaa(rp, cx, hp, 0.85, i64.rounds)
     e64 = _l1(pi64, ref)
     e32 = _l1(pi32, ref) / np.abs(ref).sum()
-    print("16M: rounds %d, FP64 L1 %.3e, FP32 rel L1 %.3e" % (i64.rounds, e64, e32))
+    edf = _l1(pidf, ref)
+    print("16M: rounds %d, FP64 L1 %.3e, FP32 rel L1 %.3e, DF64 L1 %.3e" % (i64.rounds, e64, e32, edf))
     assert e64 <= 1e-12
     assert e32 <= 1e-6
+    assert edf <= 1e-12
 
 
 def test_config_16M_seeded_sample(pkg, big_chung_lu):
@@ -91,10 +94,12 @@ def test_config_16M_seeded_sample(pkg, big_chung_lu):
     p = torch.as_tensor(hp).cuda()
     pi64, i64 = _solve(pkg, G, p, 0.85, 1e-6, precision=pkg.CPAA_F64)
     pi32, i32 = _solve(pkg, G, p, 0.85, 1e-6, precision=pkg.CPAA_F32)
+    pidf, idf = _solve(pkg, G, p, 0.85, 1e-6, precision=pkg.CPAA_DF64)
     ref = O.cpaa(rp, cx, hp, 0.85, i64.rounds)
     assert i64.rounds == O.rounds_needed(0.85, 1e-6, O.kappa(rp, hp))
     assert _l1(pi64, ref) <= 1e-12
     assert _l1(pi32, ref) / np.abs(ref).sum() <= 1e-6
+    assert _l1(pidf, ref) <= 1e-12
 
 
 def test_config_grid_precision_study(pkg):
@@ -108,7 +113,8 @@ def test_config_grid_precision_study(pkg):
     del g
     p = torch.full((n,), 1.0 / n, dtype=torch.float64, device="cuda")
     res = {}
-    for name, prec in (("f64", pkg.CPAA_F64), ("f32", pkg.CPAA_F32), ("bf16", pkg.CPAA_BF16)):
+    for name, prec in (("f64", pkg.CPAA_F64), ("f32", pkg.CPAA_F32), ("bf16", pkg.CPAA_BF16),
+                       ("df64", pkg.CPAA_DF64)):
         res[name] = _solve(pkg, G, p, 0.85, 1e-6, precision=prec)
     M = res["f64"][1].rounds
     assert all(r[1].rounds == M for r in res.values())
@@ -116,6 +122,7 @@ def test_config_grid_precision_study(pkg):
     errs = {k: _l1(v[0], ref) for k, v in res.items()}
     print("grid: rounds %d, L1 errors %s" % (M, errs))
     assert errs["f64"] <= 1e-12
+    assert errs["df64"] <= 1e-12
     assert errs["f32"] <= 1e-6
     assert errs["bf16"] <= 5e-2
     G.close()

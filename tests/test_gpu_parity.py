@@ -83,6 +83,22 @@ def test_f32_matches_oracle(pkg, uploaded, gi):
         assert rel <= 1e-6, (g.name, pname, rel)
 
 
+@pytest.mark.parametrize("gi", range(len(GRAPHS)), ids=[g.name for g in GRAPHS])
+def test_df64_matches_oracle(pkg, uploaded, gi):
+    """Double-float iterates (pairs of FP32, about 48 significant bits): the
+    FP64 bound, L1 <= 1e-12 against the oracle for the same M, at a fixed M and
+    from the stopping rule, for three vectors."""
+    g, G = GRAPHS[gi], uploaded[gi]
+    rp, cx = g.numpy()
+    for pname, p in _p_variants(g.n).items():
+        pi, info = solve(pkg, G, p, 0.85, 1e-9, precision=pkg.CPAA_DF64)
+        ref = O.cpaa(rp, cx, p, 0.85, info.rounds)
+        assert np.abs(pi - ref).sum() <= 1e-12, (g.name, pname)
+        pi, _ = solve(pkg, G, p, 0.95, fixed_rounds=60, precision=pkg.CPAA_DF64)
+        ref = O.cpaa(rp, cx, p, 0.95, 60)
+        assert np.abs(pi - ref).sum() <= 1e-12, (g.name, pname, "M=60")
+
+
 @pytest.mark.parametrize("gi", [0, 3, 12, 13, 14], ids=lambda i: GRAPHS[i].name)
 def test_bf16_error_is_bounded(pkg, uploaded, gi):
     g, G = GRAPHS[gi], uploaded[gi]
@@ -186,7 +202,7 @@ def test_batch_columns_equal_single(pkg, uploaded):
     seeds = ci.seed_vectors(g.n, B, seed=3)
     P = ci.seed_dense(g.n, seeds)
     cs = np.array([0.5, 0.85, 0.95, 0.85, 0.7])
-    for prec in (pkg.CPAA_F64, pkg.CPAA_F32):
+    for prec in (pkg.CPAA_F64, pkg.CPAA_F32, pkg.CPAA_DF64):
         Pd = torch.as_tensor(P).cuda()
         PI = torch.empty_like(Pd)
         infos = G.solve_batch(B, Pd, cs, 1e-7, PI, precision=prec)

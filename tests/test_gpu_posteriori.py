@@ -148,3 +148,7 @@ def test_stop_rule_invalid(pkg, uploaded):
     out = torch.empty_like(pd)
     with pytest.raises(pkg.CpaaError, match="power method"):
         G.power_solve(pd, 0.85, 1e-6, out, stop_rule=pkg.CPAA_STOP_POSTERIORI)
+    with pytest.raises(pkg.CpaaError, match="power method"):
+        G.power_solve(pd, 0.85, 1e-6, out, precision=pkg.CPAA_DF64)
+    with pytest.raises(pkg.CpaaError, match="server"):
+        pkg.Server(1 << 30, precision=pkg.CPAA_DF64)
