@@ -105,7 +105,7 @@ def test_posteriori_f32_matches_oracle(pkg, uploaded, gi):
         assert np.abs(pi - ref).sum() / np.abs(ref).sum() <= 1e-6, pname
 
 
-@pytest.mark.parametrize("prec", ["F64", "F32"])
+@pytest.mark.parametrize("prec", ["F64", "F32", "DF64"])
 def test_posteriori_batch_columns_equal_single(pkg, uploaded, prec):
     g, G = GRAPHS[1], uploaded[1]
     P = ci.seed_dense(g.n, ci.seed_vectors(g.n, 6, seed=21))
