@@ -701,7 +701,9 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk,
-        "gpu_launches": sum(i.rounds + 6 for i in infos),
+        # per solve: stats + its block sum, prep, the rounds, the last round's two
+        # fixed-order sum kernels, the normaliser's two kernels and the finalisation
+        "gpu_launches": sum(i.rounds + 8 for i in infos),
         "f64": f64,
         "power": power,
         "batch": batch,

@@ -286,21 +286,14 @@ __device__ __forceinline__ void cta_sum_w(A (&v)[W], A (&s_w)[kWarps][W]) {
         }
 }
 
-// Buffers of the CTA items' shared arrays: two (no trailing barrier per item)
-// where a long chunk's slice sums fit the static shared-memory budget.
-template <class A, int W> constexpr int kItemBufs = sizeof(A) * W <= 16 ? 2 : 1;
-
 // One hub tile (p.hub_tile entries of a hub row) by one CTA.  The CTA
 // that takes the row's last ticket adds the tile partials in tile order and
 // writes the row (an atomic ticket: no CTA waits for another).
 template <int P, int W>
-__device__ __forceinline__ void hub_tile(const StepParams<P, W> &p, int4 t, unsigned active, int par) {
+__device__ __forceinline__ void hub_tile(const StepParams<P, W> &p, int4 t, unsigned active) {
     using A = typename Prec<P>::A;
-    // two buffers, alternating with the CTA's items (see cheb_step_kernel)
-    __shared__ A s_w2[kItemBufs<A, W>][kWarps][W];
-    __shared__ int s_last2[kItemBufs<A, W>];
-    A(&s_w)[kWarps][W] = s_w2[par];
-    int &s_last = s_last2[par];
+    __shared__ A s_w[kWarps][W];
+    __shared__ int s_last;
     const int tid = threadIdx.x;
     const int h = t.x, j = t.y, slot = t.z, hub = t.w - 1;
     const int e0 = p.hub_row_ptr[h], e1 = p.hub_row_ptr[h + 1];
@@ -362,8 +355,7 @@ __device__ __forceinline__ void hub_tile(const StepParams<P, W> &p, int4 t, unsi
             p.long_cnt[hub] = 0;  // ready for the next round
         }
     }
-    // with one buffer, s_w and s_last are reused by the CTA's next item
-    if constexpr (kItemBufs<A, W> == 1) __syncthreads();
+    __syncthreads();  // s_w and s_last are reused by the CTA's next item
 }
 
 // Groups of kSellVec entries a lane gathers at once in a short chunk (single
@@ -439,10 +431,9 @@ __device__ __forceinline__ void chunk_sum(const StepParams<P, W> &p, const int32
 // A long chunk by one CTA: warp w sums slice w of the entries of all 32
 // rows; the slices are added in warp order and warp 0 finishes the rows.
 template <int P, int W>
-__device__ __forceinline__ void long_chunk(const StepParams<P, W> &p, int4 dsc, unsigned active, int par) {
+__device__ __forceinline__ void long_chunk(const StepParams<P, W> &p, int4 dsc, unsigned active) {
     using A = typename Prec<P>::A;
-    __shared__ A s_part2[kItemBufs<A, W>][kWarps][W][kChunkRows];
-    A(&s_part)[kWarps][W][kChunkRows] = s_part2[par];
+    __shared__ A s_part[kWarps][W][kChunkRows];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int c = dsc.x;
     const int64_t off = (int64_t)dsc.y * (kChunkRows * kSellVec);
@@ -477,8 +468,7 @@ __device__ __forceinline__ void long_chunk(const StepParams<P, W> &p, int4 dsc, 
             warp_item_sums<A, W>(tT, tA, p.ipart, p.n_hub + c);
         }
     }
-    // with one buffer, s_part is reused by the CTA's next item
-    if constexpr (kItemBufs<A, W> == 1) __syncthreads();
+    __syncthreads();  // s_part is reused by the CTA's next item
 }
 
 // Persistent grid (as many CTAs as fit on the GPU at once).  Phase 1: CTAs
@@ -494,12 +484,8 @@ __global__ void __launch_bounds__(kThreads) cheb_step_kernel(const StepParams<P,
     if (p.stop && active == 0) return;
     const int n_cta_items = p.num_hub_tiles + p.num_long_chunks;
     for (int it = blockIdx.x; it < n_cta_items; it += gridDim.x) {
-        // the shared buffers alternate with the CTA's items: every item passes at
-        // least one CTA barrier after its last read of its buffer, so an item
-        // two steps later can write that buffer without a trailing barrier
-        const int par = kItemBufs<A, W> == 1 ? 0 : (int)((it / gridDim.x) & 1);
-        if (it < p.num_hub_tiles) hub_tile<P, W>(p, p.hub_tiles[it], active, par);
-        else long_chunk<P, W>(p, ld_stream4(&p.chunk_desc[it - p.num_hub_tiles].x), active, par);
+        if (it < p.num_hub_tiles) hub_tile<P, W>(p, p.hub_tiles[it], active);
+        else long_chunk<P, W>(p, ld_stream4(&p.chunk_desc[it - p.num_hub_tiles].x), active);
     }
     const int lane = threadIdx.x & 31;
     const int nwarps = (int)gridDim.x * kWarps;
