@@ -397,8 +397,8 @@ def run_serving(pkg, args):
             out.append((gi, seeds, float(rng.choice([0.5, 0.85, 0.95]))))
         return out
 
-    def run(queries, rate, stop_rule=pkg.CPAA_STOP_RIGOROUS):
-        S = pkg.Server(64 << 30, stop_rule=stop_rule)
+    def run(queries, rate, stop_rule=pkg.CPAA_STOP_RIGOROUS, fused=False):
+        S = pkg.Server(64 << 30, stop_rule=stop_rule, fused=fused)
         ids = [S.add_graph(x, 16) for x in G]
         tickets = []
         lock = threading.Condition()
@@ -447,6 +447,7 @@ def run_serving(pkg, args):
     sat_queries = make(args.serve_queries // 4)
     sat_qps, sat_st = run(sat_queries, None)
     post_qps, post_st = run(sat_queries, None, pkg.CPAA_STOP_POSTERIORI)
+    fused_qps, fused_st = run(sat_queries, None, pkg.CPAA_STOP_RIGOROUS, True)
     rate = 0.7 * sat_qps
     qps, st = run(make(args.serve_queries), rate)
     for x in G:
@@ -462,7 +463,10 @@ def run_serving(pkg, args):
             "saturated_effective_gteps": sat_st["effective_gteps"], "completed": st["completed"],
             "failed": st["failed"],
             "posteriori_saturated_qps": post_qps, "posteriori_saturated_p50_ms": post_st["p50_us"] / 1e3,
-            "posteriori_saturated_p99_ms": post_st["p99_us"] / 1e3}
+            "posteriori_saturated_p99_ms": post_st["p99_us"] / 1e3,
+            "fused_saturated_qps": fused_qps, "fused_saturated_p50_ms": fused_st["p50_us"] / 1e3,
+            "fused_saturated_p99_ms": fused_st["p99_us"] / 1e3,
+            "fused_saturated_effective_gteps": fused_st["effective_gteps"]}
 
 
 def run_reference(args):

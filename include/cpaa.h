@@ -79,6 +79,10 @@ typedef enum { CPAA_F64 = 0, CPAA_F32 = 1, CPAA_BF16 = 2, CPAA_DF64 = 3 } cpaa_p
 #define CPAA_DEVICE_IO 1u   /* p / pi (P / PI) are device pointers */
 #define CPAA_TIME_ROUNDS 2u /* time the M round launches with CUDA events on the solve's
                                stream; the result is cpaa_info.rounds_ms */
+#define CPAA_SERVER_FUSED 4u /* cpaa_server_create: all graphs on one stream, each round of
+                                every graph with live queries in one kernel launch over the
+                                graphs' work lists, instead of one stream and one launch per
+                                graph (results are the same bits either way) */
 
 /* cpaa_options.stop_rule.  The paper runs a fixed M and bounds the truncation
  * by ERR_M = 2 beta^(M+1) / (1 + beta) (Eq. 41), a bound on the neglected

@@ -15,7 +15,7 @@ __all__ = [
     "CPAA_OK", "CPAA_EINVAL", "CPAA_ENOMEM", "CPAA_ENOTCONV", "CPAA_ECUDA", "CPAA_ETIMEOUT",
     "CPAA_EBUSY", "CPAA_ECANCELLED", "CPAA_ENOTFOUND",
     "CPAA_F64", "CPAA_F32", "CPAA_BF16", "CPAA_DF64", "CPAA_GRAPH_DEVICE_INPUT", "CPAA_GRAPH_VALIDATE",
-    "CPAA_DEVICE_IO", "CPAA_TIME_ROUNDS", "CPAA_STOP_RIGOROUS", "CPAA_STOP_POSTERIORI",
+    "CPAA_DEVICE_IO", "CPAA_TIME_ROUNDS", "CPAA_SERVER_FUSED", "CPAA_STOP_RIGOROUS", "CPAA_STOP_POSTERIORI",
     "cpaa_options_init", "cpaa_graph_create", "cpaa_graph_destroy", "cpaa_graph_info",
     "cpaa_solve", "cpaa_solve_batch", "cpaa_rounds_needed", "cpaa_l1_bound",
     "cpaa_status_string", "cpaa_last_error", "cpaa_solve_fixed_noalloc", "cpaa_power_solve", "Graph",
@@ -32,6 +32,7 @@ CPAA_DEVICE_IO = 1
 CPAA_NOALLOC_MAX_N = 1300000
 CPAA_SERVER_MAX_SEEDS = 64
 CPAA_TIME_ROUNDS = 2
+CPAA_SERVER_FUSED = 4
 CPAA_STOP_RIGOROUS, CPAA_STOP_POSTERIORI = 0, 1
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -281,11 +282,13 @@ def cpaa_solve_fixed_noalloc(n, nnz, row_ptr, col_idx, p, c, rounds, pi, normali
 
 
 def cpaa_server_create(budget_bytes, precision=CPAA_F32, normalize=0, max_rounds=0,
-                       stop_rule=CPAA_STOP_RIGOROUS):
+                       stop_rule=CPAA_STOP_RIGOROUS, fused=False):
     o = cpaa_options_init()
     o.precision = int(precision)
     o.normalize = int(normalize)
     o.stop_rule = int(stop_rule)
+    if fused:
+        o.flags |= CPAA_SERVER_FUSED
     if max_rounds:
         o.max_rounds = int(max_rounds)
     h = ctypes.c_void_p()
@@ -337,8 +340,8 @@ class Server:
     """Owning wrapper of a cpaa_server handle."""
 
     def __init__(self, budget_bytes, precision=CPAA_F32, normalize=0, max_rounds=0,
-                 stop_rule=CPAA_STOP_RIGOROUS):
-        self.handle = cpaa_server_create(budget_bytes, precision, normalize, max_rounds, stop_rule)
+                 stop_rule=CPAA_STOP_RIGOROUS, fused=False):
+        self.handle = cpaa_server_create(budget_bytes, precision, normalize, max_rounds, stop_rule, fused)
 
     def add_graph(self, graph, max_slots=0):
         return cpaa_server_add_graph(self.handle, graph.handle, max_slots)

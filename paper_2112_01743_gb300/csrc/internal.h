@@ -252,6 +252,9 @@ struct StepLaunch {
 };
 void prepare_step(int precision, int width);
 cudaError_t launch_step(const StepLaunch &s);
+// One round of up to 8 graphs in a single launch (same precision, width and
+// stream; FP64, FP32 or BF16).
+cudaError_t launch_step_multi(const StepLaunch *sl, int ng);
 
 // Solve pieces (solve.cu), shared by cpaa_solve and cpaa_solve_batch.
 int stats_blocks(int64_t n);

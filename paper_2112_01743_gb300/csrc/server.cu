@@ -43,6 +43,7 @@ namespace srv {
 
 using clk = std::chrono::steady_clock;
 constexpr int kInFlight = 4;
+constexpr int kMaxFusedGraphs = 8;  // graphs per fused round launch
 constexpr size_t kMaxQueue = size_t(1) << 20;
 
 __device__ __forceinline__ void sput(double *p, double v) { *p = v; }
@@ -196,6 +197,7 @@ struct GraphState {
     std::vector<double> deg;        // caller order
     std::vector<Slot> slots;
     std::deque<ReqP> pending;
+    bool own_stream = true;
     int64_t G = 0;       // rounds launched
     int64_t G_seen = 0;  // rounds whose completion the scheduler has processed
     cudaEvent_t ring[kInFlight] = {};
@@ -227,6 +229,8 @@ struct cpaa_server {
     size_t budget = 0, used = 0;
     int prec = CPAA_F32, normalize = 0, max_rounds = kDefaultMaxRounds;
     int posteriori = 0;  // stop rule CPAA_STOP_POSTERIORI
+    int fused = 0;       // CPAA_SERVER_FUSED: one stream, one round launch over all graphs
+    cudaStream_t fstream = nullptr;
     int device = 0;
     std::vector<std::unique_ptr<GraphState>> graphs;
     std::mutex mu;
@@ -362,7 +366,12 @@ static double us_since(clk::time_point a, clk::time_point b) {
 }
 
 // One scheduling pass over a graph; true if anything was launched.
-static bool step_graph(cpaa_server *s, GraphState &gs) {
+// The host side of a graph's next round: completed rounds processed,
+// cancellations and admissions made, and (if any column is live) the round's
+// launch described in sl.  Returns true when sl is to be launched; *admitted_any
+// tells whether queries joined.
+static bool plan_round(cpaa_server *s, GraphState &gs, StepLaunch &sl, unsigned *live_out, bool *admitted_any) {
+    *admitted_any = false;
     process_completed_rounds(s, gs);
     // at most kInFlight rounds queued: launch G+1 waits until round G+1-kInFlight
     // has completed and been processed (its ring entry is then free)
@@ -435,9 +444,11 @@ static bool step_graph(cpaa_server *s, GraphState &gs) {
         }
     }
     for (auto &a : admitted) slot_prep(s, gs, a.first, a.second);
-    if (!live) return !admitted.empty();
+    *admitted_any = !admitted.empty();
+    *live_out = live;
+    if (!live) return false;
 
-    StepLaunch sl;
+    sl = StepLaunch();
     sl.g = gs.g;
     sl.precision = s->prec;
     sl.width = gs.W;
@@ -479,7 +490,12 @@ static bool step_graph(cpaa_server *s, GraphState &gs) {
         sl.sa.stop = &gs.dstop->stop;
         sl.sa.stop_round = gs.dstop->round;
     }
-    if (launch_step(sl) != cudaSuccess) return false;
+    return true;
+}
+
+// The host side after a graph's round was launched: the stop state copied
+// out, the round counted, and columns at their last round finalised.
+static void after_round(cpaa_server *s, GraphState &gs, unsigned live) {
     const int64_t Gn = gs.G + 1;
     if (gs.dstop)
         copy_stop_kernel<<<1, 64, 0, gs.stream>>>(gs.dstop, gs.d_ring + Gn % kInFlight);
@@ -491,6 +507,52 @@ static bool step_graph(cpaa_server *s, GraphState &gs) {
         if (++gs.slots[b].k == gs.slots[b].req->M) due.push_back(b);
     }
     finish_slots(s, gs, due);
+}
+
+// One scheduling pass over a graph with its own stream; true if anything was
+// launched.
+static bool step_graph(cpaa_server *s, GraphState &gs) {
+    StepLaunch sl;
+    unsigned live = 0;
+    bool admitted = false;
+    if (!plan_round(s, gs, sl, &live, &admitted)) return admitted;
+    if (launch_step(sl) != cudaSuccess) return admitted;
+    after_round(s, gs, live);
+    return true;
+}
+
+// Fused mode: one scheduling pass over every graph, their rounds launched
+// together (one kernel per group of up to kMaxFusedGraphs graphs of one tile
+// width) on the server's single stream.
+static bool step_fused(cpaa_server *s, const std::vector<GraphState *> &gl) {
+    std::vector<StepLaunch> sls;
+    std::vector<std::pair<GraphState *, unsigned>> parts;
+    bool any = false;
+    for (auto *gs : gl) {
+        StepLaunch sl;
+        unsigned live = 0;
+        bool admitted = false;
+        if (plan_round(s, *gs, sl, &live, &admitted)) {
+            sls.push_back(sl);
+            parts.push_back({gs, live});
+        }
+        any |= admitted;
+    }
+    if (sls.empty()) return any;
+    std::vector<char> done(sls.size(), 0);
+    for (size_t i = 0; i < sls.size(); ++i) {
+        if (done[i]) continue;
+        std::vector<StepLaunch> group;
+        std::vector<size_t> members;
+        for (size_t j = i; j < sls.size() && (int)group.size() < kMaxFusedGraphs; ++j)
+            if (!done[j] && sls[j].width == sls[i].width) {
+                group.push_back(sls[j]);
+                members.push_back(j);
+                done[j] = 1;
+            }
+        if (launch_step_multi(group.data(), (int)group.size()) != cudaSuccess) continue;
+        for (size_t j : members) after_round(s, *parts[j].first, parts[j].second);
+    }
     return true;
 }
 
@@ -513,7 +575,11 @@ static void scheduler_main(cpaa_server *s) {
             for (auto &g : s->graphs) gl.push_back(g.get());
         }
         bool progressed = false;
-        for (auto *g : gl) progressed |= step_graph(s, *g);
+        if (s->fused) {
+            progressed = step_fused(s, gl);
+        } else {
+            for (auto *g : gl) progressed |= step_graph(s, *g);
+        }
         if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
 }
@@ -605,7 +671,7 @@ static void free_graph_state(GraphState &gs) {
     if (gs.h_slot) cudaFreeHost(gs.h_slot);
     for (auto &e : gs.ring) if (e) cudaEventDestroy(e);
     for (auto &sl : gs.slots) if (sl.done) cudaEventDestroy(sl.done);
-    if (gs.stream) cudaStreamDestroy(gs.stream);
+    if (gs.stream && gs.own_stream) cudaStreamDestroy(gs.stream);
 }
 
 static double percentile(std::vector<double> v, double q) {
@@ -636,13 +702,16 @@ extern "C" cpaa_status cpaa_server_create(size_t device_mem_budget, const cpaa_o
         return fail(CPAA_EINVAL, "unknown stop_rule");
     cpaa_server *s = new cpaa_server();
     s->posteriori = o.stop_rule == CPAA_STOP_POSTERIORI;
+    s->fused = (o.flags & CPAA_SERVER_FUSED) != 0;
     s->budget = device_mem_budget;
     s->prec = o.precision;
     s->normalize = o.normalize;
     s->max_rounds = o.max_rounds > 0 ? o.max_rounds : kDefaultMaxRounds;
     cudaGetDevice(&s->device);
     cudaError_t e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && s->fused) e = cudaStreamCreateWithFlags(&s->fstream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
+        if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
         delete s;
         return cuda_fail(e, "cudaStreamCreateWithFlags");
     }
@@ -681,7 +750,12 @@ extern "C" cpaa_status cpaa_server_add_graph(cpaa_server *s, cpaa_graph *g, int 
     } while (0)
     {
         const size_t vb = (size_t)(n + 1) * W * vbytes(s->prec), rb = (size_t)n * W * rbytes(s->prec);
-        SCK(cudaStreamCreateWithFlags(&gs->stream, cudaStreamNonBlocking));
+        if (s->fused) {  // every graph's work goes to the server's stream
+            gs->stream = s->fstream;
+            gs->own_stream = false;
+        } else {
+            SCK(cudaStreamCreateWithFlags(&gs->stream, cudaStreamNonBlocking));
+        }
         SALLOC(gs->y[0], vb);
         SALLOC(gs->y[1], vb);
         SALLOC(gs->rho, rb);
@@ -919,6 +993,7 @@ extern "C" cpaa_status cpaa_server_destroy(cpaa_server *s) {
     }
     for (auto &g : s->graphs) free_graph_state(*g);
     if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+    if (s->fstream) cudaStreamDestroy(s->fstream);
     delete s;
     return CPAA_OK;
 }

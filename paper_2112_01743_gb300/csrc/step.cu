@@ -471,13 +471,50 @@ __device__ __forceinline__ void long_chunk(const StepParams<P, W> &p, int4 dsc, 
     __syncthreads();  // s_part is reused by the CTA's next item
 }
 
+// A short SELL chunk by one warp: lane l sums row n_hub + 32 c + l and
+// finishes it; the chunk's partial sums go to its item slot in rounds that
+// take sums.
+template <int P, int W>
+__device__ __forceinline__ void short_chunk(const StepParams<P, W> &p, int4 dsc, unsigned active) {
+    using A = typename Prec<P>::A;
+    const int lane = threadIdx.x & 31;
+    const int c = dsc.x;
+    const int64_t off = (int64_t)dsc.y * (kChunkRows * kSellVec);
+    const int len = dsc.z;
+    const int64_t r = p.n_hub + (int64_t)c * kChunkRows + lane;
+    const bool live = r < p.n;
+    // for narrow tiles the row's own operands are fetched before the gather
+    // so that their latency overlaps it
+    constexpr bool kEarly = W <= 4;
+    A inv = A(0), d = A(0);
+    RowOps<P, W> o;
+    if (live) {
+        inv = ld_once(p.inv_deg + r);
+        if (p.reduce) d = ld_once(p.deg + r);  // only the round's sums need d
+        if constexpr (kEarly) load_ops<P, W>(p, r, o);
+    }
+    A acc[W];
+    chunk_sum<P, W>(p, p.sell_col + off + kSellVec * lane, 0, len, acc);
+    A yv[W];
+#pragma unroll
+    for (int b = 0; b < W; ++b) yv[b] = A(0);
+    if (live) {
+        if constexpr (!kEarly) load_ops<P, W>(p, r, o);
+        row_finish<P, W>(p, r, acc, inv, o, yv, active);
+    }
+    if (p.reduce) {
+        A tT[W], tA[W];
+        row_terms<A, W>(yv, d, tT, tA);
+        warp_item_sums<A, W>(tT, tA, p.ipart, p.n_hub + c);
+    }
+}
+
 // Persistent grid (as many CTAs as fit on the GPU at once).  Phase 1: CTAs
 // take the CTA-sized items (hub tiles, then long chunks) round-robin.  Phase
 // 2: every warp takes short chunks round-robin from the longest-first order,
 // which balances the warps without any atomics.
 template <int P, int W>
 __global__ void __launch_bounds__(kThreads) cheb_step_kernel(const StepParams<P, W> p) {
-    using A = typename Prec<P>::A;
     // columns stopped by the a-posteriori rule no longer accumulate; once
     // every column has stopped the remaining rounds do nothing
     const unsigned active = p.stop ? (p.active & ~*p.stop) : p.active;
@@ -487,40 +524,45 @@ __global__ void __launch_bounds__(kThreads) cheb_step_kernel(const StepParams<P,
         if (it < p.num_hub_tiles) hub_tile<P, W>(p, p.hub_tiles[it], active);
         else long_chunk<P, W>(p, ld_stream4(&p.chunk_desc[it - p.num_hub_tiles].x), active);
     }
-    const int lane = threadIdx.x & 31;
     const int nwarps = (int)gridDim.x * kWarps;
     for (int idx = p.num_long_chunks + (int)blockIdx.x * kWarps + (int)(threadIdx.x >> 5); idx < p.num_chunks;
-         idx += nwarps) {
-        const int4 dsc = ld_stream4(&p.chunk_desc[idx].x);
-        const int c = dsc.x;
-        const int64_t off = (int64_t)dsc.y * (kChunkRows * kSellVec);
-        const int len = dsc.z;
-        const int64_t r = p.n_hub + (int64_t)c * kChunkRows + lane;
-        const bool live = r < p.n;
-        // for narrow tiles the row's own operands are fetched before the gather
-        // so that their latency overlaps it
-        constexpr bool kEarly = W <= 4;
-        A inv = A(0), d = A(0);
-        RowOps<P, W> o;
-        if (live) {
-            inv = ld_once(p.inv_deg + r);
-            if (p.reduce) d = ld_once(p.deg + r);  // only the round's sums need d
-            if constexpr (kEarly) load_ops<P, W>(p, r, o);
-        }
-        A acc[W];
-        chunk_sum<P, W>(p, p.sell_col + off + kSellVec * lane, 0, len, acc);
-        A yv[W];
-#pragma unroll
-        for (int b = 0; b < W; ++b) yv[b] = A(0);
-        if (live) {
-            if constexpr (!kEarly) load_ops<P, W>(p, r, o);
-            row_finish<P, W>(p, r, acc, inv, o, yv, active);
-        }
-        if (p.reduce) {
-            A tT[W], tA[W];
-            row_terms<A, W>(yv, d, tT, tA);
-            warp_item_sums<A, W>(tT, tA, p.ipart, p.n_hub + c);
-        }
+         idx += nwarps)
+        short_chunk<P, W>(p, ld_stream4(&p.chunk_desc[idx].x), active);
+}
+
+// One round over several graphs in one launch (the server's fused mode): the
+// CTA items of every graph, then the short chunks of every graph, each work
+// list the graphs' lists back to back.  The per-graph parameters sit in the
+// launch's constant parameter space and are indexed in place.
+constexpr int kMaxFused = 8;
+template <int P, int W>
+struct MultiParams {
+    int ng;
+    int cta_off[kMaxFused + 1];   // prefix sums of the graphs' CTA items
+    int warp_off[kMaxFused + 1];  // prefix sums of the graphs' short chunks
+    StepParams<P, W> g[kMaxFused];
+};
+
+template <int P, int W>
+__global__ void __launch_bounds__(kThreads) cheb_step_multi_kernel(const __grid_constant__ MultiParams<P, W> mp) {
+    for (int it = blockIdx.x; it < mp.cta_off[mp.ng]; it += gridDim.x) {
+        int gi = 0;
+        while (it >= mp.cta_off[gi + 1]) ++gi;
+        const StepParams<P, W> &p = mp.g[gi];
+        const unsigned active = p.stop ? (p.active & ~*p.stop) : p.active;
+        if (p.stop && active == 0) continue;
+        const int local = it - mp.cta_off[gi];
+        if (local < p.num_hub_tiles) hub_tile<P, W>(p, p.hub_tiles[local], active);
+        else long_chunk<P, W>(p, ld_stream4(&p.chunk_desc[local - p.num_hub_tiles].x), active);
+    }
+    const int nwarps = (int)gridDim.x * kWarps;
+    for (int idx = (int)blockIdx.x * kWarps + (int)(threadIdx.x >> 5); idx < mp.warp_off[mp.ng]; idx += nwarps) {
+        int gi = 0;
+        while (idx >= mp.warp_off[gi + 1]) ++gi;
+        const StepParams<P, W> &p = mp.g[gi];
+        const unsigned active = p.stop ? (p.active & ~*p.stop) : p.active;
+        if (p.stop && active == 0) continue;
+        short_chunk<P, W>(p, ld_stream4(&p.chunk_desc[p.num_long_chunks + idx - mp.warp_off[gi]].x), active);
     }
 }
 
@@ -601,12 +643,25 @@ static int resident_ctas() {
 }
 
 template <int P, int W>
-static cudaError_t launch_typed(const StepLaunch &s) {
+static int resident_multi_ctas() {
+    static int per_sm = 0, sms = 0;
+    if (per_sm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cheb_step_multi_kernel<P, W>, kThreads, 0);
+        if (per_sm < 1) per_sm = 1;
+    }
+    return per_sm * sms;
+}
+
+// The kernel parameters of one graph's round.
+template <int P, int W>
+static void fill_params(const StepLaunch &s, StepParams<P, W> &p) {
     using A = typename Prec<P>::A;
     using S = typename Prec<P>::S;
     using R = typename Prec<P>::R;
     const cpaa_graph *g = s.g;
-    StepParams<P, W> p;
     p.hub_tiles = g->hub_tiles;
     p.num_hub_tiles = g->num_hub_tiles;
     p.hub_tile = g->hub_tile;
@@ -641,22 +696,79 @@ static cudaError_t launch_typed(const StepLaunch &s) {
     p.reduce = s.reduce;
     p.first = s.first;
     p.power = s.power;
+}
+
+// The two fixed-order sum kernels of a round that takes sums.  The item
+// slots are hub rows, then chunks; their split into blocks depends on the
+// graph alone, so the sums are the same bits for every tile width.
+template <int W>
+static void launch_sums(const StepLaunch &s) {
+    const cpaa_graph *g = s.g;
+    const int64_t items = (int64_t)g->n_hub + g->num_chunks;
+    const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>(kSumBlocks, (items + kThreads - 1) / kThreads));
+    const int64_t per = (items + nblk - 1) / nblk;
+    item_sum_kernel<W><<<nblk, kThreads, 0, s.stream>>>(s.ipart, items, per, s.ipart2);
+    item_final_kernel<W><<<1, 64, 0, s.stream>>>(s.ipart2, nblk, s.red, s.sa);
+}
+
+template <int P, int W>
+static cudaError_t launch_typed(const StepLaunch &s) {
+    const cpaa_graph *g = s.g;
+    StepParams<P, W> p;
+    fill_params<P, W>(s, p);
     // a small graph needs fewer CTAs than fit: one per CTA item plus one per
     // kWarps short chunks
     const int64_t needed = (int64_t)g->num_hub_tiles + g->num_long_chunks +
                            (g->num_chunks - g->num_long_chunks + kWarps - 1) / kWarps;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(resident_ctas<P, W>(), needed));
     cheb_step_kernel<P, W><<<grid, kThreads, 0, s.stream>>>(p);
-    if (s.reduce) {
-        // slots: hub rows, then chunks; the split into blocks depends on the
-        // graph alone, so the sums are the same bits for every tile width
-        const int64_t items = (int64_t)g->n_hub + g->num_chunks;
-        const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>(kSumBlocks, (items + kThreads - 1) / kThreads));
-        const int64_t per = (items + nblk - 1) / nblk;
-        item_sum_kernel<W><<<nblk, kThreads, 0, s.stream>>>(s.ipart, items, per, s.ipart2);
-        item_final_kernel<W><<<1, 64, 0, s.stream>>>(s.ipart2, nblk, s.red, s.sa);
-    }
+    if (s.reduce) launch_sums<W>(s);
     return cudaGetLastError();
+}
+
+// One round of ng graphs (same precision and width, same stream) in one launch.
+template <int P, int W>
+static cudaError_t launch_multi_typed(const StepLaunch *sl, int ng) {
+    MultiParams<P, W> mp;
+    mp.ng = ng;
+    mp.cta_off[0] = mp.warp_off[0] = 0;
+    for (int i = 0; i < ng; ++i) {
+        const cpaa_graph *g = sl[i].g;
+        fill_params<P, W>(sl[i], mp.g[i]);
+        mp.cta_off[i + 1] = mp.cta_off[i] + g->num_hub_tiles + g->num_long_chunks;
+        mp.warp_off[i + 1] = mp.warp_off[i] + (g->num_chunks - g->num_long_chunks);
+    }
+    const int64_t needed = (int64_t)mp.cta_off[ng] + (mp.warp_off[ng] + kWarps - 1) / kWarps;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(resident_multi_ctas<P, W>(), needed));
+    cheb_step_multi_kernel<P, W><<<grid, kThreads, 0, sl[0].stream>>>(mp);
+    for (int i = 0; i < ng; ++i)
+        if (sl[i].reduce) launch_sums<W>(sl[i]);
+    return cudaGetLastError();
+}
+
+template <int P>
+static cudaError_t launch_multi_w(const StepLaunch *sl, int ng) {
+    switch (sl[0].width) {
+        case 1: return launch_multi_typed<P, 1>(sl, ng);
+        case 2: return launch_multi_typed<P, 2>(sl, ng);
+        case 4: return launch_multi_typed<P, 4>(sl, ng);
+        case 8: return launch_multi_typed<P, 8>(sl, ng);
+        case 16: return launch_multi_typed<P, 16>(sl, ng);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_step_multi(const StepLaunch *sl, int ng) {
+    if (ng < 1 || ng > kMaxFused) return cudaErrorInvalidValue;
+    for (int i = 1; i < ng; ++i)
+        if (sl[i].precision != sl[0].precision || sl[i].width != sl[0].width || sl[i].stream != sl[0].stream)
+            return cudaErrorInvalidValue;
+    switch (sl[0].precision) {
+        case CPAA_F64: return launch_multi_w<CPAA_F64>(sl, ng);
+        case CPAA_F32: return launch_multi_w<CPAA_F32>(sl, ng);
+        case CPAA_BF16: return launch_multi_w<CPAA_BF16>(sl, ng);
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <int P>

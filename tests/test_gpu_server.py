@@ -189,3 +189,42 @@ def test_posteriori_rule_alone_equals_in_mix(pkg):
         S.close()
         for x in G:
             x.close()
+
+
+@pytest.mark.parametrize("rule", ["RIGOROUS", "POSTERIORI"])
+def test_fused_mode_matches_per_graph_mode(pkg, rule):
+    """CPAA_SERVER_FUSED (one launch per round over all graphs, one stream)
+    gives the same bits as the per-graph mode, alone and in a mix."""
+    graphs = [ci.chung_lu(5000, 40000, seed=31), ci.chung_lu(60000, 600000, seed=32),
+              ci.grid_deleted(100, 120, 0.2, seed=3)]
+    G = [upload(pkg, g) for g in graphs]
+    sr = getattr(pkg, "CPAA_STOP_" + rule)
+    qs = _queries(graphs, 40, seed=13)
+    out = {}
+    try:
+        for fused in (False, True):
+            S = pkg.Server(2 << 30, stop_rule=sr, fused=fused)
+            ids = [S.add_graph(x, 8) for x in G]
+            tickets = [S.submit(ids[g2], sd, w, c, tol) for g2, sd, w, c, tol in qs]
+            res = []
+            for (g2, sd, w, c, tol), t in zip(qs, tickets):
+                pi = np.empty(graphs[g2].n)
+                st, info = S.wait(t, pi, timeout_us=120_000_000)
+                assert st == pkg.CPAA_OK
+                res.append((pi, info.rounds))
+            out[fused] = res
+            S.close()
+        for (a, ra), (b, rb) in zip(out[False], out[True]):
+            assert ra == rb
+            assert np.array_equal(a, b)
+        # and against the oracle for a few of them
+        for i in (0, 17, 39):
+            g2, sd, w, c, tol = qs[i]
+            rp, cx = graphs[g2].numpy()
+            p = np.zeros(graphs[g2].n)
+            p[sd] = 1.0 / len(sd)
+            ref = O.cpaa(rp, cx, p, c, out[True][i][1])
+            assert np.abs(out[True][i][0] - ref).sum() / np.abs(ref).sum() <= 1e-6
+    finally:
+        for x in G:
+            x.close()
