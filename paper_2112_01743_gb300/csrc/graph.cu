@@ -302,7 +302,7 @@ extern "C" cpaa_status cpaa_graph_create(int64_t n, int64_t nnz, const int32_t *
         g->num_chunks = (int)L.chunk_off.size();
         g->num_long_chunks = 0;
         while (g->num_long_chunks < g->num_chunks &&
-               L.chunk_len[L.chunk_order[g->num_long_chunks]] > kLongChunk)
+               L.chunk_len[L.chunk_order[g->num_long_chunks]] > (nnz < (int64_t(1) << 22) ? kSmallLongChunk : kLongChunk))
             ++g->num_long_chunks;
         g->sell_entries = L.sell_entries;
 

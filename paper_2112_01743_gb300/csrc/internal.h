@@ -50,7 +50,9 @@ namespace cpaa {
 //
 // Defaults of the thresholds: timed on the 2^24-vertex Chung-Lu graph (single
 // FP32 vector) against hub thresholds of 1024 to 16384, tiles of 1024 to 16384
-// entries and long-chunk thresholds of 32 to 128, and on the 10^4-vertex one.
+// entries and long-chunk thresholds of 32 to 128, and on the 10^4-vertex one
+// (FP64), where graphs below 2^22 entries take long chunks above 8 entries
+// and hub tiles down to 512 entries: there a round is a chain of latencies.
 // ---------------------------------------------------------------------------
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
@@ -80,9 +82,19 @@ constexpr int kHeavyMin = CPAA_HEAVY_MIN;        // ... and >= this
 #define CPAA_LONG_CHUNK 32
 #endif
 constexpr int kHubDegree = CPAA_HUB_DEGREE;       // hub rows: degree above this (the cap)
-constexpr int kMinHubDegree = 64;
+#ifndef CPAA_MIN_HUB_DEGREE
+#define CPAA_MIN_HUB_DEGREE 64
+#endif
+#ifndef CPAA_MIN_HUB_TILE
+#define CPAA_MIN_HUB_TILE 512
+#endif
+#ifndef CPAA_SMALL_LONG_CHUNK
+#define CPAA_SMALL_LONG_CHUNK 8
+#endif
+constexpr int kMinHubDegree = CPAA_MIN_HUB_DEGREE;
 constexpr int kMaxHubTile = CPAA_MAX_HUB_TILE;    // entries of a hub tile (the cap)
-constexpr int kMinHubTile = 2048;
+constexpr int kMinHubTile = CPAA_MIN_HUB_TILE;
+constexpr int kSmallLongChunk = CPAA_SMALL_LONG_CHUNK;  // long-chunk threshold of small graphs
 constexpr int kLongChunk = CPAA_LONG_CHUNK;       // SELL chunks longer than this get a whole CTA
 constexpr int kSumBlocks = 256; // CTAs of the first level of the per-round item sums
 constexpr int kDefaultMaxRounds = 2000;
