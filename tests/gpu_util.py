@@ -21,9 +21,9 @@ def solve(pkg, G, p, c, tol=1e-8, **kw):
 def boundary_graphs():
     """Graphs that put rows on every side of the tiling thresholds plus ragged
     general graphs.  On graphs this small the hub threshold is 64 and a hub
-    tile holds 2048 entries, so the star centres (degree n - 1) fall on both
-    sides of one, two and five tiles; the larger graphs of the full-size tests
-    use the 4096 threshold and 8192-entry tiles."""
+    tile holds 512 entries, so the star centres (degree n - 1) fall on both
+    sides of four and eight tiles (2048 and 4096 entries); the larger graphs of
+    the full-size tests use the 4096 threshold and 8192-entry tiles."""
     gs = [ci.star(2046), ci.star(2047), ci.star(2048), ci.star(2049), ci.star(4097),
           ci.star(4098), ci.star(4099), ci.star(9999), ci.path(2), ci.cycle(3),
           ci.complete(70), ci.complete_bipartite(3, 3000),
