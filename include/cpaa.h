@@ -159,6 +159,20 @@ cpaa_status cpaa_graph_destroy(cpaa_graph *g);
 cpaa_status cpaa_graph_info(const cpaa_graph *g, int64_t *n, int64_t *nnz,
                             int64_t *device_bytes, int64_t *num_tiles);
 
+/* How cpaa_graph_create laid the graph out for the round kernels (no paper
+ * counterpart: this is the GPU layout).  Rows above hub_degree are hub rows,
+ * kept as CSR and cut into tiles of hub_tile entries, one CTA per tile; the
+ * other rows form SELL chunks of 32 rows (sell_entries counts their entries
+ * with padding), of which long_chunks, those above the long-chunk threshold,
+ * get a CTA and the rest a warp. */
+typedef struct {
+    int64_t hub_rows, hub_entries, hub_tiles;
+    int64_t chunks, long_chunks, sell_entries;
+    int hub_degree, hub_tile;
+} cpaa_layout;
+
+cpaa_status cpaa_graph_layout(const cpaa_graph *g, cpaa_layout *out);
+
 /* Personalised PageRank of one vector (Sec. 2.1, Algorithm 1).
  *   p    FP64[n], p >= 0, |sum p - 1| <= 1e-9
  *   c    damping factor, 0 < c < 1

@@ -16,8 +16,8 @@ __all__ = [
     "CPAA_EBUSY", "CPAA_ECANCELLED", "CPAA_ENOTFOUND",
     "CPAA_F64", "CPAA_F32", "CPAA_BF16", "CPAA_DF64", "CPAA_GRAPH_DEVICE_INPUT", "CPAA_GRAPH_VALIDATE",
     "CPAA_DEVICE_IO", "CPAA_TIME_ROUNDS", "CPAA_SERVER_FUSED", "CPAA_STOP_RIGOROUS", "CPAA_STOP_POSTERIORI",
-    "cpaa_options_init", "cpaa_graph_create", "cpaa_graph_destroy", "cpaa_graph_info",
-    "cpaa_solve", "cpaa_solve_batch", "cpaa_rounds_needed", "cpaa_l1_bound",
+    "cpaa_options_init", "cpaa_graph_create", "cpaa_graph_destroy", "cpaa_graph_info", "cpaa_graph_layout",
+    "CpaaLayout", "cpaa_solve", "cpaa_solve_batch", "cpaa_rounds_needed", "cpaa_l1_bound",
     "cpaa_status_string", "cpaa_last_error", "cpaa_solve_fixed_noalloc", "cpaa_power_solve", "Graph",
     "EXPORTED_SYMBOLS", "CPAA_NOALLOC_MAX_N", "CPAA_SERVER_MAX_SEEDS", "CpaaServerStats",
     "cpaa_server_create", "cpaa_server_add_graph", "cpaa_server_submit", "cpaa_server_wait",
@@ -40,7 +40,7 @@ library_path = os.path.join(HERE, "_build", "libcpaa.so")
 
 # Every function include/cpaa.h declares (the CPU test checks the exports).
 EXPORTED_SYMBOLS = [
-    "cpaa_options_init", "cpaa_graph_create", "cpaa_graph_destroy", "cpaa_graph_info",
+    "cpaa_options_init", "cpaa_graph_create", "cpaa_graph_destroy", "cpaa_graph_info", "cpaa_graph_layout",
     "cpaa_solve", "cpaa_solve_batch", "cpaa_rounds_needed", "cpaa_l1_bound",
     "cpaa_status_string", "cpaa_last_error", "cpaa_solve_fixed_noalloc", "cpaa_power_solve",
     "cpaa_server_create", "cpaa_server_add_graph", "cpaa_server_submit", "cpaa_server_wait",
@@ -52,6 +52,12 @@ class CpaaError(RuntimeError):
     def __init__(self, status, message):
         super().__init__("%s: %s" % (_status_name(status), message))
         self.status = status
+
+
+class CpaaLayout(ctypes.Structure):
+    _fields_ = [("hub_rows", ctypes.c_int64), ("hub_entries", ctypes.c_int64), ("hub_tiles", ctypes.c_int64),
+                ("chunks", ctypes.c_int64), ("long_chunks", ctypes.c_int64), ("sell_entries", ctypes.c_int64),
+                ("hub_degree", ctypes.c_int), ("hub_tile", ctypes.c_int)]
 
 
 class CpaaOptions(ctypes.Structure):
@@ -103,6 +109,8 @@ def lib():
     L.cpaa_graph_destroy.argtypes = [vp]
     L.cpaa_graph_info.restype = cint
     L.cpaa_graph_info.argtypes = [vp] + [ctypes.POINTER(i64)] * 4
+    L.cpaa_graph_layout.restype = cint
+    L.cpaa_graph_layout.argtypes = [vp, ctypes.POINTER(CpaaLayout)]
     L.cpaa_solve.restype = cint
     L.cpaa_solve.argtypes = [vp, vp, dbl, dbl, vp, ctypes.POINTER(CpaaOptions), ctypes.POINTER(CpaaInfo)]
     L.cpaa_power_solve.restype = cint
@@ -190,6 +198,12 @@ def cpaa_graph_create(n, nnz, row_ptr, col_idx, flags=0):
 
 def cpaa_graph_destroy(g):
     return _check(lib().cpaa_graph_destroy(g))
+
+
+def cpaa_graph_layout(g):
+    o = CpaaLayout()
+    _check(lib().cpaa_graph_layout(g, ctypes.byref(o)))
+    return {f: getattr(o, f) for f, _ in o._fields_}
 
 
 def cpaa_graph_info(g):
@@ -398,6 +412,9 @@ class Graph:
 
     def info(self):
         return cpaa_graph_info(self.handle)
+
+    def layout(self):
+        return cpaa_graph_layout(self.handle)
 
     def solve(self, p, c, tol, pi, **kw):
         return cpaa_solve(self.handle, p, c, tol, pi, **kw)

@@ -381,6 +381,20 @@ extern "C" cpaa_status cpaa_graph_destroy(cpaa_graph *g) {
     return CPAA_OK;
 }
 
+extern "C" cpaa_status cpaa_graph_layout(const cpaa_graph *g, cpaa_layout *out) {
+    clear_error();
+    if (!g || !out) return fail(CPAA_EINVAL, "graph or out is NULL");
+    out->hub_rows = g->n_hub;
+    out->hub_entries = g->hub_nnz;
+    out->hub_tiles = g->num_hub_tiles;
+    out->chunks = g->num_chunks;
+    out->long_chunks = g->num_long_chunks;
+    out->sell_entries = g->sell_entries;
+    out->hub_degree = g->hub_degree;
+    out->hub_tile = g->hub_tile;
+    return CPAA_OK;
+}
+
 extern "C" cpaa_status cpaa_graph_info(const cpaa_graph *g, int64_t *n, int64_t *nnz,
                                        int64_t *device_bytes, int64_t *num_tiles) {
     clear_error();

@@ -282,3 +282,23 @@ def test_round_graph_cache_across_keys_and_workspace_growth(pkg):
         assert info.rounds == M
         assert err <= (1e-12 if prec == "F64" else 1e-6 * np.abs(ref).sum()), (i, err)
     G.close()
+
+
+def test_layout_thresholds(pkg, uploaded):
+    """cpaa_graph_layout reports the tiling the thresholds give: on the small
+    boundary graphs a hub threshold of 64 and 512-entry hub tiles, hub rows
+    cut into ceil(degree / 512) tiles, every entry in a hub row or a chunk."""
+    for g, G in zip(GRAPHS, uploaded):
+        lay = G.layout()
+        rp, _ = g.numpy()
+        deg = np.diff(rp)
+        assert lay["hub_degree"] == 64 if g.nnz < 64 * 4096 else lay["hub_degree"] == min(4096, g.nnz // 4096)
+        assert lay["hub_tile"] == max(512, 2 * lay["hub_degree"])
+        hub = deg[deg > lay["hub_degree"]]
+        assert lay["hub_rows"] == hub.size
+        assert lay["hub_entries"] == hub.sum()
+        assert lay["hub_tiles"] == int(np.sum((hub + lay["hub_tile"] - 1) // lay["hub_tile"]))
+        rest = g.n - hub.size
+        assert lay["chunks"] == (rest + 31) // 32
+        assert lay["sell_entries"] >= deg.sum() - hub.sum()
+        assert 0 <= lay["long_chunks"] <= lay["chunks"]
