@@ -6,13 +6,15 @@
 //   host:      kappa = sqrt(nnz) sqrt(sum p^2/d); M from the L1 bound;
 //   prep:      y_0 = D^-1 p, rho = (c_0/2) y_0 (Algorithm 1's initial
 //              accumulator, in scaled space), comp = 0;
-//   rounds:    max M launches of the round kernel (step.cu); a vector stops
-//              accumulating after its own M;
+//   rounds:    max M launches of the round kernel (step.cu), captured once
+//              as a CUDA graph per key and replayed; a vector stops
+//              accumulating after its own M, or earlier under the
+//              a-posteriori rule (decided on the device after each round);
 //   finalize:  pi = d * rho / sum(d * rho) (Algorithm 1's last line) or
 //              (1 - c) d * rho (Sec. 2.1), the sum in a fixed order.
-// Every sum a vector's result depends on runs in an order fixed by n alone,
-// and every rounding is an explicit intrinsic, so a vector gives the same bits
-// alone (cpaa_solve) and in any batch.
+// Every sum a vector's result depends on runs in an order fixed by the graph
+// alone, and every rounding is an explicit intrinsic, so a vector gives the
+// same bits alone (cpaa_solve) and in any batch.
 #include <algorithm>
 #include <cmath>
 #include <cstring>

@@ -10,9 +10,10 @@
 //     y_1[u]     = (1/d_u) sum_{j in N(u)} y_0[j]                  (k = 1)
 //     y_{k+1}[u] = (2/d_u) sum_{j in N(u)} y_k[j] - y_{k-1}[u]     (k >= 1)
 // which is T_{k+1} = 2 P T_k - T_{k-1} (Chebyshev property (3), Sec. 2.2)
-// divided by d_u.  The accumulator is rho = D^-1 pibar, rho += c_k y_k, and
-// the finalisation multiplies by d_u again.  y_{k+1} overwrites y_{k-1} in
-// place: row u is the only reader of y_{k-1}[u].
+// divided by d_u; the kernel reads 2/d_u and makes the update one fused
+// multiply-add.  The accumulator is rho = D^-1 pibar, rho += c_k y_k, and the
+// finalisation multiplies by d_u again.  y_{k+1} overwrites y_{k-1} in place:
+// row u is the only reader of y_{k-1}[u].
 //
 // Layout: vector b of a tile is column b of a row-major [(n+1) x W] array
 // (row n is the padding sentinel, kept at zero).  Column b accumulates while
@@ -26,13 +27,16 @@
 // them, are the same bits for a vector alone and in any tile.
 //
 // Work split (internal.h): a persistent grid.  CTAs first take the hub tiles
-// (one tile of a hub row each) and the long SELL chunks (more than kLongChunk
-// entries per row, split over the CTA's warps) round-robin; then every warp
-// takes short SELL chunks, one lane per row, round-robin from the
-// longest-first order (chunk descriptors are stored in that order).  Every sum runs in a fixed order (a lane adds its
-// row's entries in CSR order, slices are added in warp order; hub tiles use
-// shuffle trees over thread-strided sums and the tiles are added in tile
-// order), so a result never depends on scheduling.
+// (one tile of a hub row each) and the long SELL chunks (above the long-chunk
+// threshold, split over the CTA's warps) round-robin; then every warp takes
+// short SELL chunks, one lane per row, round-robin from the longest-first
+// order (chunk descriptors are stored in that order).  Every sum runs in a
+// fixed order (a lane adds its row's entries in CSR order, slices are added
+// in warp order; hub tiles use shuffle trees over thread-strided sums and the
+// tiles are added in tile order), so a result never depends on scheduling.
+//
+// Number formats (device_common.cuh): FP64, FP32 and BF16 iterates, and
+// double-float pairs of FP32 (DF64) whose arithmetic runs on the FP32 pipes.
 #include <algorithm>
 #include <cstring>
 
