@@ -217,9 +217,10 @@ cpaa_status cpaa_solve_batch(cpaa_graph *g, int B, const double *P, const double
  * graph's running tile before the next round, while the other columns of the
  * tile keep going (each column has its own round counter, coefficients and
  * stopping round).  Each graph runs on its own CUDA stream, so the work of
- * different graphs overlaps on the device.  A query's result does not depend
- * on what else is running: every column's arithmetic is the same, in the same
- * order, whatever the other columns hold.
+ * different graphs overlaps on the device (or, with CPAA_SERVER_FUSED, one
+ * launch per round covers every graph with live queries).  A query's result
+ * does not depend on what else is running: every column's arithmetic is the
+ * same, in the same order, whatever the other columns hold.
  * ------------------------------------------------------------------------ */
 typedef struct cpaa_server cpaa_server;
 
@@ -237,9 +238,10 @@ typedef struct {
 } cpaa_server_stats;
 
 /* Create a server.  device_mem_budget bounds the device memory of all slots;
- * opt (NULL for defaults) sets the precision (default for serving: CPAA_F32),
- * normalize and max_rounds; its stream and flags are ignored.  Starts two host
- * threads (scheduler, completion). */
+ * opt (NULL for defaults) sets the precision (CPAA_F64, CPAA_F32 or
+ * CPAA_BF16; default for serving: CPAA_F32), normalize, max_rounds and
+ * stop_rule; of its flags only CPAA_SERVER_FUSED is read, and its stream is
+ * ignored.  Starts two host threads (scheduler, completion). */
 cpaa_status cpaa_server_create(size_t device_mem_budget, const cpaa_options *opt,
                                cpaa_server **out);
 
@@ -260,9 +262,9 @@ cpaa_status cpaa_server_submit(cpaa_server *s, int graph_id, int nseeds, const i
 /* Wait up to timeout_us (< 0: forever) for a query.  A finished query's vector
  * waits in its slot's device memory (holding the slot) until this call copies
  * it to pi -- n doubles in the caller's vertex order, host or device memory,
- * or NULL to discard it -- fills info (may be NULL; mass, l1 and sum_pibar are
- * NaN: they are not reduced when serving), frees the slot and releases the
- * ticket.  CPAA_ETIMEOUT leaves the query in place; CPAA_ECANCELLED releases a
+ * or NULL to discard it -- fills info (may be NULL; rounds and bound are those
+ * of the stop rule that ended the query; mass, l1 and sum_pibar are NaN: they
+ * are not reported when serving), frees the slot and releases the ticket.  CPAA_ETIMEOUT leaves the query in place; CPAA_ECANCELLED releases a
  * cancelled query; CPAA_ENOTFOUND names no query. */
 cpaa_status cpaa_server_wait(cpaa_server *s, uint64_t ticket, double *pi, cpaa_info *info,
                              int64_t timeout_us);

@@ -154,3 +154,91 @@ def test_config_batched_4M_sampled_columns(pkg):
         print("batched column %d: rounds %d, rel L1 %.3e" % (b, infos[b].rounds, rel))
         assert rel <= 1e-6
     G.close()
+
+
+def _with_hubs(n, edges, degrees, seed):
+    """A Chung-Lu graph on n vertices plus one extra vertex per entry of
+    `degrees`, joined to that many distinct vertices of the graph."""
+    g = ci.chung_lu(n, edges, seed=seed)
+    rp, cx = g.numpy()
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    keep = rows < cx
+    e = [np.stack([rows[keep], cx[keep]], 1)]
+    rng = np.random.default_rng(seed)
+    for i, d in enumerate(degrees):
+        nb = rng.choice(n, size=d, replace=False)
+        e.append(np.stack([np.full(d, n + i), nb], 1))
+    return ci.from_edges(n + len(degrees), np.concatenate(e), name="chung_lu_with_hubs")
+
+
+def test_large_graph_tile_boundaries(pkg):
+    """A graph large enough for the 4096 hub threshold and 8192-entry hub
+    tiles, with hub rows of exactly one tile, one tile plus one entry, and the
+    threshold itself: FP64 against the oracle, FP32 and DF64 beside it, and a
+    batch whose columns equal single solves."""
+    degs = [4096, 4097, 8192, 8193, 16384]
+    g = _with_hubs(1 << 20, 16_000_000, degs, seed=77)
+    G = pkg.Graph(g.row_ptr.cuda(), g.col_idx.cuda(), n=g.n, validate=True)
+    lay = G.layout()
+    assert lay["hub_degree"] == 4096 and lay["hub_tile"] == 8192
+    rp, cx = g.numpy()
+    deg = np.diff(rp)
+    hub = deg[deg > 4096]
+    assert lay["hub_tiles"] == int(np.sum((hub + 8191) // 8192))
+    n = g.n
+    hp = np.zeros(n)
+    hp[[n - 1, n - 3, 5, 77777]] = 0.25  # two of the added hubs among the seeds
+    p = torch.as_tensor(hp).cuda()
+    pi64, i64 = _solve(pkg, G, p, 0.85, 1e-9, precision=pkg.CPAA_F64)
+    ref = O.cpaa(rp, cx, hp, 0.85, i64.rounds)
+    assert _l1(pi64, ref) <= 1e-12
+    pidf, idf = _solve(pkg, G, p, 0.85, 1e-9, precision=pkg.CPAA_DF64)
+    assert _l1(pidf, ref) <= 1e-12
+    pi32, _ = _solve(pkg, G, p, 0.85, 1e-9, precision=pkg.CPAA_F32, fixed_rounds=i64.rounds)
+    assert _l1(pi32, ref) / np.abs(ref).sum() <= 1e-6
+    P = torch.as_tensor(ci.seed_dense(n, ci.seed_vectors(n, 5, seed=3))).cuda()
+    PI = torch.empty_like(P)
+    infos = G.solve_batch(5, P, np.full(5, 0.85), 1e-7, PI, precision=pkg.CPAA_F32, batch_width=4)
+    torch.cuda.synchronize()
+    for b in (0, 4):
+        single, info = _solve(pkg, G, P[b].contiguous(), 0.85, 1e-7, precision=pkg.CPAA_F32)
+        assert infos[b].rounds == info.rounds
+        assert torch.equal(PI[b], single)
+    G.close()
+
+
+def test_option_combinations(pkg):
+    """Less common combinations: the (1 - c) scaling with DF64 and with the
+    a-posteriori rule, per-round history under that rule, and every tile width
+    in DF64."""
+    g = ci.chung_lu(50000, 400000, seed=9)
+    G = pkg.Graph(g.row_ptr.cuda(), g.col_idx.cuda(), n=g.n, validate=True)
+    rp, cx = g.numpy()
+    n = g.n
+    hp = np.zeros(n)
+    hp[[3, 40000]] = 0.5
+    p = torch.as_tensor(hp).cuda()
+    for prec, bound in ((pkg.CPAA_DF64, 1e-12), (pkg.CPAA_F64, 1e-12)):
+        pi, info = _solve(pkg, G, p, 0.9, 1e-8, precision=prec, normalize=1,
+                          stop_rule=pkg.CPAA_STOP_POSTERIORI)
+        ref = O.cpaa(rp, cx, hp, 0.9, info.rounds, normalize=1)
+        assert _l1(pi, ref) <= bound
+    hist = np.zeros(2 * 200)
+    pi, info = _solve(pkg, G, p, 0.85, 1e-8, stop_rule=pkg.CPAA_STOP_POSTERIORI, history=hist)
+    _, mass, l1 = O.cpaa(rp, cx, hp, 0.85, info.rounds, history=True)
+    M = info.rounds
+    assert np.abs(hist[0:2 * (M + 1):2] - mass).max() < 1e-12
+    assert np.abs(hist[1:2 * (M + 1):2] - l1).max() < 1e-10 * l1.max()
+    P = torch.as_tensor(ci.seed_dense(n, ci.seed_vectors(n, 6, seed=4))).cuda()
+    res = {}
+    for W in (1, 2, 4, 8, 16):
+        PI = torch.empty_like(P)
+        infos = G.solve_batch(6, P, np.full(6, 0.85), 1e-8, PI, precision=pkg.CPAA_DF64, batch_width=W)
+        torch.cuda.synchronize()
+        res[W] = (PI.cpu().numpy(), [i.rounds for i in infos])
+    for W in (2, 4, 8, 16):
+        assert res[W][1] == res[1][1]
+        assert np.array_equal(res[W][0], res[1][0])
+    ref = O.cpaa(rp, cx, P[2].cpu().numpy(), 0.85, res[1][1][2])
+    assert np.abs(res[1][0][2] - ref).sum() <= 1e-12
+    G.close()
