@@ -1,7 +1,8 @@
-// device_common.cuh -- number formats and the per-row epilogue arithmetic
-// shared by the single-vector round kernel (step.cu) and the batched one
-// (batch.cu).  Every rounding step is an explicit intrinsic, so both kernels
-// produce bit-identical values for the same inputs.
+// device_common.cuh -- number formats (FP64, FP32, BF16 storage, and the
+// double-float pairs of DF64) and the per-row arithmetic of the round kernel
+// (step.cu), which serves single vectors, batched tiles and the server alike.
+// Every rounding step is an explicit intrinsic, so a value is the same bits
+// whichever of them computed it.
 #pragma once
 
 #include "internal.h"
@@ -81,11 +82,6 @@ __device__ __forceinline__ double to_double(double v) { return v; }
 __device__ __forceinline__ double to_double(float v) { return (double)v; }
 // ---------------------------------------------------------------------------
 
-// Gathered iterate: ld.global.nc, allocating in L1 (hub values repeat).
-__device__ __forceinline__ double load_y(const double *p) { return __ldg(p); }
-__device__ __forceinline__ float load_y(const float *p) { return __ldg(p); }
-__device__ __forceinline__ float load_y(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
-
 __device__ __forceinline__ double to_acc(double v) { return v; }
 __device__ __forceinline__ df to_acc(df v) { return v; }
 __device__ __forceinline__ float to_acc(float v) { return v; }
@@ -103,14 +99,12 @@ __device__ __forceinline__ float round_y(float v, const __nv_bfloat16 *) {
 }
 
 // Streaming loads/stores (read or written once per round: evict first).
-__device__ __forceinline__ int ld_stream(const int32_t *p) { return __ldcs(p); }
 __device__ __forceinline__ int4 ld_stream4(const int32_t *p) { return __ldcs(reinterpret_cast<const int4 *>(p)); }
 template <class T> __device__ __forceinline__ T ld_once(const T *p) { return __ldcs(p); }
 __device__ __forceinline__ df ld_once(const df *p) {
     const float2 v = __ldcs(reinterpret_cast<const float2 *>(p));
     return df(v.x, v.y);
 }
-template <class T> __device__ __forceinline__ void st_once(T *p, T v) { __stcs(p, v); }
 
 // Explicitly rounded arithmetic (no contraction differences between kernels).
 __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
