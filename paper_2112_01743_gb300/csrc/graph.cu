@@ -4,7 +4,8 @@
 // The graph is the undirected G of Sec. 2.1 held as symmetric CSR.  Its
 // degrees d_u = row_ptr[u+1] - row_ptr[u] give P = A D^-1; the round kernels
 // work in the scaled space y = D^-1 T (see step.cu), so the graph also keeps
-// d and 1/d in FP64 and FP32, in the new vertex order.
+// d, 1/d and 2/d in FP64 and FP32 (and d, 2/d as double-floats), in the new
+// vertex order.
 #include <algorithm>
 #include <cstring>
 #include <numeric>

@@ -18,6 +18,11 @@
 // queries join quickly.  Each column's arithmetic is the same whatever the
 // other columns hold, so a result is bit-identical alone and in a mix.
 //
+// Fused mode (CPAA_SERVER_FUSED): all graphs share one stream, and each
+// scheduling pass launches the rounds of every graph with live columns as one
+// kernel over the graphs' work lists (launch_step_multi); the per-graph host
+// logic is the same.
+//
 // With the a-posteriori stopping rule every round also takes its per-column
 // sums and tests the rule on the device (step.cu); a column that passes stops
 // accumulating at once.  After each round a one-warp kernel writes the stop
