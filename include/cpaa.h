@@ -65,9 +65,8 @@ typedef enum {
  * accumulator.  DF64: double-float -- every value is an unevaluated sum of
  * two FP32 numbers (about 48 significant bits, FP32 exponent range), with
  * error-free FP32 transformations for the arithmetic: FP64-class accuracy on
- * the FP32 pipes of a GPU whose FP64 rate is low (cpaa_solve and
- * cpaa_solve_batch; not the power method or the server).  The coefficients
- * c_k, the stopping rule and every output stay FP64 on all four. */
+ * the FP32 pipes of a GPU whose FP64 rate is low.  The coefficients c_k, the
+ * stopping rule and every output stay FP64 on all four. */
 typedef enum { CPAA_F64 = 0, CPAA_F32 = 1, CPAA_BF16 = 2, CPAA_DF64 = 3 } cpaa_precision;
 
 /* cpaa_graph_create flags */
@@ -191,8 +190,8 @@ cpaa_status cpaa_solve(cpaa_graph *g, const double *p, double c, double tol, dou
  * power method x <- c P x + (1 - c) p from x = p (the SPI of Sec. 5.1, also its
  * ground truth).  It runs T rounds, the smallest with 2 c^T < tol (since
  * ||x_T - pi*||_1 <= c^T ||p - pi*||_1 <= 2 c^T), or opt->fixed_rounds.
- * Arguments, info (bound = 2 c^T) and errors as cpaa_solve; CPAA_F64 or
- * CPAA_F32 only.  normalize = 1 returns x_T as it is (it sums to 1 up to
+ * Arguments, info (bound = 2 c^T) and errors as cpaa_solve; CPAA_F64, CPAA_F32
+ * or CPAA_DF64.  normalize = 1 returns x_T as it is (it sums to 1 up to
  * rounding); normalize = 0 divides by its sum. */
 cpaa_status cpaa_power_solve(cpaa_graph *g, const double *p, double c, double tol, double *pi,
                              const cpaa_options *opt, cpaa_info *info);
@@ -238,8 +237,8 @@ typedef struct {
 } cpaa_server_stats;
 
 /* Create a server.  device_mem_budget bounds the device memory of all slots;
- * opt (NULL for defaults) sets the precision (CPAA_F64, CPAA_F32 or
- * CPAA_BF16; default for serving: CPAA_F32), normalize, max_rounds and
+ * opt (NULL for defaults) sets the precision (any of the four; default for
+ * serving: CPAA_F32), normalize, max_rounds and
  * stop_rule; of its flags only CPAA_SERVER_FUSED is read, and its stream is
  * ignored.  Starts two host threads (scheduler, completion). */
 cpaa_status cpaa_server_create(size_t device_mem_budget, const cpaa_options *opt,

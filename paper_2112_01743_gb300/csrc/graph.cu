@@ -54,7 +54,7 @@ __global__ void validate_kernel(const int32_t *__restrict__ row_ptr,
 __global__ void vertex_arrays_kernel(const int32_t *__restrict__ row_ptr,
                                      const int32_t *__restrict__ perm, int64_t n, double *deg64,
                                      double *inv64, double *inv2_64, float *deg32, float *inv32,
-                                     float *inv2_32, df *deg_df, df *inv2_df, int32_t *inv_perm) {
+                                     float *inv2_32, df *deg_df, df *inv_df, df *inv2_df, int32_t *inv_perm) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
          r += (int64_t)gridDim.x * blockDim.x) {
         const int32_t u = perm[r];
@@ -66,6 +66,7 @@ __global__ void vertex_arrays_kernel(const int32_t *__restrict__ row_ptr,
         inv32[r] = 1.0f / (float)d;
         inv2_32[r] = 2.0f / (float)d;
         deg_df[r] = df((double)d);
+        inv_df[r] = df(1.0 / (double)d);
         inv2_df[r] = df(2.0 / (double)d);
         inv_perm[u] = (int32_t)r;
     }
@@ -126,7 +127,7 @@ static void release(cpaa_graph *g) {
     cudaFree(g->long_cnt); cudaFree(g->sell_col); cudaFree(g->chunk_off);
     cudaFree(g->chunk_len); cudaFree(g->chunk_order); cudaFree(g->chunk_desc); cudaFree(g->deg64); cudaFree(g->inv_deg64);
     cudaFree(g->deg32); cudaFree(g->inv_deg32); cudaFree(g->inv2_deg64); cudaFree(g->inv2_deg32);
-    cudaFree(g->deg_df); cudaFree(g->inv2_deg_df);
+    cudaFree(g->deg_df); cudaFree(g->inv_deg_df); cudaFree(g->inv2_deg_df);
     delete g;
 }
 
@@ -317,10 +318,11 @@ extern "C" cpaa_status cpaa_graph_create(int64_t n, int64_t nnz, const int32_t *
         ALLOC(g->inv2_deg64, sizeof(double) * n);
         ALLOC(g->inv2_deg32, sizeof(float) * n);
         ALLOC(g->deg_df, sizeof(df) * n);
+        ALLOC(g->inv_deg_df, sizeof(df) * n);
         ALLOC(g->inv2_deg_df, sizeof(df) * n);
         vertex_arrays_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 8192), 256>>>(
             d_rp, g->perm, n, g->deg64, g->inv_deg64, g->inv2_deg64, g->deg32, g->inv_deg32, g->inv2_deg32,
-            g->deg_df, g->inv2_deg_df, d_inv);
+            g->deg_df, g->inv_deg_df, g->inv2_deg_df, d_inv);
         CK(cudaGetLastError());
 
         ALLOC(g->hub_row_ptr, sizeof(int32_t) * (L.n_hub + 1));

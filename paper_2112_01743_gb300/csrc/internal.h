@@ -206,7 +206,8 @@ struct cpaa_graph {
     double *deg64 = nullptr;         // d_u
     double *inv_deg64 = nullptr;     // 1 / d_u
     double *inv2_deg64 = nullptr;    // 2 / d_u (the recurrence's factor)
-    cpaa::df *deg_df = nullptr;      // d_u and 2 / d_u as double-floats (CPAA_DF64)
+    cpaa::df *deg_df = nullptr;      // d_u, 1 / d_u and 2 / d_u as double-floats (CPAA_DF64)
+    cpaa::df *inv_deg_df = nullptr;
     cpaa::df *inv2_deg_df = nullptr;
     float *deg32 = nullptr;
     float *inv_deg32 = nullptr;
@@ -265,7 +266,7 @@ struct StepLaunch {
 void prepare_step(int precision, int width);
 cudaError_t launch_step(const StepLaunch &s);
 // One round of up to 8 graphs in a single launch (same precision, width and
-// stream; FP64, FP32 or BF16).
+// stream).
 cudaError_t launch_step_multi(const StepLaunch *sl, int ng);
 
 // Solve pieces (solve.cu), shared by cpaa_solve and cpaa_solve_batch.

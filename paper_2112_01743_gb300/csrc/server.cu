@@ -57,6 +57,8 @@ __device__ __forceinline__ void sput(__nv_bfloat16 *p, double v) { *p = __double
 __device__ __forceinline__ double sget(const double *p) { return *p; }
 __device__ __forceinline__ double sget(const float *p) { return (double)*p; }
 __device__ __forceinline__ double sget(const __nv_bfloat16 *p) { return (double)__bfloat162float(*p); }
+__device__ __forceinline__ void sput(df *p, double v) { *p = df(v); }
+__device__ __forceinline__ double sget(const df *p) { return __dadd_rn((double)p->hi, (double)p->lo); }
 
 // Stop state of a graph's columns under the a-posteriori rule (device, and
 // pinned host copies of it).
@@ -254,8 +256,8 @@ struct cpaa_server {
 namespace cpaa {
 namespace srv {
 
-static size_t vbytes(int prec) { return prec == CPAA_F64 ? 8 : prec == CPAA_F32 ? 4 : 2; }
-static size_t rbytes(int prec) { return prec == CPAA_F64 ? 8 : 4; }
+static size_t vbytes(int prec) { return prec == CPAA_F64 || prec == CPAA_DF64 ? 8 : prec == CPAA_F32 ? 4 : 2; }
+static size_t rbytes(int prec) { return prec == CPAA_F64 || prec == CPAA_DF64 ? 8 : 4; }
 
 static size_t graph_bytes(const cpaa_graph *g, int prec, int W, int posteriori) {
     const size_t n = (size_t)g->n;
@@ -315,11 +317,13 @@ static void slot_final_w(GraphState &gs, int b, int normalize, double c) {
 static void slot_prep(cpaa_server *s, GraphState &gs, int b, const SeedArgs &a) {
     if (s->prec == CPAA_F64) slot_prep_w<double, double>(gs, b, a);
     else if (s->prec == CPAA_F32) slot_prep_w<float, float>(gs, b, a);
+    else if (s->prec == CPAA_DF64) slot_prep_w<df, df>(gs, b, a);
     else slot_prep_w<__nv_bfloat16, float>(gs, b, a);
 }
 
 static void slot_final(cpaa_server *s, GraphState &gs, int b, double c) {
     if (s->prec == CPAA_F64) slot_final_w<double>(gs, b, s->normalize, c);
+    else if (s->prec == CPAA_DF64) slot_final_w<df>(gs, b, s->normalize, c);
     else slot_final_w<float>(gs, b, s->normalize, c);
     // the column's stop state as of its finalisation (read by the completion thread)
     if (gs.dstop) copy_stop_kernel<<<1, 64, 0, gs.stream>>>(gs.dstop, gs.d_slot + b);
@@ -700,8 +704,9 @@ extern "C" cpaa_status cpaa_server_create(size_t device_mem_budget, const cpaa_o
         cpaa_options_init(&o);
         o.precision = CPAA_F32;
     }
-    if (o.precision != CPAA_F64 && o.precision != CPAA_F32 && o.precision != CPAA_BF16)
-        return fail(CPAA_EINVAL, "the server runs in FP64, FP32 or BF16");
+    if (o.precision != CPAA_F64 && o.precision != CPAA_F32 && o.precision != CPAA_BF16 &&
+        o.precision != CPAA_DF64)
+        return fail(CPAA_EINVAL, "unknown precision");
     if (o.normalize != 0 && o.normalize != 1) return fail(CPAA_EINVAL, "normalize must be 0 or 1");
     if (o.stop_rule != CPAA_STOP_RIGOROUS && o.stop_rule != CPAA_STOP_POSTERIORI)
         return fail(CPAA_EINVAL, "unknown stop_rule");

@@ -494,8 +494,8 @@ static cpaa_status solve_one(cpaa_graph *g, const double *p, double c, double to
     if (opt.precision != CPAA_F64 && opt.precision != CPAA_F32 && opt.precision != CPAA_BF16 &&
         opt.precision != CPAA_DF64)
         return fail(CPAA_EINVAL, "unknown precision");
-    if (power && opt.precision != CPAA_F64 && opt.precision != CPAA_F32)
-        return fail(CPAA_EINVAL, "the power method runs in FP64 or FP32");
+    if (power && opt.precision == CPAA_BF16)
+        return fail(CPAA_EINVAL, "the power method runs in FP64, FP32 or DF64");
     if (opt.normalize != 0 && opt.normalize != 1) return fail(CPAA_EINVAL, "normalize must be 0 or 1");
     if (opt.stop_rule != CPAA_STOP_RIGOROUS && opt.stop_rule != CPAA_STOP_POSTERIORI)
         return fail(CPAA_EINVAL, "unknown stop_rule");

@@ -684,7 +684,7 @@ static void fill_params(const StepLaunch &s, StepParams<P, W> &p) {
         p.inv_deg = s.power ? g->inv_deg64 : g->inv2_deg64;
     } else if constexpr (P == CPAA_DF64) {
         p.deg = g->deg_df;
-        p.inv_deg = g->inv2_deg_df;  // no power-method rounds in this format
+        p.inv_deg = s.power ? g->inv_deg_df : g->inv2_deg_df;
     } else {
         p.deg = g->deg32;
         p.inv_deg = s.power ? g->inv_deg32 : g->inv2_deg32;
@@ -771,6 +771,7 @@ cudaError_t launch_step_multi(const StepLaunch *sl, int ng) {
         case CPAA_F64: return launch_multi_w<CPAA_F64>(sl, ng);
         case CPAA_F32: return launch_multi_w<CPAA_F32>(sl, ng);
         case CPAA_BF16: return launch_multi_w<CPAA_BF16>(sl, ng);
+        case CPAA_DF64: return launch_multi_w<CPAA_DF64>(sl, ng);
     }
     return cudaErrorInvalidValue;
 }

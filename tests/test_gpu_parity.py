@@ -252,6 +252,11 @@ def test_power_method_matches_oracle(pkg, uploaded, gi):
     if g.n <= 2500:
         truth = O.lapack_pagerank(rp, cx, p, 0.85)
         assert np.abs(out.cpu().numpy() - truth).sum() <= 1e-8
+    outdf = torch.empty_like(pd)
+    G.power_solve(pd, 0.85, 0.0, outdf, fixed_rounds=30, normalize=1, precision=pkg.CPAA_DF64)
+    torch.cuda.synchronize()
+    ref, _ = O.power(rp, cx, p, 0.85, rounds=30)
+    assert np.abs(outdf.cpu().numpy() - ref).sum() <= 1e-12, (g.name, "DF64")
     out32 = torch.empty_like(pd)
     G.power_solve(pd, 0.85, 1e-6, out32, precision=pkg.CPAA_F32)
     torch.cuda.synchronize()

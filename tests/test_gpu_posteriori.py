@@ -149,6 +149,6 @@ def test_stop_rule_invalid(pkg, uploaded):
     with pytest.raises(pkg.CpaaError, match="power method"):
         G.power_solve(pd, 0.85, 1e-6, out, stop_rule=pkg.CPAA_STOP_POSTERIORI)
     with pytest.raises(pkg.CpaaError, match="power method"):
-        G.power_solve(pd, 0.85, 1e-6, out, precision=pkg.CPAA_DF64)
-    with pytest.raises(pkg.CpaaError, match="server"):
-        pkg.Server(1 << 30, precision=pkg.CPAA_DF64)
+        G.power_solve(pd, 0.85, 1e-6, out, precision=pkg.CPAA_BF16)
+    with pytest.raises(pkg.CpaaError, match="precision"):
+        pkg.Server(1 << 30, precision=7)

@@ -228,3 +228,37 @@ def test_fused_mode_matches_per_graph_mode(pkg, rule):
     finally:
         for x in G:
             x.close()
+
+
+@pytest.mark.parametrize("fused", [False, True])
+def test_df64_serving(pkg, fused):
+    """Serving in double-float: results within the FP64 bound of the oracle and
+    the same bits alone and in a mix, in both launch modes."""
+    graphs = [ci.chung_lu(5000, 40000, seed=31), ci.grid_deleted(100, 120, 0.2, seed=3)]
+    G = [upload(pkg, g) for g in graphs]
+    S = pkg.Server(2 << 30, precision=pkg.CPAA_DF64, fused=fused)
+    ids = [S.add_graph(x, 4) for x in G]
+    try:
+        seeds = np.array([11, 4000], dtype=np.int32)
+        alone = np.empty(graphs[0].n)
+        st, info = S.wait(S.submit(ids[0], seeds, None, 0.85, 1e-9), alone, timeout_us=120_000_000)
+        assert st == pkg.CPAA_OK
+        rp, cx = graphs[0].numpy()
+        p = np.zeros(graphs[0].n)
+        p[seeds] = 0.5
+        ref = O.cpaa(rp, cx, p, 0.85, info.rounds)
+        assert np.abs(alone - ref).sum() <= 1e-12
+        mix = _queries(graphs, 20, seed=2)
+        tickets = [S.submit(ids[g2], sd, w, c, tol) for g2, sd, w, c, tol in mix[:10]]
+        tq = S.submit(ids[0], seeds, None, 0.85, 1e-9)
+        tickets += [S.submit(ids[g2], sd, w, c, tol) for g2, sd, w, c, tol in mix[10:]]
+        in_mix = np.empty(graphs[0].n)
+        st2, info2 = S.wait(tq, in_mix, timeout_us=120_000_000)
+        assert st2 == pkg.CPAA_OK and info2.rounds == info.rounds
+        assert np.array_equal(alone, in_mix)
+        for t in tickets:
+            assert S.wait(t, None, timeout_us=120_000_000)[0] == pkg.CPAA_OK
+    finally:
+        S.close()
+        for x in G:
+            x.close()
