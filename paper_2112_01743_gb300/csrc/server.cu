@@ -358,6 +358,8 @@ static void process_completed_rounds(cpaa_server *s, GraphState &gs) {
         if (cudaEventQuery(gs.ring[r % kInFlight]) != cudaSuccess) break;
         if (gs.h_ring) {
             const DevStop &v = gs.h_ring[r % kInFlight];
+            // slot states are also changed by the completion thread and waiters
+            std::lock_guard<std::mutex> lk(s->mu);
             for (int b = 0; b < gs.W; ++b) {
                 const Slot &sl = gs.slots[b];
                 if (sl.st == LIVE && (v.stop >> b & 1u) && r > sl.g_admit &&
@@ -374,7 +376,6 @@ static double us_since(clk::time_point a, clk::time_point b) {
     return std::chrono::duration<double, std::micro>(b - a).count();
 }
 
-// One scheduling pass over a graph; true if anything was launched.
 // The host side of a graph's next round: completed rounds processed,
 // cancellations and admissions made, and (if any column is live) the round's
 // launch described in sl.  Returns true when sl is to be launched; *admitted_any
