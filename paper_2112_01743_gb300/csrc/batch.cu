@@ -46,7 +46,8 @@ static cpaa_status autotune_width(cpaa_graph *g, int prec, int B, const double *
             job.rounds[b] = kTuneRounds;
         }
         float ms = 0.0f;
-        if ((s = run_tile(g, job, st, false, &ms)) != CPAA_OK) return s;
+        if ((s = run_tile(g, job, st, false, true)) != CPAA_OK) return s;
+        if ((s = tile_rounds_ms(g, &ms)) != CPAA_OK) return s;
         const float per_col = ms / W;
         if (W == 1 || per_col < best) {
             best = per_col;
@@ -170,7 +171,7 @@ extern "C" cpaa_status cpaa_solve_batch(cpaa_graph *g, int B, const double *P, c
             job.rounds[j] = M[b];
             job.p_l1[j] = hs[3 * b];
         }
-        if ((s = run_tile(g, job, st, false, nullptr)) != CPAA_OK) return s;
+        if ((s = run_tile(g, job, st, false, false)) != CPAA_OK) return s;
         int sr[kMaxWidth];
         bool by_post[kMaxWidth] = {};
         if (job.posteriori) {

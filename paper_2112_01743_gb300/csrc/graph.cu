@@ -123,6 +123,8 @@ static void release(cpaa_graph *g) {
     if (w.h_sums) cudaFreeHost(w.h_sums);
     for (auto &rg : w.round_graphs) cudaGraphExecDestroy(rg.exec);
     if (w.capture) cudaStreamDestroy(w.capture);
+    if (w.tev[0]) cudaEventDestroy(w.tev[0]);
+    if (w.tev[1]) cudaEventDestroy(w.tev[1]);
     cudaFree(g->perm); cudaFree(g->hub_row_ptr); cudaFree(g->hub_col); cudaFree(g->hub_tiles);
     cudaFree(g->long_cnt); cudaFree(g->sell_col); cudaFree(g->chunk_off);
     cudaFree(g->chunk_len); cudaFree(g->chunk_order); cudaFree(g->chunk_desc); cudaFree(g->deg64); cudaFree(g->inv_deg64);

@@ -144,6 +144,7 @@ struct Workspace {
     };
     std::vector<RoundGraph> round_graphs;
     cudaStream_t capture = nullptr;  // private stream the captures run on
+    cudaEvent_t tev[2] = {nullptr, nullptr};  // around the rounds (CPAA_TIME_ROUNDS)
 };
 
 // One tile of up to kMaxWidth vectors for run_tile (solve.cu).
@@ -275,8 +276,12 @@ cpaa_status ensure_reduction_buffers(cpaa_graph *g);
 cpaa_status ensure_workspace(cpaa_graph *g, int prec, int width, int max_rounds);
 cudaError_t launch_stats(cpaa_graph *g, const double *p, double *out, cudaStream_t st);
 cpaa_status check_stats(const double *s, int64_t nnz, double *kappa);
+// Prep, rounds and finalisation of one tile; with time_rounds the rounds are
+// bracketed by the workspace's events, read afterwards by tile_rounds_ms
+// (which waits for them).
 cpaa_status run_tile(cpaa_graph *g, const TileJob &job, cudaStream_t st, bool history_all_rounds,
-                     float *rounds_ms);
+                     bool time_rounds);
+cpaa_status tile_rounds_ms(cpaa_graph *g, float *ms);
 void round_sums(int width, int b, int k, const std::vector<double> &h, double *sumT, double *sumA);
 
 }  // namespace cpaa

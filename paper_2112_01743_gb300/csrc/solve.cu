@@ -84,12 +84,32 @@ struct TileCols {
 };
 
 // y_0 = D^-1 p, rho = (c_0/2) y_0, comp = 0 for the W columns of a tile.
+// Buffers a tile's rounds expect zeroed: the per-round sums, the hub-row
+// tickets and the two iterate buffers' sentinel rows (cleared by prep_kernel
+// instead of four memsets).
+struct TileZero {
+    double *red;
+    int64_t red_n;
+    int *long_cnt;
+    int n_cnt;
+    unsigned char *sent0, *sent1;
+    int sent_bytes;
+};
+
 template <class S, class R, int W>
 __global__ void __launch_bounds__(kThreads) prep_kernel(const TileCols cols,
                                                         const int32_t *__restrict__ perm, int64_t n,
                                                         const double *__restrict__ inv64, S *y0,
-                                                        R *rho, R *comp) {
-    for (int64_t u = blockIdx.x * (int64_t)kThreads + threadIdx.x; u < n;
+                                                        R *rho, R *comp, const TileZero z) {
+    const int64_t t0 = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+    const int64_t nt = (int64_t)gridDim.x * kThreads;
+    for (int64_t i = t0; i < z.red_n; i += nt) z.red[i] = 0.0;
+    for (int64_t i = t0; i < z.n_cnt; i += nt) z.long_cnt[i] = 0;
+    for (int64_t i = t0; i < z.sent_bytes; i += nt) {
+        z.sent0[i] = 0;
+        z.sent1[i] = 0;
+    }
+    for (int64_t u = t0; u < n;
          u += (int64_t)gridDim.x * kThreads) {
         const int32_t src = perm[u];
         const double inv = inv64[u];
@@ -260,9 +280,19 @@ static cudaError_t tile_kernels(cpaa_graph *g, const TileJob &job, cudaStream_t 
     }
     const unsigned grid = (unsigned)std::min<int64_t>((n + kThreads - 1) / kThreads, 8192);
     if (phase == 0) {
+        int maxM = 0;
+        for (int b = 0; b < job.width; ++b) maxM = std::max(maxM, job.rounds[b]);
+        TileZero z;
+        z.red = w.red;
+        z.red_n = 2 * (int64_t)W * (maxM + 1);
+        z.long_cnt = g->long_cnt;
+        z.n_cnt = std::max(1, g->n_hub);
+        z.sent_bytes = (int)(sizeof(S) * W);
+        z.sent0 = (unsigned char *)w.y0 + (size_t)z.sent_bytes * n;
+        z.sent1 = (unsigned char *)w.y1 + (size_t)z.sent_bytes * n;
         prep_kernel<S, R, W><<<grid, kThreads, 0, st>>>(cols, g->perm, n, g->inv_deg64, (S *)w.y0,
                                                         (R *)w.rho,
-                                                        std::is_same<R, float>::value ? (R *)w.comp : nullptr);
+                                                        std::is_same<R, float>::value ? (R *)w.comp : nullptr, z);
     } else {
         // the accumulator, or (power method) the last iterate, which has the
         // same element type on the FP64 and FP32 paths
@@ -411,16 +441,12 @@ static cpaa_status round_graph(cpaa_graph *g, const TileJob &job, bool history_a
 }
 
 // Prep, the rounds and the finalisation of one tile (workspace must be sized).
-// rounds_ms (if not NULL) receives the device time of the round launches.
 cpaa_status run_tile(cpaa_graph *g, const TileJob &job, cudaStream_t st, bool history_all_rounds,
-                     float *rounds_ms) {
+                     bool time_rounds) {
     Workspace &w = g->ws;
-    const int64_t n = g->n;
     const int W = job.width;
     int maxM = 0;
     for (int b = 0; b < W; ++b) maxM = std::max(maxM, job.rounds[b]);
-    const size_t vb = store_bytes(job.precision) * (size_t)W;
-    CPAA_CUDA(cudaMemsetAsync(w.red, 0, sizeof(double) * 2 * W * (size_t)(maxM + 1), st));
     if (job.posteriori) {
         // the running max of ||T_j p||_1 starts at j = 0 (||p||_1); no column
         // has stopped
@@ -430,9 +456,7 @@ cpaa_status run_tile(cpaa_graph *g, const TileJob &job, cudaStream_t st, bool hi
         // the copy reads the caller's job, which ends with this call
         CPAA_CUDA(cudaStreamSynchronize(st));
     }
-    CPAA_CUDA(cudaMemsetAsync(g->long_cnt, 0, sizeof(int) * std::max(1, g->n_hub), st));
-    CPAA_CUDA(cudaMemsetAsync((char *)w.y0 + vb * n, 0, vb, st));  // sentinel row n
-    CPAA_CUDA(cudaMemsetAsync((char *)w.y1 + vb * n, 0, vb, st));
+    // prep also zeroes the sums, the tickets and the sentinel rows n
     CPAA_CUDA(tile_phase(g, job, st, 0));
 
     cudaGraphExec_t exec = nullptr;
@@ -440,22 +464,27 @@ cpaa_status run_tile(cpaa_graph *g, const TileJob &job, cudaStream_t st, bool hi
         cpaa_status s = round_graph(g, job, history_all_rounds, maxM, &exec);
         if (s != CPAA_OK) return s;
     }
-    cudaEvent_t ev[2] = {nullptr, nullptr};
-    if (rounds_ms) {
-        CPAA_CUDA(cudaEventCreate(&ev[0]));
-        CPAA_CUDA(cudaEventCreate(&ev[1]));
-        CPAA_CUDA(cudaEventRecord(ev[0], st));
+    if (time_rounds) {
+        if (!w.tev[0]) {
+            CPAA_CUDA(cudaEventCreate(&w.tev[0]));
+            CPAA_CUDA(cudaEventCreate(&w.tev[1]));
+        }
+        CPAA_CUDA(cudaEventRecord(w.tev[0], st));
     }
     if (exec) CPAA_CUDA(cudaGraphLaunch(exec, st));
-    if (rounds_ms) {
-        CPAA_CUDA(cudaEventRecord(ev[1], st));
-        CPAA_CUDA(cudaEventSynchronize(ev[1]));
-        CPAA_CUDA(cudaEventElapsedTime(rounds_ms, ev[0], ev[1]));
-        cudaEventDestroy(ev[0]);
-        cudaEventDestroy(ev[1]);
-    }
+    if (time_rounds) CPAA_CUDA(cudaEventRecord(w.tev[1], st));
     void *buf[2] = {w.y0, w.y1};
     CPAA_CUDA(tile_phase(g, job, st, 1, job.power ? buf[maxM & 1] : nullptr));
+    return CPAA_OK;
+}
+
+// Device time of the last run_tile's rounds (run with time_rounds); waits
+// for them.
+cpaa_status tile_rounds_ms(cpaa_graph *g, float *ms) {
+    Workspace &w = g->ws;
+    if (!w.tev[0]) return fail(CPAA_EINVAL, "no timed rounds");
+    CPAA_CUDA(cudaEventSynchronize(w.tev[1]));
+    CPAA_CUDA(cudaEventElapsedTime(ms, w.tev[0], w.tev[1]));
     return CPAA_OK;
 }
 
@@ -558,9 +587,8 @@ static cpaa_status solve_one(cpaa_graph *g, const double *p, double c, double to
     float rounds_ms = 0.0f;
     // per-round sums every round only when the caller asked for the history;
     // otherwise just the last round's (for info)
-    if ((s = run_tile(g, job, st, opt.history != nullptr,
-                      (opt.flags & CPAA_TIME_ROUNDS) ? &rounds_ms : nullptr)) != CPAA_OK)
-        return s;
+    const bool time_rounds = (opt.flags & CPAA_TIME_ROUNDS) != 0;
+    if ((s = run_tile(g, job, st, opt.history != nullptr, time_rounds)) != CPAA_OK) return s;
     if (host_io) CPAA_CUDA(cudaMemcpyAsync(pi, dpi, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
 
     bool by_posteriori = false;
@@ -605,6 +633,8 @@ static cpaa_status solve_one(cpaa_graph *g, const double *p, double c, double to
                 round_sums(1, 0, M, h, &info->mass, &info->l1);
             }
             info->sum_pibar = w.h_sums[3];
+            // the stream has been synchronised: the round events are complete
+            if (time_rounds && (s = tile_rounds_ms(g, &rounds_ms)) != CPAA_OK) return s;
             info->rounds_ms = rounds_ms;
         }
     } else if (host_io) {
