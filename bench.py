@@ -374,7 +374,8 @@ def run_serving(pkg, args):
     vertices, mean degree 16).  Queries: a uniform graph, 1-16 distinct uniform
     seeds, c uniform over {0.5, 0.85, 0.95}, tol 1e-6.  First a closed loop with
     512 queries outstanding gives the saturated rate; then an open-loop Poisson
-    stream at 0.7 x that rate; latency = submit -> result ready (server side)."""
+    stream at 0.7 x that rate, and shorter streams at 0.3, 0.5 and 0.9 x it;
+    latency = submit -> result ready (server side)."""
     import threading
     import torch
     import cpaa_inputs as ci
@@ -442,6 +443,7 @@ def run_serving(pkg, args):
         st = S.stats()
         S.close()
         st["effective_gteps"] = done["entries"] / (done["t_last"] - t0) / 1e9
+        st["mean_width"] = st["round_columns"] / max(1, st["rounds"])
         return len(queries) / (done["t_last"] - t0), st
 
     sat_queries = make(args.serve_queries // 4)
@@ -450,6 +452,18 @@ def run_serving(pkg, args):
     fused_qps, fused_st = run(sat_queries, None, pkg.CPAA_STOP_RIGOROUS, True)
     rate = 0.7 * sat_qps
     qps, st = run(make(args.serve_queries), rate)
+    sweep = []
+    for load in (0.3, 0.5, 0.7, 0.9):
+        if load == 0.7:
+            q, s = qps, st
+            count = args.serve_queries
+        else:
+            count = max(1, args.serve_queries // 8)
+            q, s = run(make(count), load * sat_qps)
+        sweep.append({"load": load, "rate_qps": load * sat_qps, "queries": count, "achieved_qps": q,
+                      "p50_ms": s["p50_us"] / 1e3, "p99_ms": s["p99_us"] / 1e3,
+                      "mean_width": s["mean_width"], "relayouts": s["relayouts"],
+                      "failed": s["failed"]})
     for x in G:
         x.close()
     return {"workload": "8 Chung-Lu graphs (n = 10k..8M, mean degree 16, gamma 2.1) resident; "
@@ -460,13 +474,15 @@ def run_serving(pkg, args):
             "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3, "mean_ms": st["mean_us"] / 1e3,
             "admit_p50_ms": st["admit_p50_us"] / 1e3, "saturated_p50_ms": sat_st["p50_us"] / 1e3,
             "saturated_p99_ms": sat_st["p99_us"] / 1e3,
-            "saturated_effective_gteps": sat_st["effective_gteps"], "completed": st["completed"],
+            "saturated_effective_gteps": sat_st["effective_gteps"],
+            "saturated_mean_width": sat_st["mean_width"], "completed": st["completed"],
             "failed": st["failed"],
             "posteriori_saturated_qps": post_qps, "posteriori_saturated_p50_ms": post_st["p50_us"] / 1e3,
             "posteriori_saturated_p99_ms": post_st["p99_us"] / 1e3,
             "fused_saturated_qps": fused_qps, "fused_saturated_p50_ms": fused_st["p50_us"] / 1e3,
             "fused_saturated_p99_ms": fused_st["p99_us"] / 1e3,
-            "fused_saturated_effective_gteps": fused_st["effective_gteps"]}
+            "fused_saturated_effective_gteps": fused_st["effective_gteps"],
+            "poisson_sweep": sweep}
 
 
 def run_reference(args):

@@ -215,7 +215,11 @@ cpaa_status cpaa_solve_batch(cpaa_graph *g, int B, const double *P, const double
  * a query waits in its graph's queue until a slot is free, then joins the
  * graph's running tile before the next round, while the other columns of the
  * tile keep going (each column has its own round counter, coefficients and
- * stopping round).  Each graph runs on its own CUDA stream, so the work of
+ * stopping round).  A query takes the graph's lowest free slot, and each
+ * round computes only the narrowest power-of-two prefix of the slots that
+ * holds every running query (the tile's vectors are re-laid out at that width
+ * when it changes), so a lone query costs a single-vector round and a full
+ * graph one round of all its slots.  Each graph runs on its own CUDA stream, so the work of
  * different graphs overlaps on the device (or, with CPAA_SERVER_FUSED, one
  * launch per round covers every graph with live queries).  A query's result
  * does not depend on what else is running: every column's arithmetic is the
@@ -234,6 +238,9 @@ typedef struct {
     int64_t device_bytes; /* reserved from the budget */
     double p50_us, p99_us, mean_us; /* submit -> result ready, completed queries */
     double admit_p50_us;  /* submit -> slot */
+    uint64_t rounds;        /* rounds launched, over all graphs */
+    uint64_t round_columns; /* sum over those rounds of the tile width (columns computed) */
+    uint64_t relayouts;     /* tile width changes */
 } cpaa_server_stats;
 
 /* Create a server.  device_mem_budget bounds the device memory of all slots;

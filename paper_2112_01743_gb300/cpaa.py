@@ -83,7 +83,8 @@ class CpaaServerStats(ctypes.Structure):
                 ("pending", ctypes.c_int64), ("running", ctypes.c_int64), ("slots", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("p50_us", ctypes.c_double),
                 ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double),
-                ("admit_p50_us", ctypes.c_double)]
+                ("admit_p50_us", ctypes.c_double), ("rounds", ctypes.c_uint64),
+                ("round_columns", ctypes.c_uint64), ("relayouts", ctypes.c_uint64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

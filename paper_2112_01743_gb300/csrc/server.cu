@@ -1,9 +1,14 @@
 // server.cu -- cpaa_server_*: continuous batching of personalised PageRank
 // queries over resident graphs (see cpaa.h).
 //
-// Per graph: W column slots in one row-major [(n+1) x W] tile (the same
-// layout and round kernel as cpaa_solve_batch), one CUDA stream, a FIFO of
-// queued queries.  Two host threads:
+// Per graph: W column slots, one CUDA stream, a FIFO of queued queries.  The
+// slots' vectors form one row-major [(n+1) x w] tile (the same layout and
+// round kernel as cpaa_solve_batch) whose width w is the smallest power of
+// two covering the highest live slot: queries take the lowest free slot, so
+// at low load a lone query runs at w = 1 (a compact, cache-resident iterate)
+// and under load the tile widens to W.  When w changes between rounds, a copy
+// kernel moves the live columns, bit for bit, into a spare buffer at the new
+// stride.  Two host threads:
 //   scheduler   - admits queued queries into free slots between rounds (a new
 //                 column's y_0 goes into the buffer the next round gathers
 //                 from, y[G & 1] after G rounds, so every column follows the
@@ -32,6 +37,7 @@
 // The rule's decision uses only that column's sums, so it too is the same
 // alone and in a mix.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -86,6 +92,23 @@ __global__ void slot_zero_kernel(S *y0, R *rho, R *comp, int64_t n, int b) {
         y0[u * W + b] = S(0.0f);
         rho[u * W + b] = R(0);
         if (comp) comp[u * W + b] = R(0);
+    }
+}
+
+// A tile's array at a new width: dst[r][b] = src[r][b] for the kept columns b
+// of both widths, 0 elsewhere (the sentinel row stays zero).  Raw element bits
+// are copied, so a moved column continues exactly as it would have.
+template <class E>
+__global__ void restride_kernel(const E *__restrict__ src, E *__restrict__ dst, int64_t rows, int wo_log,
+                                int wn_log, unsigned keep) {
+    const int64_t total = rows << wn_log;
+    const int64_t bmask = (int64_t(1) << wn_log) - 1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int b = (int)(i & bmask);
+        E v = E(0);
+        if ((keep >> b & 1u) && b < (1 << wo_log)) v = src[((i >> wn_log) << wo_log) + b];
+        dst[i] = v;
     }
 }
 
@@ -193,10 +216,13 @@ struct Slot {
 struct GraphState {
     int id = 0;
     cpaa_graph *g = nullptr;
-    int W = 1;
+    int W = 1;  // slots
+    int w = 1;  // current tile width (a power of two, 1..W)
     cudaStream_t stream = nullptr;
+    // y, rho, comp and spare: interchangeable buffers of tile_bytes each
     void *y[2] = {nullptr, nullptr};
-    void *rho = nullptr, *comp = nullptr, *long_part = nullptr;
+    void *rho = nullptr, *comp = nullptr, *spare = nullptr, *long_part = nullptr;
+    size_t tile_bytes = 0;
     int *long_cnt = nullptr;
     double *red = nullptr, *result = nullptr, *part = nullptr, *sums = nullptr;
     size_t bytes = 0;
@@ -250,6 +276,7 @@ struct cpaa_server {
     cudaStream_t copy_stream = nullptr;
     std::mutex copy_mu;
     uint64_t submitted = 0, completed = 0, cancelled = 0, failed = 0;
+    std::atomic<uint64_t> rounds{0}, round_columns{0}, relayouts{0};
     std::vector<double> lat_us, admit_us;
 };
 
@@ -259,9 +286,15 @@ namespace srv {
 static size_t vbytes(int prec) { return prec == CPAA_F64 || prec == CPAA_DF64 ? 8 : prec == CPAA_F32 ? 4 : 2; }
 static size_t rbytes(int prec) { return prec == CPAA_F64 || prec == CPAA_DF64 ? 8 : 4; }
 
+// Bytes of each of a tile's five vector buffers (y[0], y[1], rho, comp, spare).
+static size_t tile_bytes(const cpaa_graph *g, int prec, int W) {
+    const size_t n = (size_t)g->n;
+    return std::max((n + 1) * W * vbytes(prec), n * W * rbytes(prec));
+}
+
 static size_t graph_bytes(const cpaa_graph *g, int prec, int W, int posteriori) {
     const size_t n = (size_t)g->n;
-    size_t b = 2 * (n + 1) * W * vbytes(prec) + 2 * n * W * rbytes(prec) + n * W * 8 +
+    size_t b = 5 * tile_bytes(g, prec, W) + n * W * 8 +
                (size_t)std::max(1, g->num_hub_tiles) * W * 8 + (size_t)std::max(1, g->n_hub) * 4 +
                (size_t)kPrepBlocks * 8 + (size_t)W * 8 + 2 * 8 * (size_t)W;
     if (posteriori)  // per-round item sums
@@ -294,7 +327,7 @@ static void launch_slot_final(GraphState &gs, int b, int normalize, double c) {
 
 template <class S, class R>
 static void slot_prep_w(GraphState &gs, int b, const SeedArgs &a) {
-    switch (gs.W) {
+    switch (gs.w) {
         case 1: launch_slot_prep<S, R, 1>(gs, b, a); break;
         case 2: launch_slot_prep<S, R, 2>(gs, b, a); break;
         case 4: launch_slot_prep<S, R, 4>(gs, b, a); break;
@@ -305,7 +338,7 @@ static void slot_prep_w(GraphState &gs, int b, const SeedArgs &a) {
 
 template <class R>
 static void slot_final_w(GraphState &gs, int b, int normalize, double c) {
-    switch (gs.W) {
+    switch (gs.w) {
         case 1: launch_slot_final<R, 1>(gs, b, normalize, c); break;
         case 2: launch_slot_final<R, 2>(gs, b, normalize, c); break;
         case 4: launch_slot_final<R, 4>(gs, b, normalize, c); break;
@@ -327,6 +360,47 @@ static void slot_final(cpaa_server *s, GraphState &gs, int b, double c) {
     else slot_final_w<float>(gs, b, s->normalize, c);
     // the column's stop state as of its finalisation (read by the completion thread)
     if (gs.dstop) copy_stop_kernel<<<1, 64, 0, gs.stream>>>(gs.dstop, gs.d_slot + b);
+}
+
+static int log2_width(int w) {
+    int l = 0;
+    while ((1 << l) < w) ++l;
+    return l;
+}
+
+template <class E>
+static void restride(GraphState &gs, void *&buf, int64_t rows, int wn, unsigned keep) {
+    const int64_t total = rows * wn;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 4096));
+    restride_kernel<E><<<grid, 256, 0, gs.stream>>>((const E *)buf, (E *)gs.spare, rows, log2_width(gs.w),
+                                                     log2_width(wn), keep);
+    std::swap(buf, gs.spare);
+}
+
+// EY: the iterate's element (bits), ER: the accumulator's; comp is kept only
+// under Kahan summation (FP32 accumulators).
+template <class EY, class ER>
+static void restride_arrays(GraphState &gs, int wn, unsigned keep, bool kahan) {
+    const int64_t n = gs.g->n;
+    restride<EY>(gs, gs.y[0], n + 1, wn, keep);
+    restride<EY>(gs, gs.y[1], n + 1, wn, keep);
+    restride<ER>(gs, gs.rho, n, wn, keep);
+    if (kahan) restride<ER>(gs, gs.comp, n, wn, keep);
+}
+
+// Change a graph's tile width to wn between rounds (stream-ordered after every
+// kernel already queued on the graph's stream), keeping the columns in keep.
+static void set_width(cpaa_server *s, GraphState &gs, int wn, unsigned keep) {
+    if (wn == gs.w) return;
+    using u64 = unsigned long long;
+    switch (s->prec) {
+        case CPAA_F64:
+        case CPAA_DF64: restride_arrays<u64, u64>(gs, wn, keep, false); break;
+        case CPAA_F32: restride_arrays<uint32_t, uint32_t>(gs, wn, keep, true); break;
+        default: restride_arrays<uint16_t, uint32_t>(gs, wn, keep, true); break;  // BF16
+    }
+    gs.w = wn;
+    ++s->relayouts;
 }
 
 // Queue a LIVE slot's finalisation and hand it to the completion thread
@@ -453,6 +527,12 @@ static bool plan_round(cpaa_server *s, GraphState &gs, StepLaunch &sl, unsigned 
             }
         }
     }
+    if (live) {  // the narrowest tile that holds every live column
+        const int need = 32 - __builtin_clz(live);
+        int wn = 1;
+        while (wn < need) wn <<= 1;
+        set_width(s, gs, wn, live);
+    }
     for (auto &a : admitted) slot_prep(s, gs, a.first, a.second);
     *admitted_any = !admitted.empty();
     *live_out = live;
@@ -461,7 +541,7 @@ static bool plan_round(cpaa_server *s, GraphState &gs, StepLaunch &sl, unsigned 
     sl = StepLaunch();
     sl.g = gs.g;
     sl.precision = s->prec;
-    sl.width = gs.W;
+    sl.width = gs.w;
     sl.y_src = gs.y[gs.G & 1];
     sl.y_io = gs.y[(gs.G + 1) & 1];
     sl.rho = gs.rho;
@@ -470,7 +550,7 @@ static bool plan_round(cpaa_server *s, GraphState &gs, StepLaunch &sl, unsigned 
     sl.red = gs.red;
     sl.active = live;
     sl.reduce = 0;
-    sl.first = ~live & ((1u << gs.W) - 1u);
+    sl.first = ~live & ((1u << gs.w) - 1u);
     sl.power = 0;
     sl.long_cnt = gs.long_cnt;
     sl.stream = gs.stream;
@@ -510,6 +590,8 @@ static void after_round(cpaa_server *s, GraphState &gs, unsigned live) {
     if (gs.dstop)
         copy_stop_kernel<<<1, 64, 0, gs.stream>>>(gs.dstop, gs.d_ring + Gn % kInFlight);
     gs.G = Gn;
+    ++s->rounds;
+    s->round_columns += (uint64_t)gs.w;
     cudaEventRecord(gs.ring[gs.G % kInFlight], gs.stream);
     std::vector<int> due;
     for (int b = 0; b < gs.W; ++b) {
@@ -674,7 +756,8 @@ static void release_slot(cpaa_server *s, Request &r) {
 }
 
 static void free_graph_state(GraphState &gs) {
-    cudaFree(gs.y[0]); cudaFree(gs.y[1]); cudaFree(gs.rho); cudaFree(gs.comp); cudaFree(gs.long_part);
+    cudaFree(gs.y[0]); cudaFree(gs.y[1]); cudaFree(gs.rho); cudaFree(gs.comp); cudaFree(gs.spare);
+    cudaFree(gs.long_part);
     cudaFree(gs.long_cnt); cudaFree(gs.red); cudaFree(gs.result); cudaFree(gs.part); cudaFree(gs.sums);
     cudaFree(gs.ipart); cudaFree(gs.ipart2); cudaFree(gs.dstop);
     if (gs.h_ring) cudaFreeHost(gs.h_ring);
@@ -760,25 +843,27 @@ extern "C" cpaa_status cpaa_server_add_graph(cpaa_server *s, cpaa_graph *g, int 
         if (e_ != cudaSuccess) { st = cuda_fail(e_, #call); goto fail_out; }     \
     } while (0)
     {
-        const size_t vb = (size_t)(n + 1) * W * vbytes(s->prec), rb = (size_t)n * W * rbytes(s->prec);
+        const size_t tb = tile_bytes(g, s->prec, W);
+        gs->tile_bytes = tb;
         if (s->fused) {  // every graph's work goes to the server's stream
             gs->stream = s->fstream;
             gs->own_stream = false;
         } else {
             SCK(cudaStreamCreateWithFlags(&gs->stream, cudaStreamNonBlocking));
         }
-        SALLOC(gs->y[0], vb);
-        SALLOC(gs->y[1], vb);
-        SALLOC(gs->rho, rb);
-        SALLOC(gs->comp, rb);
+        SALLOC(gs->y[0], tb);
+        SALLOC(gs->y[1], tb);
+        SALLOC(gs->rho, tb);
+        SALLOC(gs->comp, tb);
+        SALLOC(gs->spare, tb);
         SALLOC(gs->long_part, (size_t)std::max(1, g->num_hub_tiles) * W * 8);
         SALLOC(gs->long_cnt, (size_t)std::max(1, g->n_hub) * 4);
         SALLOC(gs->red, 2 * 8 * (size_t)W);
         SALLOC(gs->result, (size_t)n * W * 8);
         SALLOC(gs->part, (size_t)kPrepBlocks * 8);
         SALLOC(gs->sums, (size_t)W * 8);
-        SCK(cudaMemsetAsync(gs->y[0], 0, vb, gs->stream));
-        SCK(cudaMemsetAsync(gs->y[1], 0, vb, gs->stream));
+        SCK(cudaMemsetAsync(gs->y[0], 0, tb, gs->stream));
+        SCK(cudaMemsetAsync(gs->y[1], 0, tb, gs->stream));
         SCK(cudaMemsetAsync(gs->long_cnt, 0, (size_t)std::max(1, g->n_hub) * 4, gs->stream));
         if (s->posteriori) {
             SALLOC(gs->ipart, 2 * 8 * (size_t)W * ((size_t)g->n_hub + g->num_chunks));
@@ -980,6 +1065,9 @@ extern "C" cpaa_status cpaa_server_get_stats(cpaa_server *s, cpaa_server_stats *
     for (double v : s->lat_us) m += v;
     out->mean_us = s->lat_us.empty() ? 0.0 : m / s->lat_us.size();
     out->admit_p50_us = percentile(s->admit_us, 0.50);
+    out->rounds = s->rounds;
+    out->round_columns = s->round_columns;
+    out->relayouts = s->relayouts;
     return CPAA_OK;
 }
 

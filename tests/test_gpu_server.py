@@ -262,3 +262,66 @@ def test_df64_serving(pkg, fused):
         S.close()
         for x in G:
             x.close()
+
+
+@pytest.mark.parametrize("prec,fused", [("F32", False), ("F64", False), ("BF16", False), ("DF64", False),
+                                        ("F32", True)])
+def test_tile_width_follows_live_slots(pkg, prec, fused):
+    """A graph's tile is as wide as its highest live slot needs: queries run
+    alone compute one column per round, and when the width changes while a
+    long query runs, its columns move to the new layout bit for bit (every
+    result equals the same query run alone)."""
+    import time
+    g = ci.chung_lu(300000, 3000000, seed=44)
+    G = upload(pkg, g)
+    S = pkg.Server(4 << 30, precision=getattr(pkg, "CPAA_" + prec), fused=fused)
+    gid = S.add_graph(G, 16)
+    n = g.n
+    long_q = (np.array([5, 299000, 123456], dtype=np.int32), 0.99, 1e-12)  # 238 rounds
+    rng = np.random.default_rng(7)
+    short = [(rng.choice(n, size=int(rng.integers(1, 9)), replace=False).astype(np.int32),
+              float(rng.choice([0.5, 0.85])), 1e-6) for _ in range(9)]
+    try:
+        alone = []
+        for seeds, c, tol in [long_q] + short:
+            pi = np.empty(n)
+            st, info = S.wait(S.submit(gid, seeds, None, c, tol), pi, timeout_us=120_000_000)
+            assert st == pkg.CPAA_OK
+            alone.append((pi, info.rounds))
+        s0 = S.stats()
+        assert s0["relayouts"] == 0 and s0["round_columns"] == s0["rounds"]
+        assert s0["rounds"] == sum(r for _, r in alone)
+        # the long query, then a wave of six (slots 1-6: width 8), then, once
+        # those are done, two more (width 4), all while the long one may run
+        def collect(t):
+            pi = np.empty(n)
+            st, info = S.wait(t, pi, timeout_us=120_000_000)
+            assert st == pkg.CPAA_OK
+            return pi, info.rounds
+
+        t_long = S.submit(gid, long_q[0], None, long_q[1], long_q[2])
+        time.sleep(0.001)
+        wave = [S.submit(gid, sd, None, c, tol) for sd, c, tol in short[:6]]
+        res = {1 + i: collect(t) for i, t in enumerate(wave)}
+        wave = [S.submit(gid, sd, None, c, tol) for sd, c, tol in short[6:8]]
+        res.update({7 + i: collect(t) for i, t in enumerate(wave)})
+        res[0] = collect(t_long)
+        for i, (pi, r) in res.items():
+            assert r == alone[i][1]
+            assert np.array_equal(pi, alone[i][0]), i
+        s1 = S.stats()
+        assert s1["relayouts"] >= 2
+        assert s1["round_columns"] > s1["rounds"]
+        assert s1["failed"] == 0
+        # a lone query after the mix runs at width 1 again
+        pi = np.empty(n)
+        r0, c0 = s1["rounds"], s1["round_columns"]
+        sd, c, tol = short[8]
+        st, info = S.wait(S.submit(gid, sd, None, c, tol), pi, timeout_us=120_000_000)
+        s2 = S.stats()
+        assert np.array_equal(pi, alone[9][0])
+        assert s2["rounds"] - r0 == info.rounds
+        assert s2["round_columns"] - c0 == info.rounds
+    finally:
+        S.close()
+        G.close()
