@@ -70,3 +70,35 @@ def test_config1_rounds_from_eq41():
     from oracle import oracle as O
     M = next(m for m in range(1, 200) if O.err_bound(0.85, m) < 1e-10)
     assert M == 39
+
+
+def test_struct_layouts_match_the_header(L, tmp_path):
+    """Every struct the binding mirrors has the header's size and field
+    offsets (compiled with the host C compiler against include/cpaa.h)."""
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    structs = {"cpaa_options": L.CpaaOptions, "cpaa_info": L.CpaaInfo,
+               "cpaa_server_stats": L.CpaaServerStats, "cpaa_layout": L.CpaaLayout}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "cpaa.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (name, name))
+        for f, _ in cls._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (name, f, name, f))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        s, f, v = line.split()
+        got[(s, f)] = int(v)
+    for name, cls in structs.items():
+        assert got[(name, "sizeof")] == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert got[(name, f)] == getattr(cls, f).offset, (name, f)
