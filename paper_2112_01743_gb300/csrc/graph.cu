@@ -11,6 +11,8 @@
 #include <numeric>
 #include <thread>
 
+#include <cub/device/device_segmented_sort.cuh>
+
 #include "internal.h"
 
 namespace cpaa {
@@ -72,13 +74,23 @@ __global__ void vertex_arrays_kernel(const int32_t *__restrict__ row_ptr,
     }
 }
 
+// Column ids in the new vertex order (in place; col_idx is the library's own
+// device copy).
+__global__ void relabel_kernel(int32_t *col, const int32_t *__restrict__ inv_perm, int64_t nnz) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+         e += (int64_t)gridDim.x * blockDim.x)
+        col[e] = inv_perm[col[e]];
+}
+
 // One warp per SELL chunk: lane l writes entry i of row n_hub + 32c + l at
 // chunk_off[c] + 128 (i / 4) + 4 l + i % 4 (each lane's entries in groups of
-// four, one 16-byte load), relabelled; padding gets the sentinel n.
+// four, one 16-byte load); padding gets the sentinel n.  rcol holds the
+// relabelled graph's CSR rows (new ids, ascending) at the caller's row offsets,
+// so a row's first entries are its hub and heavy neighbours: the 32 lanes of a
+// chunk gather those together, from the few cache lines that hold them.
 __global__ void build_sell_kernel(const int32_t *__restrict__ row_ptr,
-                                  const int32_t *__restrict__ col_idx,
-                                  const int32_t *__restrict__ perm,
-                                  const int32_t *__restrict__ inv_perm, int64_t n, int n_hub,
+                                  const int32_t *__restrict__ rcol,
+                                  const int32_t *__restrict__ perm, int64_t n, int n_hub,
                                   int num_chunks, const int64_t *__restrict__ chunk_off,
                                   const int32_t *__restrict__ chunk_len, int32_t *sell) {
     const int lane = threadIdx.x & 31;
@@ -96,22 +108,21 @@ __global__ void build_sell_kernel(const int32_t *__restrict__ row_ptr,
         const int len = chunk_len[c];
         for (int i = 0; i < len; ++i)
             sell[off + (int64_t)(i / kSellVec) * (kChunkRows * kSellVec) + lane * kSellVec + i % kSellVec] =
-                (i < d) ? inv_perm[col_idx[e0 + i]] : (int32_t)n;
+                (i < d) ? rcol[e0 + i] : (int32_t)n;
     }
 }
 
-// One CTA per hub row: relabelled copy of its entries.
+// One CTA per hub row: a copy of its relabelled, sorted entries.
 __global__ void build_hub_kernel(const int32_t *__restrict__ row_ptr,
-                                 const int32_t *__restrict__ col_idx,
+                                 const int32_t *__restrict__ rcol,
                                  const int32_t *__restrict__ perm,
-                                 const int32_t *__restrict__ inv_perm,
                                  const int32_t *__restrict__ hub_row_ptr, int n_hub,
                                  int32_t *hub_col) {
     for (int h = blockIdx.x; h < n_hub; h += gridDim.x) {
         const int32_t u = perm[h];
         const int e0 = row_ptr[u], d = row_ptr[u + 1] - e0;
         const int o = hub_row_ptr[h];
-        for (int i = threadIdx.x; i < d; i += blockDim.x) hub_col[o + i] = inv_perm[col_idx[e0 + i]];
+        for (int i = threadIdx.x; i < d; i += blockDim.x) hub_col[o + i] = rcol[e0 + i];
     }
 }
 
@@ -258,8 +269,9 @@ extern "C" cpaa_status cpaa_graph_create(int64_t n, int64_t nnz, const int32_t *
     g->nnz = nnz;
     cudaGetDevice(&g->device);
     cpaa_status st;
-    int32_t *d_rp = nullptr, *d_ci = nullptr, *d_inv = nullptr;
-    size_t rp_bytes = sizeof(int32_t) * (n + 1), ci_bytes = sizeof(int32_t) * nnz;
+    int32_t *d_rp = nullptr, *d_ci = nullptr, *d_inv = nullptr, *d_rs = nullptr;
+    void *d_tmp = nullptr;
+    size_t rp_bytes = sizeof(int32_t) * (n + 1), ci_bytes = sizeof(int32_t) * nnz, tmp_bytes = 0;
 #define ALLOC(ptr, bytes)                                                      \
     do {                                                                       \
         st = dev_alloc(g, (void **)&(ptr), (bytes));                           \
@@ -327,14 +339,27 @@ extern "C" cpaa_status cpaa_graph_create(int64_t n, int64_t nnz, const int32_t *
             g->deg_df, g->inv_deg_df, g->inv2_deg_df, d_inv);
         CK(cudaGetLastError());
 
+        // the relabelled graph's CSR: every caller row's entries in new ids,
+        // sorted ascending (the order in which the round adds them)
+        relabel_kernel<<<(unsigned)std::min<int64_t>((nnz + 255) / 256, 16384), 256>>>(d_ci, d_inv, nnz);
+        CK(cudaGetLastError());
+        CK(cub::DeviceSegmentedSort::SortKeys(nullptr, tmp_bytes, d_ci, d_rs, nnz, n, d_rp, d_rp + 1));
+        ALLOC(d_tmp, std::max<size_t>(tmp_bytes, 16));
+        ALLOC(d_rs, ci_bytes);
+        CK(cub::DeviceSegmentedSort::SortKeys(d_tmp, tmp_bytes, d_ci, d_rs, nnz, n, d_rp, d_rp + 1));
+        dev_free(g, &d_tmp, std::max<size_t>(tmp_bytes, 16));
+        dev_free(g, (void **)&d_ci, ci_bytes);
+        d_ci = d_rs;
+        d_rs = nullptr;
+
         ALLOC(g->hub_row_ptr, sizeof(int32_t) * (L.n_hub + 1));
         CK(cudaMemcpy(g->hub_row_ptr, L.hub_row_ptr.data(), sizeof(int32_t) * (L.n_hub + 1),
                       cudaMemcpyHostToDevice));
         ALLOC(g->hub_col, sizeof(int32_t) * (g->hub_nnz + 4));
         CK(cudaMemset(g->hub_col, 0, sizeof(int32_t) * (g->hub_nnz + 4)));
         if (L.n_hub > 0) {
-            build_hub_kernel<<<std::min(L.n_hub, 4096), 256>>>(d_rp, d_ci, g->perm, d_inv, g->hub_row_ptr,
-                                                                L.n_hub, g->hub_col);
+            build_hub_kernel<<<std::min(L.n_hub, 4096), 256>>>(d_rp, d_ci, g->perm, g->hub_row_ptr, L.n_hub,
+                                                                g->hub_col);
             CK(cudaGetLastError());
         }
         ALLOC(g->hub_tiles, sizeof(int4) * std::max<size_t>(1, L.hub_tiles.size()));
@@ -358,7 +383,7 @@ extern "C" cpaa_status cpaa_graph_create(int64_t n, int64_t nnz, const int32_t *
             CK(cudaMemcpy(g->chunk_desc, L.chunk_desc.data(), sizeof(int4) * g->num_chunks,
                           cudaMemcpyHostToDevice));
             build_sell_kernel<<<(unsigned)std::min<int64_t>(((int64_t)g->num_chunks * 32 + 255) / 256, 16384), 256>>>(
-                d_rp, d_ci, g->perm, d_inv, n, L.n_hub, g->num_chunks, g->chunk_off, g->chunk_len, g->sell_col);
+                d_rp, d_ci, g->perm, n, L.n_hub, g->num_chunks, g->chunk_off, g->chunk_len, g->sell_col);
             CK(cudaGetLastError());
         }
         CK(cudaDeviceSynchronize());
@@ -369,6 +394,8 @@ extern "C" cpaa_status cpaa_graph_create(int64_t n, int64_t nnz, const int32_t *
         return CPAA_OK;
     }
 fail_out:
+    if (d_tmp) dev_free(g, &d_tmp, std::max<size_t>(tmp_bytes, 16));
+    if (d_rs) dev_free(g, (void **)&d_rs, ci_bytes);
     if (d_inv) dev_free(g, (void **)&d_inv, sizeof(int32_t) * n);
     if (d_ci) dev_free(g, (void **)&d_ci, ci_bytes);
     if (d_rp) dev_free(g, (void **)&d_rp, rp_bytes);
