@@ -102,3 +102,45 @@ def test_struct_layouts_match_the_header(L, tmp_path):
         assert got[(name, "sizeof")] == ctypes.sizeof(cls), name
         for f, _ in cls._fields_:
             assert got[(name, f)] == getattr(cls, f).offset, (name, f)
+
+
+def test_plain_c_program_links_and_calls_host_entry_points(L, tmp_path):
+    """A C program with no Python in it compiles against include/cpaa.h,
+    links libcpaa.so and gets the same answers from the host-side entry points
+    (options defaults, the stopping rule, status names) as the binding."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    src = tmp_path / "use_abi.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include "cpaa.h"
+int main(void) {
+    cpaa_options o;
+    cpaa_options_init(&o);
+    printf("%d %d %d %d %u %d %d\n", (int)o.precision, o.normalize, o.fixed_rounds, o.max_rounds,
+           o.flags, o.batch_width, (int)o.stop_rule);
+    printf("%d %d %d\n", cpaa_rounds_needed(0.85, 1e-6, 74.0, 0, 2000),
+           cpaa_rounds_needed(0.99, 1e-12, 1.6e4, 1, 2000), cpaa_rounds_needed(0.5, 1e-300, 1.0, 0, 10));
+    printf("%.17g %.17g\n", cpaa_l1_bound(0.85, 30, 74.0, 0), cpaa_l1_bound(0.95, 7, 1.44, 1));
+    printf("%s %s\n", cpaa_status_string(CPAA_OK), cpaa_status_string(CPAA_ENOTCONV));
+    printf("[%s]\n", cpaa_last_error());
+    return 0;
+}
+''')
+    exe = tmp_path / "use_abi"
+    libdir = os.path.dirname(L.library_path)
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                    "-L", libdir, "-lcpaa", "-Wl,-rpath," + libdir], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines()
+    o = L.cpaa_options_init()
+    assert out[0].split() == [str(v) for v in (o.precision, o.normalize, o.fixed_rounds, o.max_rounds,
+                                               o.flags, o.batch_width, o.stop_rule)]
+    assert [int(v) for v in out[1].split()] == [L.cpaa_rounds_needed(0.85, 1e-6, 74.0, 0, 2000),
+                                                L.cpaa_rounds_needed(0.99, 1e-12, 1.6e4, 1, 2000), -1]
+    b = [float(v) for v in out[2].split()]
+    assert b == [L.cpaa_l1_bound(0.85, 30, 74.0, 0), L.cpaa_l1_bound(0.95, 7, 1.44, 1)]
+    assert out[3].split() == ["CPAA_OK", "CPAA_ENOTCONV"]
+    assert out[4] == "[]"
