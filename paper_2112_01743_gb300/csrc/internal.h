@@ -23,6 +23,8 @@ namespace cpaa {
 //                       each window sorted by decreasing degree.
 // Every per-vertex vector (degrees, iterates, accumulator) is stored in the new
 // order; the solve gathers p through the permutation and scatters pi back.
+// Every row's entries are the relabelled graph's CSR row: new column ids,
+// ascending (so a row starts with its hub and heavy neighbours).
 //
 // Non-hub rows are held as SELL-C-sigma (sliced ELLPACK, C = kChunkRows = 32,
 // sigma = kSortWindow): chunk c holds new rows n_hub + 32c .. + 31, padded to
@@ -42,7 +44,7 @@ namespace cpaa {
 // entries: long tiles on large graphs (fewer barriers and tickets per entry),
 // short ones on small graphs (more CTAs on a row).
 //
-// Hub rows stay CSR (relabelled columns).  Their entries are cut into tiles;
+// Hub rows stay CSR (relabelled columns, ascending).  Their entries are cut into tiles;
 // one CTA sums one tile, and the CTA that takes the last ticket of a row adds
 // the tile partials in tile order and writes the row (an atomic counter, no
 // waiting).  Hub tile encoding (int4):
