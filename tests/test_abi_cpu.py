@@ -144,3 +144,48 @@ int main(void) {
     assert b == [L.cpaa_l1_bound(0.85, 30, 74.0, 0), L.cpaa_l1_bound(0.95, 7, 1.44, 1)]
     assert out[3].split() == ["CPAA_OK", "CPAA_ENOTCONV"]
     assert out[4] == "[]"
+
+
+def test_graph_create_rejects_bad_csr_before_any_device_work(L):
+    """cpaa_graph_create checks a host CSR's sizes and row pointers on the host
+    before its first CUDA call: empty or oversized graphs, a bad row_ptr and a
+    degree-0 vertex (Sec. 2.1 needs d_i > 0) are EINVAL, with the reason."""
+    i32 = lambda v: np.asarray(v, dtype=np.int32)
+    ok_rp, ok_cx = i32([0, 1, 2]), i32([1, 0])
+    cases = [
+        (0, 2, ok_rp, ok_cx, "n out of range"),
+        (2, 0, ok_rp, ok_cx, "nnz out of range"),
+        (2, 1 << 31, ok_rp, ok_cx, "nnz out of range"),
+        (2, 2, None, ok_cx, "NULL"),
+        (2, 2, ok_rp, None, "NULL"),
+        (2, 2, i32([1, 1, 2]), ok_cx, "row_ptr[0]"),
+        (2, 3, ok_rp, i32([1, 0, 0]), "row_ptr[n] != nnz"),
+        (3, 3, i32([0, 2, 1, 3]), i32([1, 2, 0]), "decreases at row 1"),
+        (3, 2, i32([0, 1, 1, 2]), i32([2, 0]), "vertex 1 has degree 0"),
+    ]
+    for n, nnz, rp, cx, why in cases:
+        with pytest.raises(L.CpaaError) as e:
+            L.cpaa_graph_create(n, nnz, rp, cx)
+        assert e.value.status == L.CPAA_EINVAL, why
+        assert why in str(e.value), (why, str(e.value))
+
+
+def test_host_side_argument_checks(L):
+    """Checks made before any device work: NULL handles, and the server's
+    options (precision, normalisation, stopping rule)."""
+    def einval(fn, why):
+        with pytest.raises(L.CpaaError) as e:
+            fn()
+        assert e.value.status == L.CPAA_EINVAL, why
+        assert why in str(e.value), (why, str(e.value))
+
+    p, pi = np.full(2, 0.5), np.empty(2)
+    einval(lambda: L.cpaa_solve(None, p, 0.85, 1e-6, pi), "graph is NULL")
+    einval(lambda: L.cpaa_power_solve(None, p, 0.85, 1e-6, pi), "graph is NULL")
+    einval(lambda: L.cpaa_graph_info(None), "graph is NULL")
+    einval(lambda: L.cpaa_graph_layout(None), "NULL")
+    einval(lambda: L.Server(1 << 30, precision=7), "unknown precision")
+    einval(lambda: L.Server(1 << 30, normalize=2), "normalize must be 0 or 1")
+    einval(lambda: L.Server(1 << 30, stop_rule=5), "unknown stop_rule")
+    einval(lambda: L.cpaa_server_submit(None, 0, np.array([1], dtype=np.int32), None, 0.85, 1e-6), "NULL")
+    einval(lambda: L.cpaa_server_get_stats(None), "NULL")
