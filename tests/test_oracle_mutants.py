@@ -105,3 +105,27 @@ def test_planted_mistake_is_caught(name, tmp_path):
     finally:
         O._lib = saved
     assert failed, "planted mistake %r passed every pin" % name
+
+
+# Slips in the a-posteriori rule (Python, in oracle.py): each copy of the
+# function gets one and must fail the rule's hand cases.
+PY_MUTANTS = {
+    "posteriori_no_factor_2": ("l1_bound(c, M, 2.0 * m, normalize)", "l1_bound(c, M, m, normalize)"),
+    "posteriori_skips_T0": ("m = float(l1_hist[0])", "m = 0.0"),
+    "posteriori_current_term": ("m = max(m, float(l1_hist[M]))", "m = float(l1_hist[M])"),
+    "posteriori_lagging_max": ("m = max(m, float(l1_hist[M]))", "m = max(m, float(l1_hist[M - 1]))"),
+    "posteriori_reports_next_round": ("            return M\n", "            return M + 1\n"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTANTS))
+def test_planted_mistake_in_posteriori_rule_is_caught(name):
+    import inspect
+    import textwrap
+    from tests.test_oracle_pins import posteriori_hand_failures
+    src = textwrap.dedent(inspect.getsource(O.rounds_posteriori))
+    old, new = PY_MUTANTS[name]
+    assert src.count(old) == 1, name
+    ns = {"l1_bound": O.l1_bound}
+    exec(src.replace(old, new), ns)
+    assert posteriori_hand_failures(ns["rounds_posteriori"]) != [], name

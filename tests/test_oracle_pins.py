@@ -211,17 +211,37 @@ def test_posteriori_rule_against_exact_solution(c):
     assert max(margins) < 1.0
 
 
-def test_posteriori_rule_hand_case():
-    """Hand case: with ||T_j p||_1 = 1 for every j the estimate is 2, so the
-    rule's M is the first with l1_bound(c, M, 2) < tol."""
+def posteriori_hand_failures(rule):
+    """Hand cases of the a-posteriori rule (kappa replaced by twice the running
+    max of ||T_j p||_1 over j = 0..M); returns the names of the cases that
+    ``rule`` (same signature as ``oracle.rounds_posteriori``) gets wrong."""
     c, tol = 0.85, 1e-6
+    bad = []
     hist = np.ones(200)
+    # all terms 1: the estimate is 2, so M is the first with l1_bound(c, M, 2) < tol
     want = next(M for M in range(1, 200) if O.l1_bound(c, M, 2.0) < tol)
-    assert O.rounds_posteriori(c, tol, hist) == want
-    # a larger term later raises the estimate from that round on
+    if rule(c, tol, hist) != want:
+        bad.append("flat")
+    # a larger term at round want - 1 keeps the estimate up from there on
     hist2 = hist.copy(); hist2[want - 1] = 50.0
-    assert O.rounds_posteriori(c, tol, hist2) > want
-    assert O.rounds_posteriori(c, tol, hist[:want]) is None
+    if not rule(c, tol, hist2) > want:
+        bad.append("earlier_peak")
+    # a larger term at round want itself counts in round want's test
+    hist3 = hist.copy(); hist3[want] = 50.0
+    if not rule(c, tol, hist3) > want:
+        bad.append("peak_at_M")
+    # ||T_0 p||_1 = ||p||_1 counts too (j = 0 is in the max)
+    hist4 = hist.copy(); hist4[0] = 10.0
+    if rule(c, tol, hist4) != next(M for M in range(1, 200) if O.l1_bound(c, M, 20.0) < tol):
+        bad.append("T0")
+    # no M within a history too short to pass
+    if rule(c, tol, hist[:want]) is not None:
+        bad.append("short")
+    return bad
+
+
+def test_posteriori_rule_hand_case():
+    assert posteriori_hand_failures(O.rounds_posteriori) == []
 
 
 # -- closed forms ------------------------------------------------------------------
