@@ -13,6 +13,7 @@ import pytest
 import cpaa_inputs as ci
 from oracle import oracle as O
 from oracle import build as B
+from tests.test_oracle_pins import stopping_rule_truth_failures
 
 MUTANTS = {
     "recurrence_sign": ("s = 2.0 * s - j->T[u];", "s = 2.0 * s + j->T[u];"),
@@ -35,6 +36,10 @@ MUTANTS = {
                            "a[i * n + j] -= c / (double)(row_ptr[i + 1] - row_ptr[i]);"),
     "power_restart": ("job.T = x; job.Tpp = y; job.c = c; job.p = p;",
                       "job.T = p; job.Tpp = y; job.c = c; job.p = p;"),
+    "bound_normalisation_term_dropped": ("return E * kappa + (1.0 + E * kappa) * E / (1.0 - E);",
+                                         "return E * kappa;"),
+    "rounds_needed_one_late": ("if (orc_l1_bound(c, M, kappa, normalize) < tol) return M;",
+                               "if (orc_l1_bound(c, M, kappa, normalize) < tol) return M + 1;"),
 }
 
 
@@ -81,6 +86,7 @@ def _pins():
                 failed.append("power")
         except RuntimeError:
             failed.append("power")
+    failed += stopping_rule_truth_failures(c)
     return failed
 
 

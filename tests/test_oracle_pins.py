@@ -179,6 +179,52 @@ def test_l1_bound_holds(c):
                 assert err <= O.l1_bound(c, M, k, norm) * (1 + 1e-9) + 1e-15
 
 
+def stopping_rule_truth_failures(c):
+    """Pins of the rigorous stopping rule against the exact solution (LAPACK),
+    sharper than soundness; returns the names of the checks that fail.
+
+    - On a regular graph with uniform p every T_k p is p and kappa = 1, so the
+      (1-c)-scaled truncation misses exactly the coefficient mass ERR_M: its L1
+      error equals the normalize=1 bound ERR_M kappa (Eq. 41).
+    - There, rounds_needed's M is the first whose measured error is below tol.
+    - Dividing by the sum (Algorithm 1's last line) can cost more than
+      ERR_M kappa: on K_5 with one seed, c = 0.05, M = 1 the error is 1.27 x
+      ERR_M kappa, so the normalisation term of the normalize=0 bound is needed
+      and must cover it."""
+    bad = []
+    g = ci.circulant(30, [1, 4, 7])
+    rp, cx = g.numpy()
+    n = g.n
+    p = np.full(n, 1.0 / n)
+    ref = O.lapack_pagerank(rp, cx, p, c)
+    k = O.kappa(rp, p)
+    if abs(k - 1.0) > 1e-14:
+        bad.append("kappa_regular")
+    err = {M: np.abs(O.cpaa(rp, cx, p, c, M, normalize=1) - ref).sum() for M in range(1, 80)}
+    for M in (1, 2, 5, 13):
+        if abs(err[M] - O.l1_bound(c, M, k, 1)) > 1e-9 * err[M] + 1e-14:
+            bad.append("tight_M%d" % M)
+    for tol in (1e-2, 1e-4, 1e-7):
+        M = O.rounds_needed(c, tol, k, 1)
+        if not (1 <= M < 80 and err[M] < tol and (M == 1 or err[M - 1] >= tol)):
+            bad.append("minimal_%g" % tol)
+    g5 = ci.complete(5)
+    rp5, cx5 = g5.numpy()
+    e = np.zeros(5); e[0] = 1.0
+    k5 = O.kappa(rp5, e)
+    err0 = np.abs(O.cpaa(rp5, cx5, e, 0.05, 1, normalize=0) - O.lapack_pagerank(rp5, cx5, e, 0.05)).sum()
+    if not err0 > 1.2 * O.err_bound(0.05, 1) * k5:
+        bad.append("norm_case")
+    if not err0 <= O.l1_bound(0.05, 1, k5, 0):
+        bad.append("norm_term")
+    return bad
+
+
+@pytest.mark.parametrize("c", CS)
+def test_stopping_rule_against_exact_error(c):
+    assert stopping_rule_truth_failures(c) == []
+
+
 @pytest.mark.parametrize("c", CS)
 def test_posteriori_rule_against_exact_solution(c):
     """The a-posteriori rule (kappa replaced by twice the running max of
