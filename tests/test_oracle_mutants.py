@@ -13,7 +13,7 @@ import pytest
 import cpaa_inputs as ci
 from oracle import oracle as O
 from oracle import build as B
-from tests.test_oracle_pins import stopping_rule_truth_failures
+from tests.test_oracle_pins import power_stop_failures, stopping_rule_truth_failures
 
 MUTANTS = {
     "recurrence_sign": ("s = 2.0 * s - j->T[u];", "s = 2.0 * s + j->T[u];"),
@@ -40,6 +40,7 @@ MUTANTS = {
                                          "return E * kappa;"),
     "rounds_needed_one_late": ("if (orc_l1_bound(c, M, kappa, normalize) < tol) return M;",
                                "if (orc_l1_bound(c, M, kappa, normalize) < tol) return M + 1;"),
+    "power_stop_without_factor": ("if (c / (1.0 - c) * diff < tol) break;", "if (diff < tol) break;"),
 }
 
 
@@ -87,6 +88,8 @@ def _pins():
         except RuntimeError:
             failed.append("power")
     failed += stopping_rule_truth_failures(c)
+    if power_stop_failures():
+        failed.append("power_stop")
     return failed
 
 

@@ -110,6 +110,36 @@ def test_c_dense_solver_matches_lapack(gi):
     assert np.abs(O.dense_pagerank(rp, cx, p, 0.85) - O.lapack_pagerank(rp, cx, p, 0.85)).sum() < 1e-13
 
 
+def barbell(k):
+    """Two k-cliques joined by one edge: a slowly mixing graph."""
+    edges = [(i, j) for i in range(k) for j in range(i + 1, k)]
+    edges += [(k + i, k + j) for i in range(k) for j in range(i + 1, k)]
+    return ci.from_edges(2 * k, edges + [(k - 1, k)], name="barbell%d" % k)
+
+
+def power_stop_failures():
+    """The power method's stop test (c/(1-c)) ||x_{t+1} - x_t||_1 < tol bounds
+    the distance to pi* (cP shrinks L1 distances by c).  On a barbell graph
+    with one seed that bound is nearly attained (the error reaches 0.94 tol),
+    so the returned x must be within tol of the exact solution; returns the
+    failing (c, tol) cases."""
+    bad = []
+    g = barbell(20)
+    rp, cx = g.numpy()
+    p = np.zeros(g.n); p[0] = 1.0
+    for c in (0.85, 0.95):
+        ref = O.lapack_pagerank(rp, cx, p, c)
+        for tol in (1e-3, 1e-5, 1e-7, 1e-9):
+            x, _ = O.power(rp, cx, p, c, tol=tol)
+            if not np.abs(x - ref).sum() <= tol:
+                bad.append((c, tol))
+    return bad
+
+
+def test_power_method_stop_rule_against_exact_error():
+    assert power_stop_failures() == []
+
+
 @pytest.mark.parametrize("gi", range(8))
 def test_power_method_matches_lapack(gi):
     g = _graphs()[gi]
