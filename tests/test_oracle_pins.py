@@ -30,6 +30,20 @@ def test_coeffs_match_defining_integral(c):
         assert abs(ck[k] - ref) <= 1e-12 * max(1.0, abs(ck[0])), (k, ck[k], ref)
 
 
+@pytest.mark.parametrize("c", [0.1, 0.5, 0.85, 0.95, 0.99])
+def test_coeffs_match_printed_closed_forms(c):
+    """The proof of Proposition 1 (Sec. 4.2.1) prints c_0, c_1 and c_2 in closed
+    form, and sigma_k as a ratio of two expressions in c; the oracle's first
+    coefficients must equal the printed ones and its beta the printed sigma."""
+    r = math.sqrt(1.0 - c * c)
+    printed = [2.0 / r, 2.0 / c * (1.0 - r) / r, 2.0 / (c * c) * (2.0 * (1.0 - r) - c * c) / r]
+    ck = O.cheb_coeffs(c, 2)
+    for k in range(3):
+        assert abs(ck[k] - printed[k]) <= 1e-13 * printed[0], (k, ck[k], printed[k])
+    sigma = (c * c - (2.0 - c) * (1.0 - r)) / (c * c - c * (1.0 - r))
+    assert abs(O.beta(c) - sigma) <= 1e-12 * sigma
+
+
 @pytest.mark.parametrize("c", CS)
 def test_coeff_three_term_relation(c):
     """c_{k-1} + c_{k+1} = (2/c) c_k (proof of Proposition 1)."""
