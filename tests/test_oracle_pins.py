@@ -150,6 +150,19 @@ def power_stop_failures():
     return bad
 
 
+def test_power_method_ground_truth_rounds():
+    """Sec. 5.1 takes 210 power-method rounds at c = 0.85 as the ground truth
+    (0.85^210 is about 1.5e-15): after that many rounds the oracle's power
+    method agrees with LAPACK to rounding, also on the slowly mixing barbell."""
+    g0 = GOLD["ground_truth_power_rounds"]["value"]
+    for g in (barbell(20), ci.chung_lu(300, 2000, seed=3)):
+        rp, cx = g.numpy()
+        p = np.zeros(g.n); p[0] = 1.0
+        x, _ = O.power(rp, cx, p, 0.85, rounds=g0)
+        assert np.abs(x - O.lapack_pagerank(rp, cx, p, 0.85)).sum() < 1e-13, g.name
+    assert 0.85 ** g0 < 2e-15
+
+
 def test_power_method_stop_rule_against_exact_error():
     assert power_stop_failures() == []
 
