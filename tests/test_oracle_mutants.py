@@ -13,7 +13,8 @@ import pytest
 import cpaa_inputs as ci
 from oracle import oracle as O
 from oracle import build as B
-from tests.test_oracle_pins import power_stop_failures, stopping_rule_truth_failures
+from tests.test_oracle_pins import (negative_entry_truncation_failures, power_stop_failures,
+                                    stopping_rule_truth_failures)
 
 MUTANTS = {
     "recurrence_sign": ("s = 2.0 * s - j->T[u];", "s = 2.0 * s + j->T[u];"),
@@ -41,6 +42,8 @@ MUTANTS = {
     "rounds_needed_one_late": ("if (orc_l1_bound(c, M, kappa, normalize) < tol) return M;",
                                "if (orc_l1_bound(c, M, kappa, normalize) < tol) return M + 1;"),
     "power_stop_without_factor": ("if (c / (1.0 - c) * diff < tol) break;", "if (diff < tol) break;"),
+    "normaliser_sums_magnitudes": ("for (int64_t i = 0; i < n; ++i) s += pibar[i];",
+                                   "for (int64_t i = 0; i < n; ++i) s += fabs(pibar[i]);"),
 }
 
 
@@ -90,6 +93,7 @@ def _pins():
     failed += stopping_rule_truth_failures(c)
     if power_stop_failures():
         failed.append("power_stop")
+    failed += negative_entry_truncation_failures()
     return failed
 
 

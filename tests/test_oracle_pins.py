@@ -196,6 +196,29 @@ def test_truncation_matches_eigen_path(gi, M):
         assert np.abs(a - b).sum() < 1e-12, (g.name, M, norm)
 
 
+def negative_entry_truncation_failures():
+    """For c > 0.943 (beta^2 > 1/2) the degree-2 truncation's constant term
+    c_0/2 - c_2 is negative, so on K_50 with one seed (every neighbour of the
+    seed has degree 49) pibar_2 has a negative entry at the seed.  The
+    recurrence must still equal the eigen path there, in both normalisations
+    (Algorithm 1's last line divides by the signed sum)."""
+    bad = []
+    g = ci.complete(50)
+    rp, cx = g.numpy()
+    p = np.zeros(50); p[0] = 1.0
+    if not O.cpaa(rp, cx, p, 0.95, 2, normalize=1).min() < -1e-4:
+        bad.append("no_negative_entry")
+    for norm in (0, 1):
+        if np.abs(O.cpaa(rp, cx, p, 0.95, 2, normalize=norm)
+                  - O.eig_truncation(rp, cx, p, 0.95, 2, normalize=norm)).sum() > 1e-13:
+            bad.append("norm%d" % norm)
+    return bad
+
+
+def test_truncation_with_a_negative_entry():
+    assert negative_entry_truncation_failures() == []
+
+
 @pytest.mark.parametrize("c", CS)
 def test_truncated_sum_is_one_minus_err(c):
     """With (1-c) scaling the M-term result sums to exactly 1 - ERR_M (mass view of
