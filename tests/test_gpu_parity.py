@@ -149,6 +149,29 @@ def test_reversibility_on_gpu(pkg, uploaded):
     assert abs(a[t] / d[t] - b[s] / d[s]) < 1e-12 * max(a[t] / d[t], 1e-300) + 1e-15
 
 
+def test_truncation_with_a_negative_entry(pkg):
+    """At c = 0.95 the degree-2 truncation's constant term c_0/2 - c_2 is
+    negative, so on K_50 with one seed pibar after M = 2 rounds is negative at
+    the seed.  The device path matches the oracle there in both
+    normalisations (the divide-by-sum uses the signed sum)."""
+    g = ci.complete(50)
+    G = upload(pkg, g)
+    rp, cx = g.numpy()
+    p = np.zeros(50); p[0] = 1.0
+    assert O.cpaa(rp, cx, p, 0.95, 2, normalize=1).min() < -1e-4
+    for norm in (0, 1):
+        ref = O.cpaa(rp, cx, p, 0.95, 2, normalize=norm)
+        for prec in ("F64", "DF64", "F32"):
+            pi, info = solve(pkg, G, p, 0.95, fixed_rounds=2, normalize=norm,
+                             precision=getattr(pkg, "CPAA_" + prec))
+            assert info.rounds == 2
+            err = np.abs(pi - ref).sum()
+            if prec == "F32":
+                assert err / np.abs(ref).sum() <= 1e-6, (norm, err)
+            else:
+                assert err <= 1e-12, (prec, norm, err)
+
+
 def test_single_vertex_self_loop(pkg):
     G = upload(pkg, ci.from_edges(1, [(0, 0)], name="one"))
     pi, info = solve(pkg, G, np.ones(1), 0.85, 1e-10)
