@@ -219,10 +219,9 @@ struct GraphState {
     int W = 1;  // slots
     int w = 1;  // current tile width (a power of two, 1..W)
     cudaStream_t stream = nullptr;
-    // y, rho, comp and spare: interchangeable buffers of tile_bytes each
+    // y, rho, comp and spare: interchangeable buffers of tile_bytes(g, prec, W) each
     void *y[2] = {nullptr, nullptr};
     void *rho = nullptr, *comp = nullptr, *spare = nullptr, *long_part = nullptr;
-    size_t tile_bytes = 0;
     int *long_cnt = nullptr;
     double *red = nullptr, *result = nullptr, *part = nullptr, *sums = nullptr;
     size_t bytes = 0;
@@ -844,7 +843,6 @@ extern "C" cpaa_status cpaa_server_add_graph(cpaa_server *s, cpaa_graph *g, int 
     } while (0)
     {
         const size_t tb = tile_bytes(g, s->prec, W);
-        gs->tile_bytes = tb;
         if (s->fused) {  // every graph's work goes to the server's stream
             gs->stream = s->fstream;
             gs->own_stream = false;
