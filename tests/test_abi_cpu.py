@@ -189,3 +189,42 @@ def test_host_side_argument_checks(L):
     einval(lambda: L.Server(1 << 30, stop_rule=5), "unknown stop_rule")
     einval(lambda: L.cpaa_server_submit(None, 0, np.array([1], dtype=np.int32), None, 0.85, 1e-6), "NULL")
     einval(lambda: L.cpaa_server_get_stats(None), "NULL")
+
+
+def _fresh_python(code):
+    import subprocess
+    import sys
+    return subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True)
+
+
+def test_missing_library_fails_loudly(L):
+    """With no built library the binding raises on first use; there is no
+    other implementation to fall back to."""
+    r = _fresh_python(
+        "import paper_2112_01743_gb300.cpaa as m\n"
+        "m.library_path = '/nonexistent/libcpaa.so'\n"
+        "try:\n"
+        "    m.cpaa_options_init()\n"
+        "except ImportError as e:\n"
+        "    print('raised:', e)\n"
+        "else:\n"
+        "    print('no error')\n")
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.startswith("raised:") and "not built" in r.stdout, r.stdout
+
+
+def test_product_never_loads_the_oracle(L):
+    """The library and its binding import nothing from oracle/ (only the tests,
+    the smoke check and the benchmark's CPU leg may)."""
+    r = _fresh_python(
+        "import sys, paper_2112_01743_gb300 as pkg\n"
+        "pkg.cpaa_options_init(); pkg.cpaa_rounds_needed(0.85, 1e-6, 10.0)\n"
+        "print(sorted(m for m in sys.modules if m == 'oracle' or m.startswith('oracle.')))\n")
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == "[]", r.stdout
+    for dirpath, _, files in os.walk(os.path.join(ROOT, "paper_2112_01743_gb300")):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle\b", src, re.M), f
+                assert "cpaa_oracle" not in src and "liboracle" not in src, f
