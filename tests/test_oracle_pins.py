@@ -444,3 +444,49 @@ def test_thread_count_does_not_change_result():
     a = O.cpaa(rp, cx, p, 0.85, 20, nthreads=1)
     b = O.cpaa(rp, cx, p, 0.85, 20, nthreads=7)
     assert np.array_equal(a, b)
+
+
+# -- fuzzing: random small graphs, self-loops included ---------------------------
+
+def _random_graph(n, density, loops, seed):
+    """Random symmetric graph on n vertices; every vertex gets degree >= 1 (a
+    self-loop is one entry and counts once in d_u, Sec. 2.1)."""
+    rng = np.random.default_rng(seed)
+    edges = [(u, v) for u in range(n) for v in range(u + 1, n) if rng.random() < density]
+    edges += [(u, u) for u in range(n) if rng.random() < loops]
+    deg = np.zeros(n, dtype=int)
+    for u, v in edges:
+        deg[u] += 1
+        deg[v] += u != v
+    edges += [(u, u) for u in range(n) if deg[u] == 0]
+    return ci.from_edges(n, edges, name="fuzz")
+
+
+def test_fuzz_truncation_and_solution_on_random_small_graphs():
+    """Random graphs of 1-12 vertices with self-loops, random p on the simplex,
+    c and M: the recurrence equals the eigen path after M rounds in both
+    normalisations, and a converged solve equals LAPACK."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+
+    @hyp.settings(max_examples=80, deadline=None, derandomize=True)
+    @hyp.given(n=st.integers(1, 12), density=st.floats(0.0, 1.0), loops=st.floats(0.0, 1.0),
+               seed=st.integers(0, 2 ** 31 - 1), c=st.floats(0.05, 0.97), M=st.integers(0, 25),
+               single=st.booleans())
+    def check(n, density, loops, seed, c, M, single):
+        g = _random_graph(n, density, loops, seed)
+        rp, cx = g.numpy()
+        rng = np.random.default_rng(seed + 1)
+        if single:
+            p = np.zeros(n); p[rng.integers(n)] = 1.0
+        else:
+            p = rng.dirichlet(np.ones(n))
+        scale = O.cheb_coeffs(c, 0)[0]
+        for norm in (0, 1):
+            a = O.cpaa(rp, cx, p, c, M, normalize=norm)
+            b = O.eig_truncation(rp, cx, p, c, M, normalize=norm)
+            assert np.abs(a - b).sum() <= 1e-12 * max(1.0, scale), (n, c, M, norm)
+        pi, _ = O.solve(rp, cx, p, c, 1e-12)
+        assert np.abs(pi - O.lapack_pagerank(rp, cx, p, c)).sum() <= 1e-11
+
+    check()
