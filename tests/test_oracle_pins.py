@@ -5,6 +5,7 @@ forms derived by hand, invariants, and brute force on tiny graphs."""
 import json
 import math
 import os
+import warnings
 
 import numpy as np
 import pytest
@@ -13,7 +14,8 @@ from scipy import integrate
 import cpaa_inputs as ci
 from oracle import oracle as O
 
-GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+with open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")) as _f:
+    GOLD = json.load(_f)
 CS = [0.5, 0.85, 0.95]
 
 
@@ -24,8 +26,14 @@ def test_coeffs_match_defining_integral(c):
     """c_k = (2/pi) int_0^pi cos(kt)/(1 - c cos t) dt, by adaptive quadrature."""
     ck = O.cheb_coeffs(c, 40)
     for k in range(0, 41, 3):
-        val, err = integrate.quad(lambda t: math.cos(k * t) / (1.0 - c * math.cos(t)),
-                                  0.0, math.pi, limit=400, epsabs=1e-15, epsrel=1e-13)
+        # the oscillatory rule (weight cos(k t)) keeps its accuracy at large k,
+        # where c_k is a tiny remainder of cancelling lobes; QUADPACK then
+        # reports that no relative tolerance is reachable, while the assertion
+        # below bounds the difference absolutely
+        with warnings.catch_warnings():
+            warnings.simplefilter("ignore", integrate.IntegrationWarning)
+            val, err = integrate.quad(lambda t: 1.0 / (1.0 - c * math.cos(t)), 0.0, math.pi,
+                                      weight="cos", wvar=k, limit=400, epsabs=1e-15, epsrel=1e-13)
         ref = 2.0 / math.pi * val
         assert abs(ck[k] - ref) <= 1e-12 * max(1.0, abs(ck[0])), (k, ck[k], ref)
 
