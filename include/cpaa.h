@@ -71,8 +71,11 @@ typedef enum { CPAA_F64 = 0, CPAA_F32 = 1, CPAA_BF16 = 2, CPAA_DF64 = 3 } cpaa_p
 
 /* cpaa_graph_create flags */
 #define CPAA_GRAPH_DEVICE_INPUT 1u /* row_ptr / col_idx are device pointers */
-#define CPAA_GRAPH_VALIDATE 2u     /* also check column range, row order and symmetry
-                                      (one device pass over col_idx) */
+#define CPAA_GRAPH_VALIDATE 2u     /* accepted and ignored: the row-order and symmetry
+                                      checks it once enabled are now the default */
+#define CPAA_GRAPH_TRUSTED 4u      /* skip the row-order and symmetry checks (one device
+                                      pass over col_idx) for a CSR the caller has already
+                                      checked; the column range is checked regardless */
 
 /* cpaa_options.flags */
 #define CPAA_DEVICE_IO 1u   /* p / pi (P / PI) are device pointers */
@@ -113,8 +116,10 @@ typedef struct {
     void *stream;             /* cudaStream_t to run on; NULL = legacy default stream */
     double *history;          /* optional host array [2*(M+1)]: sum T_k and sum |T_k|
                                  for k = 0..M (the mass view of Sec. 4.1); cpaa_solve only */
-    int batch_width;          /* cpaa_solve_batch: vectors per tile, 1/2/4/8/16, or 0 to pick
-                                 the widest whose gathered array fits in L2 (default 0) */
+    int batch_width;          /* cpaa_solve_batch: vectors per tile, 1/2/4/8/16, or 0 (default):
+                                 the first batch of at least 16 columns of a precision on a
+                                 graph times a few rounds at every width on its own columns
+                                 and keeps the fastest per column for that graph */
     cpaa_stop_rule stop_rule; /* default CPAA_STOP_RIGOROUS; cpaa_solve and cpaa_solve_batch */
 } cpaa_options;
 
@@ -140,13 +145,16 @@ void cpaa_options_init(cpaa_options *opt);
  *   nnz      CSR entries, row_ptr[n]; 0 < nnz < 2^31
  *   row_ptr  int32[n+1], host or device (CPAA_GRAPH_DEVICE_INPUT)
  *   col_idx  int32[nnz], same memory space as row_ptr
- *   flags    CPAA_GRAPH_DEVICE_INPUT | CPAA_GRAPH_VALIDATE
+ *   flags    CPAA_GRAPH_DEVICE_INPUT | CPAA_GRAPH_TRUSTED
  *   out      receives the handle; release with cpaa_graph_destroy
  * Always checked: row_ptr[0] = 0, row_ptr non-decreasing, row_ptr[n] = nnz,
- * every degree >= 1.  With CPAA_GRAPH_VALIDATE also: 0 <= col_idx < n,
- * strictly ascending rows, and A symmetric (the remark closing Sec. 3:
- * Eq. 31 needs the real spectrum that an undirected graph gives).  Violations return
- * CPAA_EINVAL and no handle.  Runs on the current CUDA device. */
+ * every degree >= 1 (on the host), and 0 <= col_idx < n (on the device, in
+ * the relabelling pass; an out-of-range id is never used as an index).
+ * Unless CPAA_GRAPH_TRUSTED is given, also: strictly ascending rows (no
+ * duplicate entries) and A symmetric (the remark closing Sec. 3: Eq. 31 needs
+ * the real spectrum that an undirected graph gives).  Violations return
+ * CPAA_EINVAL, with the counts in cpaa_last_error, and no handle.  Runs on
+ * the current CUDA device. */
 cpaa_status cpaa_graph_create(int64_t n, int64_t nnz, const int32_t *row_ptr,
                               const int32_t *col_idx, unsigned flags, cpaa_graph **out);
 
@@ -302,20 +310,22 @@ cpaa_status cpaa_server_destroy(cpaa_server *s);
  *                             memory; 1 <= n <= CPAA_NOALLOC_MAX_N
  *   p                         FP64[n] in device memory, p >= 0, sum 1 (not checked)
  *   c                         damping factor in (0, 1)
- *   rounds                    Algorithm 1's M (0..2000); cpaa_rounds_needed
- *                             gives the M for a tolerance
+ *   rounds                    number of recurrence rounds (0..2000);
+ *                             cpaa_rounds_needed gives it for a tolerance
  *   normalize                 as in cpaa_options
  *   pi                        FP64[n] output in device memory
  *   stream                    cudaStream_t, NULL = legacy default stream
  * Arithmetic is FP64 and matches cpaa_solve with fixed_rounds = rounds to
- * rounding.  The call returns after the stream has finished its work (it reads
- * back an error counter): CPAA_EINVAL if n is beyond CPAA_NOALLOC_MAX_N or an
- * argument is out of range, and also if the CSR had a column outside [0, n) or
- * a row of degree <= 0 (such entries are skipped, never read out of bounds).
- * The first call on a device looks up the scratch array's address (make it
- * before any stream capture).  All calls share that array and it keeps the
- * previous call's contents; calls that overlap on the GPU race, so serialise
- * them. */
+ * rounding.  Every call blocks: it reads back an error counter and returns
+ * only after the stream has finished its work, so it must never be called on
+ * a stream that is being captured into a CUDA graph.  It returns CPAA_EINVAL
+ * if n is beyond CPAA_NOALLOC_MAX_N or an argument is out of range, and also
+ * if the CSR has a column outside [0, n) or a row of degree <= 0, whatever
+ * `rounds` is (such entries are skipped, never read out of bounds).  A call on
+ * a device whose scratch address is not yet known looks it up first (a failed
+ * lookup is retried by the next call).  All calls share that array and it
+ * keeps the previous call's contents; calls that overlap on the GPU race, so
+ * serialise them. */
 cpaa_status cpaa_solve_fixed_noalloc(int64_t n, int64_t nnz, const int32_t *row_ptr,
                                      const int32_t *col_idx, const double *p, double c,
                                      int rounds, int normalize, double *pi, void *stream);

@@ -15,6 +15,7 @@ __all__ = [
     "CPAA_OK", "CPAA_EINVAL", "CPAA_ENOMEM", "CPAA_ENOTCONV", "CPAA_ECUDA", "CPAA_ETIMEOUT",
     "CPAA_EBUSY", "CPAA_ECANCELLED", "CPAA_ENOTFOUND",
     "CPAA_F64", "CPAA_F32", "CPAA_BF16", "CPAA_DF64", "CPAA_GRAPH_DEVICE_INPUT", "CPAA_GRAPH_VALIDATE",
+    "CPAA_GRAPH_TRUSTED",
     "CPAA_DEVICE_IO", "CPAA_TIME_ROUNDS", "CPAA_SERVER_FUSED", "CPAA_STOP_RIGOROUS", "CPAA_STOP_POSTERIORI",
     "cpaa_options_init", "cpaa_graph_create", "cpaa_graph_destroy", "cpaa_graph_info", "cpaa_graph_layout",
     "CpaaLayout", "cpaa_solve", "cpaa_solve_batch", "cpaa_rounds_needed", "cpaa_l1_bound",
@@ -27,7 +28,7 @@ __all__ = [
 CPAA_OK, CPAA_EINVAL, CPAA_ENOMEM, CPAA_ENOTCONV, CPAA_ECUDA = 0, 1, 2, 3, 4
 CPAA_ETIMEOUT, CPAA_EBUSY, CPAA_ECANCELLED, CPAA_ENOTFOUND = 5, 6, 7, 8
 CPAA_F64, CPAA_F32, CPAA_BF16, CPAA_DF64 = 0, 1, 2, 3
-CPAA_GRAPH_DEVICE_INPUT, CPAA_GRAPH_VALIDATE = 1, 2
+CPAA_GRAPH_DEVICE_INPUT, CPAA_GRAPH_VALIDATE, CPAA_GRAPH_TRUSTED = 1, 2, 4
 CPAA_DEVICE_IO = 1
 CPAA_NOALLOC_MAX_N = 1300000
 CPAA_SERVER_MAX_SEEDS = 64
@@ -404,12 +405,14 @@ def cpaa_last_error():
 class Graph:
     """Owning wrapper of a cpaa_graph handle."""
 
-    def __init__(self, row_ptr, col_idx, n=None, validate=False):
+    def __init__(self, row_ptr, col_idx, n=None, validate=True):
+        """validate=False passes CPAA_GRAPH_TRUSTED (no row-order or symmetry
+        check; the column range is checked either way)."""
         n = int(n if n is not None else len(row_ptr) - 1)
         nnz = int(col_idx.numel() if hasattr(col_idx, "numel") else len(col_idx))
         self.n, self.nnz = n, nnz
         self.handle = cpaa_graph_create(n, nnz, row_ptr, col_idx,
-                                        CPAA_GRAPH_VALIDATE if validate else 0)
+                                        0 if validate else CPAA_GRAPH_TRUSTED)
 
     def info(self):
         return cpaa_graph_info(self.handle)

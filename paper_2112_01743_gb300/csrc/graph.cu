@@ -75,11 +75,23 @@ __global__ void vertex_arrays_kernel(const int32_t *__restrict__ row_ptr,
 }
 
 // Column ids in the new vertex order (in place; col_idx is the library's own
-// device copy).
-__global__ void relabel_kernel(int32_t *col, const int32_t *__restrict__ inv_perm, int64_t nnz) {
+// device copy).  Every column is range-checked here, whatever the caller's
+// flags: an id outside [0, n) is counted in *bad and replaced by 0, so it is
+// never used as an index (the caller then rejects the graph).
+__global__ void relabel_kernel(int32_t *col, const int32_t *__restrict__ inv_perm, int64_t n, int64_t nnz,
+                               unsigned long long *bad) {
+    unsigned long long nbad = 0;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
-         e += (int64_t)gridDim.x * blockDim.x)
-        col[e] = inv_perm[col[e]];
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = col[e];
+        if (v < 0 || v >= n) {
+            ++nbad;
+            col[e] = 0;
+        } else {
+            col[e] = inv_perm[v];
+        }
+    }
+    if (nbad) atomicAdd(bad, nbad);
 }
 
 // One warp per SELL chunk: lane l writes entry i of row n_hub + 32c + l at
@@ -226,11 +238,14 @@ static void host_layout(const int32_t *rp, int64_t n, int hub_deg, int tile, Hos
     std::stable_sort(L.chunk_order.begin(), L.chunk_order.end(),
                      [&](int32_t a, int32_t b) { return L.chunk_len[a] > L.chunk_len[b]; });
     // one 16-byte descriptor per chunk in processing order: the round kernel
-    // finds a chunk's row, offset and length with a single load
+    // finds a chunk's row, offset, stored length and longest row (the entries
+    // it gathers per lane; the stored groups past it are never read) with a
+    // single load
     L.chunk_desc.resize((size_t)nch);
     for (int64_t i = 0; i < nch; ++i) {
         const int32_t c = L.chunk_order[(size_t)i];
-        L.chunk_desc[(size_t)i] = make_int4(c, (int)(L.chunk_off[c] / (kChunkRows * kSellVec)), L.chunk_len[c], 0);
+        L.chunk_desc[(size_t)i] = make_int4(c, (int)(L.chunk_off[c] / (kChunkRows * kSellVec)), L.chunk_len[c],
+                                            deg(rest[(size_t)c * kChunkRows]));
     }
 }
 
@@ -270,6 +285,7 @@ extern "C" cpaa_status cpaa_graph_create(int64_t n, int64_t nnz, const int32_t *
     cudaGetDevice(&g->device);
     cpaa_status st;
     int32_t *d_rp = nullptr, *d_ci = nullptr, *d_inv = nullptr, *d_rs = nullptr;
+    unsigned long long *d_bad = nullptr;  // [0..2] validate_kernel, [3] relabel_kernel
     void *d_tmp = nullptr;
     size_t rp_bytes = sizeof(int32_t) * (n + 1), ci_bytes = sizeof(int32_t) * nnz, tmp_bytes = 0;
 #define ALLOC(ptr, bytes)                                                      \
@@ -290,15 +306,15 @@ extern "C" cpaa_status cpaa_graph_create(int64_t n, int64_t nnz, const int32_t *
         CK(cudaMemcpy(d_rp, row_ptr, rp_bytes, kind));
         CK(cudaMemcpy(d_ci, col_idx, ci_bytes, kind));
 
-        if (flags & CPAA_GRAPH_VALIDATE) {
-            unsigned long long *bad = nullptr;
-            ALLOC(bad, 3 * sizeof(unsigned long long));
-            CK(cudaMemset(bad, 0, 3 * sizeof(unsigned long long)));
-            validate_kernel<<<1024, 256>>>(d_rp, d_ci, n, nnz, bad);
+        // order and symmetry (and column range) unless the caller vouches for
+        // the CSR; the column range alone is checked again by relabel_kernel
+        ALLOC(d_bad, 4 * sizeof(unsigned long long));
+        CK(cudaMemset(d_bad, 0, 4 * sizeof(unsigned long long)));
+        if (!(flags & CPAA_GRAPH_TRUSTED)) {
+            validate_kernel<<<1024, 256>>>(d_rp, d_ci, n, nnz, d_bad);
             CK(cudaGetLastError());
             unsigned long long hb[3];
-            CK(cudaMemcpy(hb, bad, sizeof(hb), cudaMemcpyDeviceToHost));
-            dev_free(g, (void **)&bad, 3 * sizeof(unsigned long long));
+            CK(cudaMemcpy(hb, d_bad, sizeof(hb), cudaMemcpyDeviceToHost));
             if (hb[0] || hb[1] || hb[2]) {
                 st = fail(CPAA_EINVAL, "invalid CSR: " + std::to_string(hb[0]) + " column(s) out of range, " +
                                            std::to_string(hb[1]) + " unsorted/duplicate entr(ies), " +
@@ -341,8 +357,18 @@ extern "C" cpaa_status cpaa_graph_create(int64_t n, int64_t nnz, const int32_t *
 
         // the relabelled graph's CSR: every caller row's entries in new ids,
         // sorted ascending (the order in which the round adds them)
-        relabel_kernel<<<(unsigned)std::min<int64_t>((nnz + 255) / 256, 16384), 256>>>(d_ci, d_inv, nnz);
+        relabel_kernel<<<(unsigned)std::min<int64_t>((nnz + 255) / 256, 16384), 256>>>(d_ci, d_inv, n, nnz,
+                                                                                      d_bad + 3);
         CK(cudaGetLastError());
+        {
+            unsigned long long nbad = 0;
+            CK(cudaMemcpy(&nbad, d_bad + 3, sizeof(nbad), cudaMemcpyDeviceToHost));
+            if (nbad) {
+                st = fail(CPAA_EINVAL, "invalid CSR: " + std::to_string(nbad) + " column(s) out of range [0, n)");
+                goto fail_out;
+            }
+        }
+        dev_free(g, (void **)&d_bad, 4 * sizeof(unsigned long long));
         CK(cub::DeviceSegmentedSort::SortKeys(nullptr, tmp_bytes, d_ci, d_rs, nnz, n, d_rp, d_rp + 1));
         ALLOC(d_tmp, std::max<size_t>(tmp_bytes, 16));
         ALLOC(d_rs, ci_bytes);
@@ -394,6 +420,7 @@ extern "C" cpaa_status cpaa_graph_create(int64_t n, int64_t nnz, const int32_t *
         return CPAA_OK;
     }
 fail_out:
+    if (d_bad) dev_free(g, (void **)&d_bad, 4 * sizeof(unsigned long long));
     if (d_tmp) dev_free(g, &d_tmp, std::max<size_t>(tmp_bytes, 16));
     if (d_rs) dev_free(g, (void **)&d_rs, ci_bytes);
     if (d_inv) dev_free(g, (void **)&d_inv, sizeof(int32_t) * n);

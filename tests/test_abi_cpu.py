@@ -28,6 +28,17 @@ def test_header_declares_the_binding_names(L):
     assert _declared() == sorted(L.EXPORTED_SYMBOLS)
 
 
+def test_header_constants_match_the_binding(L):
+    """The flag and limit macros of include/cpaa.h have the binding's values."""
+    src = open(os.path.join(ROOT, "include", "cpaa.h")).read()
+    names = ("CPAA_GRAPH_DEVICE_INPUT", "CPAA_GRAPH_VALIDATE", "CPAA_GRAPH_TRUSTED", "CPAA_DEVICE_IO",
+             "CPAA_TIME_ROUNDS", "CPAA_SERVER_FUSED", "CPAA_NOALLOC_MAX_N", "CPAA_SERVER_MAX_SEEDS")
+    for name in names:
+        m = re.search(r"#define\s+%s\s+(\d+)u?\b" % name, src)
+        assert m, name
+        assert int(m.group(1)) == getattr(L, name), name
+
+
 def test_library_exports_every_declared_symbol(L):
     lib = L.lib()
     for name in _declared():

@@ -219,6 +219,52 @@ def test_invalid_graphs(pkg):
                               torch.tensor([1, 0, 0], dtype=torch.int32).cuda())
 
 
+def test_invalid_graphs_default_flags(pkg):
+    """With the default flags (no CPAA_GRAPH_VALIDATE) an asymmetric CSR, an
+    unsorted row and a column >= n or < 0 are rejected with CPAA_EINVAL
+    (Sec. 2.1: A symmetric; the remark closing Sec. 3), with the offending
+    count in the message; host and device inputs alike."""
+    import re
+    cases = [(2, [0, 1, 2], [1, 1], r"[1-9]\d* entr\(ies\) without a mirror"),   # 0 -> 1, no 1 -> 0
+             (3, [0, 2, 3, 4], [1, 2, 0, 1], r"2 entr\(ies\) without a mirror"),  # 0-2 and 2-1 unmatched
+             (2, [0, 1, 2], [1, 2], r"^.*: 1 column\(s\) out of range"),           # column n
+             (2, [0, 1, 2], [1, -1], r"^.*: 1 column\(s\) out of range"),          # negative column
+             (3, [0, 2, 3, 4], [2, 1, 0, 0], r"[1-9]\d* unsorted")]
+    for n, rp, cx, msg in cases:
+        for dev in (False, True):
+            r = torch.tensor(rp, dtype=torch.int32)
+            c = torch.tensor(cx, dtype=torch.int32)
+            if dev:
+                r, c = r.cuda(), c.cuda()
+            with pytest.raises(pkg.CpaaError) as ei:
+                pkg.cpaa_graph_create(n, len(cx), r, c)
+            assert ei.value.status == pkg.CPAA_EINVAL
+            assert re.search(msg, str(ei.value)), str(ei.value)
+
+
+def test_out_of_range_column_trusted(pkg):
+    """CPAA_GRAPH_TRUSTED skips the order and symmetry checks, never the column
+    range: the relabelling pass counts the bad entry (it is not used as an
+    index) and the graph is rejected; a valid graph created trusted solves
+    like a checked one."""
+    for cx in ([1, 2], [1, -7], [1, 1 << 30]):
+        with pytest.raises(pkg.CpaaError) as ei:
+            pkg.cpaa_graph_create(2, 2, torch.tensor([0, 1, 2], dtype=torch.int32).cuda(),
+                                  torch.tensor(cx, dtype=torch.int32).cuda(), pkg.CPAA_GRAPH_TRUSTED)
+        assert ei.value.status == pkg.CPAA_EINVAL
+        assert "out of range" in str(ei.value)
+    g = ci.chung_lu(3000, 20000, seed=11)
+    G1 = upload(pkg, g, validate=True)
+    G2 = upload(pkg, g, validate=False)
+    p = np.zeros(g.n)
+    p[[1, 2000]] = 0.5
+    a, ia = solve(pkg, G1, p, 0.85)
+    b, ib = solve(pkg, G2, p, 0.85)
+    assert ia.rounds == ib.rounds and np.array_equal(a, b)
+    G1.close()
+    G2.close()
+
+
 def test_batch_columns_equal_single(pkg, uploaded):
     g, G = GRAPHS[13], uploaded[13]
     B = 5
