@@ -10,13 +10,17 @@
 // kNoAllocScratchBytes (32 MiB), that the library reserves on each GPU that
 // loads it and keeps until the process exits.
 //
-// Set-up: the first call on a device (with that device current) looks up the
-// array's device address with cudaGetSymbolAddress and caches it per device;
-// make that first call before any stream capture.  Every later call reuses the
-// same array, which keeps the previous call's contents.  Every value a call
-// reads from the array is written earlier in the same call, except the error
-// counter, which is cleared at the start.  Calls whose work overlaps on the GPU
-// (two streams, or two host threads) race on the array: serialise them.
+// Set-up: a call on a device whose scratch address is not yet known (with
+// that device current) looks it up with cudaGetSymbolAddress and caches it
+// for that device; only a successful lookup is cached, so a lookup that
+// failed (for instance for lack of memory to load the module) is tried again
+// by the next call.  Every call reads back an error counter and waits for its
+// stream, so no call may be made on a stream that is being captured.  Every
+// later call reuses the same array, which keeps the previous call's contents.
+// Every value a call reads from the array is written earlier in the same
+// call, except the error counter, which is cleared at the start.  Calls whose
+// work overlaps on the GPU (two streams, or two host threads) race on the
+// array: serialise them.
 //
 // The kernels are a plain FP64 variant of the round kernel in step.cu: one
 // warp per row, lanes striding over the row's entries, a fixed shuffle tree
@@ -37,9 +41,8 @@ constexpr size_t kAlign = 256;
 
 static __device__ __align__(256) unsigned char g_scratch[kNoAllocScratchBytes];
 
-static void *g_scratch_ptr[kMaxDevices];
-static std::once_flag g_once[kMaxDevices];
-static cudaError_t g_setup_err[kMaxDevices];
+static void *g_scratch_ptr[kMaxDevices];  // cached device address, NULL until a lookup succeeds
+static std::mutex g_setup_mu;
 
 static size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -122,6 +125,19 @@ __global__ void __launch_bounds__(kThreadsNA) na_round(const int32_t *__restrict
     }
 }
 
+// Column range check on its own, for a call with no rounds (na_round checks
+// the columns it gathers in every round).
+__global__ void __launch_bounds__(kThreadsNA) na_check_cols(const int32_t *__restrict__ ci, int64_t n,
+                                                            int64_t nnz, unsigned long long *err) {
+    unsigned long long bad = 0;
+    for (int64_t e = blockIdx.x * (int64_t)kThreadsNA + threadIdx.x; e < nnz;
+         e += (int64_t)gridDim.x * kThreadsNA) {
+        const int32_t j = ci[e];
+        if (j < 0 || j >= n) ++bad;
+    }
+    if (bad) atomicAdd(err, bad);
+}
+
 // Fixed-order sum of d_u rho[u]: per-CTA partials over a fixed grid.
 __global__ void __launch_bounds__(kThreadsNA) na_norm_part(const int32_t *__restrict__ rp,
                                                            const double *__restrict__ rho,
@@ -165,18 +181,24 @@ __global__ void __launch_bounds__(kThreadsNA) na_finalize(const int32_t *__restr
         pi[u] = scale * ((double)deg_of(rp, u) * rho[u]);
 }
 
-// Per-device address of g_scratch, looked up once with that device current.
+// Per-device address of g_scratch, looked up with that device current.  A
+// successful lookup is kept for the life of the process; a failed one is not,
+// so the next call tries again.
 static cudaError_t scratch_for_current_device(void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::call_once(g_once[dev], [dev]() {
+    std::lock_guard<std::mutex> lk(g_setup_mu);
+    if (!g_scratch_ptr[dev]) {
         void *ptr = nullptr;
-        g_setup_err[dev] = cudaGetSymbolAddress(&ptr, g_scratch);
-        g_scratch_ptr[dev] = (g_setup_err[dev] == cudaSuccess) ? ptr : nullptr;
-    });
-    if (g_setup_err[dev] != cudaSuccess) return g_setup_err[dev];
+        e = cudaGetSymbolAddress(&ptr, g_scratch);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return e;
+        }
+        g_scratch_ptr[dev] = ptr;
+    }
     *out = g_scratch_ptr[dev];
     return cudaSuccess;
 }
@@ -223,6 +245,10 @@ extern "C" cpaa_status cpaa_solve_fixed_noalloc(int64_t n, int64_t nnz, const in
     CPAA_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned long long), st));
     na_prep<<<grid, kThreadsNA, 0, st>>>(row_ptr, p, n, ck[0] / 2.0, y[0], rho, err);
     CPAA_CUDA(cudaGetLastError());
+    if (rounds == 0) {
+        na_check_cols<<<grid, kThreadsNA, 0, st>>>(col_idx, n, nnz, err);
+        CPAA_CUDA(cudaGetLastError());
+    }
     for (int k = 1; k <= rounds; ++k) {
         na_round<<<rgrid, kThreadsNA, 0, st>>>(row_ptr, col_idx, n, nnz, y[(k - 1) & 1], y[k & 1], rho,
                                                ck[k], k == 1, err);
