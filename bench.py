@@ -2,12 +2,15 @@
 """CPAA PageRank benchmark on one GB300 per rank.
 
 Workload (default): Chung-Lu power-law undirected graph, n = 2^24 vertices,
-2.56e8 endpoint-pair draws (exponent 2.1, seed 0) plus a Hamiltonian ring,
-symmetric int32 CSR; damping c = 0.85; uniform p = 1/n; stop when the
-rigorous L1 bound is below 1e-6.  One step = one full cpaa_solve (prep,
-kappa, M fused recurrence rounds, finalisation) on inputs already resident in
-HBM.  The CSR (about 2 GB of column indices) is far larger than the 126 MB
-L2, so no extra L2 flush is needed between steps.
+256M distinct undirected edges (the first 2.56e8 distinct pairs drawn,
+exponent 2.1, seed 0) plus a Hamiltonian ring, symmetric int32 CSR (about
+545M entries); damping c = 0.85; uniform p = 1/n; stop when the rigorous L1
+bound is below 1e-6.  One step = one full cpaa_solve in FP64, the paper's
+arithmetic (prep, kappa, M fused recurrence rounds, finalisation), on inputs
+already resident in HBM.  The CSR (about 2.2 GB of column indices) is far
+larger than the 126 MB L2, so no extra L2 flush is needed between steps.
+The same solve in FP32 and in double-float (DF64) is timed as named legs of
+the same line.
 
 Printed: one JSON line (rank 0).  ``value`` is GTEPS = nnz x rounds / s over
 all ranks; ``e2e`` is the same through the C ABI with host buffers (H2D of p
@@ -38,20 +41,20 @@ sys.path.insert(0, ROOT)
 METRIC = "CPAA GTEPS (% HBM roofline); time to 1e-6 L1 vs plain FP64 on same GB300"
 
 WORKLOADS = {
-    "chung_lu_16M": dict(n=1 << 24, edges=256_000_000, gamma=2.1, seed=0, c=0.85, tol=1e-6,
-                         desc="Chung-Lu n=2^24, 2.56e8 pair draws, gamma=2.1, seed 0, + ring; "
-                              "c=0.85, uniform p, tol 1e-6 L1"),
+    "chung_lu_16M": dict(n=1 << 24, edges=256_000_000, distinct=True, gamma=2.1, seed=0, c=0.85, tol=1e-6,
+                         desc="Chung-Lu power-law graph (exponent 2.1, seed 0), n=2^24 (16.7M) vertices, "
+                              "256M distinct undirected edges + ring; c=0.85, uniform p, tol 1e-6 L1"),
     "chung_lu_10k": dict(n=10_000, edges=100_000, gamma=2.1, seed=0, c=0.85, tol=1e-10,
                          desc="Chung-Lu n=10000, 1e5 pair draws, gamma=2.1, seed 0, + ring; "
                               "c=0.85, uniform p, tol 1e-10"),
-    "chung_lu_4M": dict(n=1 << 22, edges=64_000_000, gamma=2.1, seed=0, c=0.85, tol=1e-6,
-                        desc="Chung-Lu n=2^22, 6.4e7 pair draws, gamma=2.1, seed 0, + ring; "
+    "chung_lu_4M": dict(n=1 << 22, edges=64_000_000, distinct=True, gamma=2.1, seed=0, c=0.85, tol=1e-6,
+                        desc="Chung-Lu n=2^22, 64M distinct undirected edges, gamma=2.1, seed 0, + ring; "
                              "c=0.85, uniform p, tol 1e-6 L1"),
     "chung_lu_1M": dict(n=1 << 20, edges=16_000_000, gamma=2.1, seed=0, c=0.85, tol=1e-6,
                         desc="Chung-Lu n=2^20, 1.6e7 pair draws, gamma=2.1, seed 0, + ring; "
                              "c=0.85, uniform p, tol 1e-6 L1"),
-    "chung_lu_16M_shuffled": dict(n=1 << 24, edges=256_000_000, gamma=2.1, seed=0, c=0.85, tol=1e-6,
-                                  shuffle=1,
+    "chung_lu_16M_shuffled": dict(n=1 << 24, edges=256_000_000, distinct=True, gamma=2.1, seed=0, c=0.85,
+                                  tol=1e-6, shuffle=1,
                                   desc="Chung-Lu n=2^24 as chung_lu_16M, vertex ids randomly permuted "
                                        "(seed 1); c=0.85, uniform p, tol 1e-6 L1"),
     "grid_4096": dict(rows=4096, cols=4096, frac=0.2, seed=0, c=0.85, tol=1e-6,
@@ -183,7 +186,8 @@ def make_graph(wl, device):
     if "rows" in w:
         g = ci.grid_deleted(w["rows"], w["cols"], w["frac"], seed=w["seed"], device=device)
     else:
-        g = ci.chung_lu(w["n"], w["edges"], gamma=w["gamma"], seed=w["seed"], device=device)
+        g = ci.chung_lu(w["n"], w["edges"], gamma=w["gamma"], seed=w["seed"], device=device,
+                        distinct=w.get("distinct", False))
         if w.get("shuffle"):
             g = ci.shuffled(g, seed=w["shuffle"])
     return g, time.time() - t
@@ -240,7 +244,7 @@ def run_batch(pkg, args, stream):
     plain FP64 single-vector solve, per query (time to the same L1 bound)."""
     import torch
     import cpaa_inputs as ci
-    g = ci.chung_lu(1 << 22, 64_000_000, seed=0, device="cuda")
+    g = ci.chung_lu(1 << 22, 64_000_000, seed=0, device="cuda", distinct=True)
     n, nnz = g.n, g.nnz
     G = pkg.Graph(g.row_ptr, g.col_idx, n=n)
     del g
@@ -285,8 +289,8 @@ def run_batch(pkg, args, stream):
     G.close()
     rounds = [i.rounds for i in infos]
     rounds2 = [i.rounds for i in infos2]
-    return {"workload": "Chung-Lu n=2^22, 6.4e7 pair draws, gamma=2.1, seed 0, + ring; 256 vectors "
-                        "uniform over 1-16 seeds; c=0.85; tol 1e-6 L1",
+    return {"workload": "Chung-Lu n=2^22, 64M distinct undirected edges, gamma=2.1, seed 0, + ring; 256 "
+                        "vectors uniform over 1-16 seeds; c=0.85; tol 1e-6 L1",
             "n": n, "nnz": nnz, "B": B, "precision": "f32",
             "ms_batch": t_batch, "ms_per_query_batched_f32": t_batch / B,
             "ms_per_query_single_f64": t_single,
@@ -585,41 +589,31 @@ def run_ours(args):
     peak, peak_kind = measured_peak_gbs()
     achieved = ab / (round_ms * 1e-3) / 1e9
 
-    # ---- plain FP64 single-vector form on the same GPU (time to the same tol)
-    f64 = None
-    if prec != "f64" and not args.skip_f64:
-        for _ in range(3):
-            solve("f64")
-        torch.cuda.synchronize()
-        e0.record(stream)
-        inf64 = [solve("f64") for _ in range(args.steps)]
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = e0.elapsed_time(e1) / args.steps
-        r64 = sum(i.rounds_ms for i in inf64) / sum(i.rounds for i in inf64)
-        ab64 = alg_bytes_per_round(n, nnz, "f64")
-        l1 = float((pi_main - pi).abs().sum().item())
-        f64 = {"ms_per_solve": ms64, "gteps": nnz * inf64[0].rounds / (ms64 * 1e-3) / 1e9,
-               "rounds": inf64[0].rounds, "round_ms": r64,
-               "hbm_frac_of_measured": ab64 / (r64 * 1e-3) / 1e9 / peak,
-               "fp64_adds_per_round": nnz,
-               "speedup_of_%s" % prec: ms64 / (ms_total / args.steps),
-               "l1_%s_vs_f64" % prec: l1}
-        # the double-float form (FP64-class accuracy on the FP32 pipes)
-        pdf = torch.empty_like(p)
-        for _ in range(3):
-            G.solve(p, wl["c"], wl["tol"], pdf, precision=PREC["df64"])
-        torch.cuda.synchronize()
-        e0.record(stream)
-        infdf = [G.solve(p, wl["c"], wl["tol"], pdf, precision=PREC["df64"], time_rounds=True)
-                 for _ in range(args.steps)]
-        e1.record(stream)
-        torch.cuda.synchronize()
-        msdf = e0.elapsed_time(e1) / args.steps
-        rdf = sum(i.rounds_ms for i in infdf) / sum(i.rounds for i in infdf)
-        f64["df64"] = {"ms_per_solve": msdf, "round_ms": rdf,
-                       "hbm_frac_of_measured": alg_bytes_per_round(n, nnz, "df64") / (rdf * 1e-3) / 1e9 / peak,
-                       "l1_vs_f64": float((pdf - pi).abs().sum().item())}
+    # ---- the other number formats on the same graph and tolerance: FP32 (the
+    # 1e-6-relative path, time to the same L1 bound as the plain FP64 form) and
+    # DF64 (FP64-class accuracy on the FP32 pipes); FP64 when the main line is not
+    legs = {}
+    if not args.skip_legs:
+        for name in ("f64", "f32", "df64"):
+            if name == prec:
+                continue
+            out = torch.empty_like(p)
+            for _ in range(3):
+                G.solve(p, wl["c"], wl["tol"], out, precision=PREC[name])
+            torch.cuda.synchronize()
+            e0.record(stream)
+            inf = [G.solve(p, wl["c"], wl["tol"], out, precision=PREC[name], time_rounds=True)
+                   for _ in range(args.steps)]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            r = sum(i.rounds_ms for i in inf) / sum(i.rounds for i in inf)
+            legs[name] = {"ms_per_solve": ms, "rounds": inf[0].rounds, "round_ms": r,
+                          "gteps": nnz * inf[0].rounds / (ms * 1e-3) / 1e9,
+                          "hbm_frac_of_measured": alg_bytes_per_round(n, nnz, name) / (r * 1e-3) / 1e9 / peak,
+                          "l1_vs_%s" % prec: float((out - pi_main).abs().sum().item()),
+                          "speedup_vs_%s" % prec: (ms_total / args.steps) / ms}
+            del out
 
     # ---- the paper's comparison: power method (SPI) on the same kernels, same L1 bound
     power = None
@@ -634,9 +628,11 @@ def run_ours(args):
             e1.record(stream)
             torch.cuda.synchronize()
             ms_pow = e0.elapsed_time(e1) / args.steps
-            ms_cheb = (ms_total / args.steps) if name == prec else (f64["ms_per_solve"] if (f64 and name == "f64") else None)
+            ms_cheb = (ms_total / args.steps) if name == prec else (legs[name]["ms_per_solve"] if name in legs
+                                                                   else None)
             power[name] = {"rounds": pinf[0].rounds, "ms_per_solve": ms_pow,
-                           "cpaa_rounds": rounds if name == prec else (f64["rounds"] if f64 else None),
+                           "cpaa_rounds": rounds if name == prec else (legs[name]["rounds"] if name in legs
+                                                                       else None),
                            "cpaa_ms_per_solve": ms_cheb,
                            "cpaa_speedup": (ms_pow / ms_cheb) if ms_cheb else None,
                            "l1_vs_cpaa_same_precision": float((pp - pi_main).abs().sum().item()) if name == prec else None}
@@ -724,7 +720,7 @@ def run_ours(args):
         # per solve: stats + its block sum, prep, the rounds, the last round's two
         # fixed-order sum kernels, the normaliser's two kernels and the finalisation
         "gpu_launches": sum(i.rounds + 8 for i in infos),
-        "f64": f64,
+        "legs": legs,
         "power": power,
         "batch": batch,
         "small": small,
@@ -742,10 +738,11 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="chung_lu_16M")
-    ap.add_argument("--precision", choices=sorted(PREC), default="f32")
+    ap.add_argument("--precision", choices=sorted(PREC), default="f64",
+                    help="number format of the main line (default: FP64, the paper's)")
     ap.add_argument("--ref-rounds", type=int, default=2,
                     help="oracle rounds per CPU sample (bounded CPU work)")
-    ap.add_argument("--skip-f64", action="store_true")
+    ap.add_argument("--skip-legs", action="store_true", help="skip the other number formats")
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-serve", action="store_true")
     ap.add_argument("--skip-grid", action="store_true")

@@ -8,7 +8,10 @@ Workload recipes (the paper's own datasets are not available; these stand in):
 * ``chung_lu``: weights w_i = (i+1)^(-1/(gamma-1)); draw E endpoint pairs
   i.i.d. from categorical(w) by inverse CDF on 53-bit counter-based integers;
   drop self-loops and duplicates; add the ring (i, i+1 mod n) so every vertex
-  has degree >= 2.  Vertex ids stay in weight order (hubs first).
+  has degree >= 2.  Vertex ids stay in weight order (hubs first).  With
+  ``distinct=True``, E counts distinct edges instead of draws: the graph keeps
+  the first E distinct non-loop pairs in draw order (draws continue until E
+  are found), then adds the ring.
 * ``grid_deleted``: a rows x cols 4-neighbour lattice; every vertex but the
   corner (0,0) keeps one edge to its upper or left neighbour (chosen by a
   hashed bit), which forms a spanning tree; a seeded uniform sample of the
@@ -72,7 +75,20 @@ def from_edges(n, edges, device="cpu", name="edges"):
     return _csr_from_undirected_keys(n, keys, device, name)
 
 
-def chung_lu(n, edges, gamma=2.1, seed=0, ring=True, device="cpu", chunk=1 << 25):
+def _chung_lu_keys(n, cum_t, seed, start, stop, device):
+    """Keys min * n + max of draws [start, stop), self-loops dropped, in draw order."""
+    idx = rng.arange(start, stop, device)
+    r1 = rng.u53(seed, 0, idx)
+    r2 = rng.u53(seed, 1, idx)
+    u = torch.searchsorted(cum_t, r1, right=True)
+    v = torch.searchsorted(cum_t, r2, right=True)
+    del r1, r2, idx
+    keep = u != v
+    u, v = u[keep], v[keep]
+    return torch.minimum(u, v) * n + torch.maximum(u, v)
+
+
+def chung_lu(n, edges, gamma=2.1, seed=0, ring=True, device="cpu", chunk=1 << 25, distinct=False):
     """Chung-Lu power-law graph (see module docstring)."""
     i = np.arange(1, n + 1, dtype=np.float64)
     w = i ** (-1.0 / (gamma - 1.0))
@@ -81,20 +97,30 @@ def chung_lu(n, edges, gamma=2.1, seed=0, ring=True, device="cpu", chunk=1 << 25
     cum_int[-1] = 2 ** 53
     cum_t = torch.as_tensor(cum_int, device=device)
     parts = []
-    for start in range(0, edges, chunk):
-        stop = min(edges, start + chunk)
-        idx = rng.arange(start, stop, device)
-        r1 = rng.u53(seed, 0, idx)
-        r2 = rng.u53(seed, 1, idx)
-        u = torch.searchsorted(cum_t, r1, right=True)
-        v = torch.searchsorted(cum_t, r2, right=True)
-        del r1, r2, idx
-        keep = u != v
-        u, v = u[keep], v[keep]
-        lo = torch.minimum(u, v)
-        hi = torch.maximum(u, v)
-        parts.append(torch.unique(lo * n + hi))
-        del u, v, lo, hi
+    if distinct:
+        if edges > n * (n - 1) // 2:
+            raise ValueError("more distinct edges than vertex pairs")
+        have = torch.empty(0, dtype=torch.int64, device=device)  # kept keys, sorted
+        start = 0
+        while have.numel() < edges:
+            k = _chung_lu_keys(n, cum_t, seed, start, start + chunk, device)
+            start += chunk
+            if have.numel():
+                pos = torch.searchsorted(have, k).clamp_(max=have.numel() - 1)
+                k = k[have[pos] != k]
+            if k.numel() == 0:
+                continue
+            # first occurrence of each new key within the chunk, in draw order
+            uk, inv = torch.unique(k, return_inverse=True)
+            first = torch.full((uk.numel(),), k.numel(), dtype=torch.int64, device=device)
+            first.scatter_reduce_(0, inv, torch.arange(k.numel(), device=device), reduce="amin")
+            newk = uk[torch.argsort(first)][:edges - have.numel()]
+            have, _ = torch.sort(torch.cat([have, newk]))
+            del k, uk, inv, first, newk
+        parts.append(have)
+    else:
+        for start in range(0, edges, chunk):
+            parts.append(torch.unique(_chung_lu_keys(n, cum_t, seed, start, min(edges, start + chunk), device)))
     if ring and n > 1:
         a = rng.arange(0, n, device)
         b = (a + 1) % n
@@ -103,8 +129,8 @@ def chung_lu(n, edges, gamma=2.1, seed=0, ring=True, device="cpu", chunk=1 << 25
         parts.append(torch.unique(lo * n + hi))
     keys = torch.unique(torch.cat(parts))
     del parts
-    return _csr_from_undirected_keys(n, keys, device, "chung_lu(n=%d,E=%d,gamma=%g,seed=%d)"
-                                     % (n, edges, gamma, seed))
+    return _csr_from_undirected_keys(n, keys, device, "chung_lu(n=%d,E=%d%s,gamma=%g,seed=%d)"
+                                     % (n, edges, " distinct" if distinct else "", gamma, seed))
 
 
 def grid_deleted(rows, cols, frac=0.2, seed=0, device="cpu"):

@@ -54,7 +54,7 @@ def test_config_10k_eq41_rounds(pkg):
 
 @pytest.fixture(scope="module")
 def big_chung_lu(pkg):
-    g = ci.chung_lu(1 << 24, 256_000_000, seed=0, device="cuda")
+    g = ci.chung_lu(1 << 24, 256_000_000, seed=0, device="cuda", distinct=True)
     G = pkg.Graph(g.row_ptr, g.col_idx, n=g.n, validate=True)
     rp, cx = g.numpy()
     del g
@@ -64,8 +64,9 @@ def big_chung_lu(pkg):
 
 
 def test_config_16M_f64_and_f32(pkg, big_chung_lu):
-    """16.7M-vertex Chung-Lu, uniform p, c = 0.85, tol 1e-6: FP64 within 1e-12
-    L1 and FP32 within 1e-6 relative L1 of the oracle run for the same M."""
+    """16.7M-vertex Chung-Lu (256M distinct edges + ring), uniform p, c =
+    0.85, tol 1e-6: FP64 within 1e-12 L1 and FP32 within 1e-6 relative L1 of
+    the oracle run for the same M."""
     G, rp, cx = big_chung_lu
     n = len(rp) - 1
     p = torch.full((n,), 1.0 / n, dtype=torch.float64, device="cuda")
@@ -132,7 +133,7 @@ def test_config_batched_4M_sampled_columns(pkg):
     """4M-vertex Chung-Lu, 256 personalised vectors (1-16 uniform seeds), c =
     0.85, tol 1e-6, FP32 tiles: sampled columns against the oracle run for the
     same rounds, and every column normalised to 1."""
-    g = ci.chung_lu(1 << 22, 64_000_000, seed=0, device="cuda")
+    g = ci.chung_lu(1 << 22, 64_000_000, seed=0, device="cuda", distinct=True)
     G = pkg.Graph(g.row_ptr, g.col_idx, n=g.n)
     rp, cx = g.numpy()
     n = g.n

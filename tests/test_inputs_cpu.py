@@ -55,3 +55,34 @@ def test_shuffle_is_seeded():
     c = ci.shuffled(g, seed=4)
     assert np.array_equal(a.col_idx.numpy(), b.col_idx.numpy())
     assert not np.array_equal(a.col_idx.numpy(), c.col_idx.numpy())
+
+
+def test_chung_lu_distinct_keeps_the_first_distinct_pairs():
+    """chung_lu(distinct=True): exactly the first E distinct non-loop pairs in
+    draw order, plus the ring; the same graph whatever the draw chunk."""
+    import torch
+    from cpaa_inputs import rng
+    n, E = 5000, 30000
+    g = ci.chung_lu(n, E, seed=3, distinct=True, chunk=1 << 12)
+    w = np.arange(1, n + 1, dtype=np.float64) ** (-1.0 / 1.1)
+    cum = np.cumsum(w)
+    cum_int = np.floor(cum / cum[-1] * float(2 ** 53)).astype(np.int64)
+    cum_int[-1] = 2 ** 53
+    cum_t = torch.as_tensor(cum_int)
+    idx = rng.arange(0, 4 * E, "cpu")
+    u = torch.searchsorted(cum_t, rng.u53(3, 0, idx), right=True).tolist()
+    v = torch.searchsorted(cum_t, rng.u53(3, 1, idx), right=True).tolist()
+    seen, order = set(), []
+    for a, b in zip(u, v):
+        if a != b and (min(a, b), max(a, b)) not in seen:
+            seen.add((min(a, b), max(a, b)))
+            order.append((min(a, b), max(a, b)))
+            if len(order) == E:
+                break
+    assert len(order) == E
+    ring = {(min(i, (i + 1) % n), max(i, (i + 1) % n)) for i in range(n)}
+    rows, cx = _edge_set(g)
+    got = set(zip(rows[rows < cx].tolist(), cx[rows < cx].tolist()))
+    assert got == set(order) | ring
+    h = ci.chung_lu(n, E, seed=3, distinct=True, chunk=1 << 15)
+    assert torch.equal(g.row_ptr, h.row_ptr) and torch.equal(g.col_idx, h.col_idx)
