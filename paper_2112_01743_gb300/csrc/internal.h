@@ -32,7 +32,10 @@ namespace cpaa {
 // in groups of kSellVec entries per lane (entry i of lane l at
 // chunk_off[c] + 128 (i / 4) + 4 l + i % 4, so a warp reads 512 contiguous
 // bytes per load); padding entries hold the sentinel column n, whose iterate
-// value is kept at zero.  One warp owns one chunk, one lane one row.
+// value is kept at zero.  One warp owns one chunk, one lane one row.  The
+// round kernel reads each lane's first L entries only, L the chunk's longest
+// row (kept in the chunk's descriptor): a last, partial group gives its first
+// L mod kSellVec entries, so no sentinel is gathered past the longest row.
 // Windows are multiples of 32 rows, so a chunk never straddles two windows
 // and its first row is its longest.
 //
@@ -201,7 +204,7 @@ struct cpaa_graph {
     int64_t *chunk_off = nullptr;    // [num_chunks]
     int32_t *chunk_len = nullptr;    // [num_chunks]
     int32_t *chunk_order = nullptr;  // chunk ids, longest first
-    int4 *chunk_desc = nullptr;      // [num_chunks] in chunk_order: {chunk, offset / 128, length, 0}
+    int4 *chunk_desc = nullptr;      // [num_chunks] in chunk_order: {chunk, offset / 128, length, longest row}
     int hub_degree = cpaa::kHubDegree;  // rows above this degree are hub rows
     int hub_tile = cpaa::kMaxHubTile;   // entries of a hub tile
     int num_long_chunks = 0;         // leading chunk_order entries longer than kLongChunk
