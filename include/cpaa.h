@@ -76,6 +76,8 @@ typedef enum { CPAA_F64 = 0, CPAA_F32 = 1, CPAA_BF16 = 2, CPAA_DF64 = 3 } cpaa_p
 #define CPAA_GRAPH_TRUSTED 4u      /* skip the row-order and symmetry checks (one device
                                       pass over col_idx) for a CSR the caller has already
                                       checked; the column range is checked regardless */
+#define CPAA_GRAPH_AUTOTUNE 8u     /* cpaa_graph_create_ex: pick the layout parameters by
+                                      timing rounds on candidate layouts (see there) */
 
 /* cpaa_options.flags */
 #define CPAA_DEVICE_IO 1u   /* p / pi (P / PI) are device pointers */
@@ -169,16 +171,46 @@ cpaa_status cpaa_graph_info(const cpaa_graph *g, int64_t *n, int64_t *nnz,
 /* How cpaa_graph_create laid the graph out for the round kernels (no paper
  * counterpart: this is the GPU layout).  Rows above hub_degree are hub rows,
  * kept as CSR and cut into tiles of hub_tile entries, one CTA per tile; the
- * other rows form SELL chunks of 32 rows (sell_entries counts their entries
- * with padding), of which long_chunks, those above the long-chunk threshold,
- * get a CTA and the rest a warp. */
+ * other rows, sorted by degree within windows of sort_window rows, form SELL
+ * chunks of 32 rows (sell_entries counts their stored entries with padding),
+ * of which long_chunks, those whose longest row exceeds long_chunk entries,
+ * get a CTA and the rest a warp.  tuned = 1 when CPAA_GRAPH_AUTOTUNE picked
+ * the parameters after timing tune_candidates layouts. */
 typedef struct {
     int64_t hub_rows, hub_entries, hub_tiles;
     int64_t chunks, long_chunks, sell_entries;
     int hub_degree, hub_tile;
+    int long_chunk, sort_window;
+    int tuned, tune_candidates;
 } cpaa_layout;
 
 cpaa_status cpaa_graph_layout(const cpaa_graph *g, cpaa_layout *out);
+
+/* Layout parameters for cpaa_graph_create_ex (no paper counterpart).  A field
+ * left at 0 takes its default: hub_degree min(4096, max(64, nnz / 4096)),
+ * hub_tile twice the hub degree within [512, 8192], long_chunk 32 (8 below
+ * 2^22 entries), sort_window 1024.  Limits: hub_degree >= 32; hub_tile a
+ * multiple of 4 in [256, 2^20]; sort_window a multiple of 32 up to 2^20;
+ * otherwise CPAA_EINVAL.  tune_precision is the number format the autotuner
+ * times rounds in (a cpaa_precision; 0 = CPAA_F64). */
+typedef struct {
+    int hub_degree, hub_tile, long_chunk, sort_window;
+    int tune_precision;
+} cpaa_layout_params;
+
+/* cpaa_graph_create with explicit layout parameters (params NULL: all
+ * defaults).  With CPAA_GRAPH_AUTOTUNE in flags the parameters are a starting
+ * point: the call builds candidate layouts around them (sort window, then hub
+ * threshold, hub tile and long-chunk threshold, a coordinate search of at most
+ * 13 layouts), times a few single-vector rounds of uniform p on each in
+ * tune_precision (CUDA events), and returns the graph with the fastest; the
+ * pick is cached for the rest of the process by device, size and degree
+ * histogram, so a second such call on a like graph builds one layout.
+ * Results of every layout agree to rounding (the sums run in another order).
+ * Other arguments, checks and errors as cpaa_graph_create. */
+cpaa_status cpaa_graph_create_ex(int64_t n, int64_t nnz, const int32_t *row_ptr,
+                                 const int32_t *col_idx, unsigned flags,
+                                 const cpaa_layout_params *params, cpaa_graph **out);
 
 /* Personalised PageRank of one vector (Sec. 2.1, Algorithm 1).
  *   p    FP64[n], p >= 0, |sum p - 1| <= 1e-9

@@ -15,7 +15,7 @@ __all__ = [
     "CPAA_OK", "CPAA_EINVAL", "CPAA_ENOMEM", "CPAA_ENOTCONV", "CPAA_ECUDA", "CPAA_ETIMEOUT",
     "CPAA_EBUSY", "CPAA_ECANCELLED", "CPAA_ENOTFOUND",
     "CPAA_F64", "CPAA_F32", "CPAA_BF16", "CPAA_DF64", "CPAA_GRAPH_DEVICE_INPUT", "CPAA_GRAPH_VALIDATE",
-    "CPAA_GRAPH_TRUSTED",
+    "CPAA_GRAPH_TRUSTED", "CPAA_GRAPH_AUTOTUNE", "CpaaLayoutParams", "cpaa_graph_create_ex",
     "CPAA_DEVICE_IO", "CPAA_TIME_ROUNDS", "CPAA_SERVER_FUSED", "CPAA_STOP_RIGOROUS", "CPAA_STOP_POSTERIORI",
     "cpaa_options_init", "cpaa_graph_create", "cpaa_graph_destroy", "cpaa_graph_info", "cpaa_graph_layout",
     "CpaaLayout", "cpaa_solve", "cpaa_solve_batch", "cpaa_rounds_needed", "cpaa_l1_bound",
@@ -28,7 +28,7 @@ __all__ = [
 CPAA_OK, CPAA_EINVAL, CPAA_ENOMEM, CPAA_ENOTCONV, CPAA_ECUDA = 0, 1, 2, 3, 4
 CPAA_ETIMEOUT, CPAA_EBUSY, CPAA_ECANCELLED, CPAA_ENOTFOUND = 5, 6, 7, 8
 CPAA_F64, CPAA_F32, CPAA_BF16, CPAA_DF64 = 0, 1, 2, 3
-CPAA_GRAPH_DEVICE_INPUT, CPAA_GRAPH_VALIDATE, CPAA_GRAPH_TRUSTED = 1, 2, 4
+CPAA_GRAPH_DEVICE_INPUT, CPAA_GRAPH_VALIDATE, CPAA_GRAPH_TRUSTED, CPAA_GRAPH_AUTOTUNE = 1, 2, 4, 8
 CPAA_DEVICE_IO = 1
 CPAA_NOALLOC_MAX_N = 1300000
 CPAA_SERVER_MAX_SEEDS = 64
@@ -41,8 +41,8 @@ library_path = os.path.join(HERE, "_build", "libcpaa.so")
 
 # Every function include/cpaa.h declares (the CPU test checks the exports).
 EXPORTED_SYMBOLS = [
-    "cpaa_options_init", "cpaa_graph_create", "cpaa_graph_destroy", "cpaa_graph_info", "cpaa_graph_layout",
-    "cpaa_solve", "cpaa_solve_batch", "cpaa_rounds_needed", "cpaa_l1_bound",
+    "cpaa_options_init", "cpaa_graph_create", "cpaa_graph_create_ex", "cpaa_graph_destroy", "cpaa_graph_info",
+    "cpaa_graph_layout", "cpaa_solve", "cpaa_solve_batch", "cpaa_rounds_needed", "cpaa_l1_bound",
     "cpaa_status_string", "cpaa_last_error", "cpaa_solve_fixed_noalloc", "cpaa_power_solve",
     "cpaa_server_create", "cpaa_server_add_graph", "cpaa_server_submit", "cpaa_server_wait",
     "cpaa_server_cancel", "cpaa_server_get_stats", "cpaa_server_destroy",
@@ -58,7 +58,14 @@ class CpaaError(RuntimeError):
 class CpaaLayout(ctypes.Structure):
     _fields_ = [("hub_rows", ctypes.c_int64), ("hub_entries", ctypes.c_int64), ("hub_tiles", ctypes.c_int64),
                 ("chunks", ctypes.c_int64), ("long_chunks", ctypes.c_int64), ("sell_entries", ctypes.c_int64),
-                ("hub_degree", ctypes.c_int), ("hub_tile", ctypes.c_int)]
+                ("hub_degree", ctypes.c_int), ("hub_tile", ctypes.c_int),
+                ("long_chunk", ctypes.c_int), ("sort_window", ctypes.c_int),
+                ("tuned", ctypes.c_int), ("tune_candidates", ctypes.c_int)]
+
+
+class CpaaLayoutParams(ctypes.Structure):
+    _fields_ = [("hub_degree", ctypes.c_int), ("hub_tile", ctypes.c_int), ("long_chunk", ctypes.c_int),
+                ("sort_window", ctypes.c_int), ("tune_precision", ctypes.c_int)]
 
 
 class CpaaOptions(ctypes.Structure):
@@ -107,6 +114,9 @@ def lib():
     L.cpaa_options_init.argtypes = [ctypes.POINTER(CpaaOptions)]
     L.cpaa_graph_create.restype = cint
     L.cpaa_graph_create.argtypes = [i64, i64, vp, vp, cuint, ctypes.POINTER(vp)]
+    L.cpaa_graph_create_ex.restype = cint
+    L.cpaa_graph_create_ex.argtypes = [i64, i64, vp, vp, cuint, ctypes.POINTER(CpaaLayoutParams),
+                                       ctypes.POINTER(vp)]
     L.cpaa_graph_destroy.restype = cint
     L.cpaa_graph_destroy.argtypes = [vp]
     L.cpaa_graph_info.restype = cint
@@ -195,6 +205,20 @@ def cpaa_graph_create(n, nnz, row_ptr, col_idx, flags=0):
         flags |= CPAA_GRAPH_DEVICE_INPUT
     _check(lib().cpaa_graph_create(int(n), int(nnz), _addr(row_ptr), _addr(col_idx), int(flags),
                                    ctypes.byref(h)))
+    return h.value
+
+
+def cpaa_graph_create_ex(n, nnz, row_ptr, col_idx, flags=0, params=None):
+    """cpaa_graph_create with layout parameters: a dict of CpaaLayoutParams
+    fields (missing ones 0, i.e. default) or None."""
+    h = ctypes.c_void_p()
+    if _is_device(row_ptr):
+        flags |= CPAA_GRAPH_DEVICE_INPUT
+    lp = None
+    if params is not None:
+        lp = CpaaLayoutParams(**{k: int(v) for k, v in params.items()})
+    _check(lib().cpaa_graph_create_ex(int(n), int(nnz), _addr(row_ptr), _addr(col_idx), int(flags),
+                                      ctypes.byref(lp) if lp is not None else None, ctypes.byref(h)))
     return h.value
 
 
@@ -405,14 +429,18 @@ def cpaa_last_error():
 class Graph:
     """Owning wrapper of a cpaa_graph handle."""
 
-    def __init__(self, row_ptr, col_idx, n=None, validate=True):
+    def __init__(self, row_ptr, col_idx, n=None, validate=True, layout=None, autotune=False):
         """validate=False passes CPAA_GRAPH_TRUSTED (no row-order or symmetry
-        check; the column range is checked either way)."""
+        check; the column range is checked either way); layout is a dict of
+        cpaa_layout_params fields; autotune passes CPAA_GRAPH_AUTOTUNE."""
         n = int(n if n is not None else len(row_ptr) - 1)
         nnz = int(col_idx.numel() if hasattr(col_idx, "numel") else len(col_idx))
         self.n, self.nnz = n, nnz
-        self.handle = cpaa_graph_create(n, nnz, row_ptr, col_idx,
-                                        0 if validate else CPAA_GRAPH_TRUSTED)
+        flags = (0 if validate else CPAA_GRAPH_TRUSTED) | (CPAA_GRAPH_AUTOTUNE if autotune else 0)
+        if layout is None and not autotune:
+            self.handle = cpaa_graph_create(n, nnz, row_ptr, col_idx, flags)
+        else:
+            self.handle = cpaa_graph_create_ex(n, nnz, row_ptr, col_idx, flags, layout)
 
     def info(self):
         return cpaa_graph_info(self.handle)

@@ -8,6 +8,7 @@
 // vertex order.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <thread>
 
@@ -157,7 +158,7 @@ static void release(cpaa_graph *g) {
 }
 
 // Host side of the relabelling: hub rows by decreasing degree, then windows
-// of kSortWindow rows sorted by decreasing degree (stable).
+// of lp.sort_window rows sorted by decreasing degree (stable).
 struct HostLayout {
     std::vector<int32_t> perm;
     int n_hub = 0;
@@ -176,7 +177,43 @@ static int hub_degree(int64_t nnz) {
 
 static int hub_tile_entries(int hub_deg) { return std::min(kMaxHubTile, std::max(kMinHubTile, 2 * hub_deg)); }
 
-static void host_layout(const int32_t *rp, int64_t n, int hub_deg, int tile, HostLayout &L) {
+// The default layout of a graph with nnz entries.
+static LayoutParams default_layout(int64_t nnz) {
+    LayoutParams lp;
+    lp.hub_degree = hub_degree(nnz);
+    lp.hub_tile = hub_tile_entries(lp.hub_degree);
+    lp.long_chunk = nnz < (int64_t(1) << 22) ? kSmallLongChunk : kLongChunk;
+    lp.sort_window = kSortWindow;
+    return lp;
+}
+
+// Caller's parameters with every 0 replaced by its default; out-of-range values are EINVAL.
+static cpaa_status resolve_layout(const cpaa_layout_params *in, int64_t nnz, LayoutParams *out) {
+    LayoutParams lp = default_layout(nnz);
+    if (in) {
+        if (in->hub_degree < 0 || (in->hub_degree > 0 && in->hub_degree < 32))
+            return fail(CPAA_EINVAL, "layout hub_degree must be 0 (default) or >= 32");
+        if (in->hub_tile < 0 || (in->hub_tile > 0 && (in->hub_tile < 256 || in->hub_tile > (1 << 20) ||
+                                                     in->hub_tile % 4 != 0)))
+            return fail(CPAA_EINVAL, "layout hub_tile must be 0 (default) or a multiple of 4 in [256, 2^20]");
+        if (in->long_chunk < 0) return fail(CPAA_EINVAL, "layout long_chunk must be >= 0");
+        if (in->sort_window < 0 ||
+            (in->sort_window > 0 && (in->sort_window % kChunkRows != 0 || in->sort_window > (1 << 20))))
+            return fail(CPAA_EINVAL, "layout sort_window must be 0 (default) or a multiple of 32 up to 2^20");
+        if (in->hub_degree > 0) {
+            lp.hub_degree = in->hub_degree;
+            lp.hub_tile = hub_tile_entries(lp.hub_degree);
+        }
+        if (in->hub_tile > 0) lp.hub_tile = in->hub_tile;
+        if (in->long_chunk > 0) lp.long_chunk = in->long_chunk;
+        if (in->sort_window > 0) lp.sort_window = in->sort_window;
+    }
+    *out = lp;
+    return CPAA_OK;
+}
+
+static void host_layout(const int32_t *rp, int64_t n, const LayoutParams &lp, HostLayout &L) {
+    const int hub_deg = lp.hub_degree, tile = lp.hub_tile, window = lp.sort_window;
     auto deg = [&](int32_t u) { return rp[u + 1] - rp[u]; };
     // heavy rows (degree at least kHeavyFactor times the mean, and at least kHeavyMin) follow the
     // hubs as one block sorted by degree: in an undirected graph a vertex is
@@ -197,14 +234,14 @@ static void host_layout(const int32_t *rp, int64_t n, int hub_deg, int tile, Hos
     // (its rows are the longest of any window they share with light rows)
     rest.insert(rest.begin(), heavy_rows.begin(), heavy_rows.end());
     const int64_t nrest = (int64_t)rest.size();
-    const int64_t nwin = (nrest + kSortWindow - 1) / kSortWindow;
+    const int64_t nwin = (nrest + window - 1) / window;
     const int nth = (int)std::max<int64_t>(1, std::min<int64_t>(16, nwin / 64));
     std::vector<std::thread> th;
     for (int t = 0; t < nth; ++t)
         th.emplace_back([&, t]() {
             for (int64_t w = t; w < nwin; w += nth) {
-                auto b = rest.begin() + w * kSortWindow;
-                auto e = rest.begin() + std::min<int64_t>(nrest, (w + 1) * kSortWindow);
+                auto b = rest.begin() + w * window;
+                auto e = rest.begin() + std::min<int64_t>(nrest, (w + 1) * window);
                 std::stable_sort(b, e, [&](int32_t a, int32_t c) { return deg(a) > deg(c); });
             }
         });
@@ -249,36 +286,11 @@ static void host_layout(const int32_t *rp, int64_t n, int hub_deg, int tile, Hos
     }
 }
 
-}  // namespace cpaa
-
-using namespace cpaa;
-
-extern "C" cpaa_status cpaa_graph_create(int64_t n, int64_t nnz, const int32_t *row_ptr,
-                                         const int32_t *col_idx, unsigned flags,
-                                         cpaa_graph **out) {
-    clear_error();
-    if (!out) return fail(CPAA_EINVAL, "out is NULL");
-    *out = nullptr;
-    if (n < 1 || n >= (int64_t(1) << 31) - 1) return fail(CPAA_EINVAL, "n out of range [1, 2^31 - 1)");
-    if (nnz < 1 || nnz >= (int64_t(1) << 31)) return fail(CPAA_EINVAL, "nnz out of range [1, 2^31)");
-    if (!row_ptr || !col_idx) return fail(CPAA_EINVAL, "row_ptr / col_idx is NULL");
+// The graph for a checked host copy hrp of row_ptr and resolved parameters.
+static cpaa_status build_graph(int64_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
+                               unsigned flags, const std::vector<int32_t> &hrp, const LayoutParams &lp,
+                               cpaa_graph **out) {
     const bool dev_in = (flags & CPAA_GRAPH_DEVICE_INPUT) != 0;
-
-    // Host copy of row_ptr: the layout is planned on the host.
-    std::vector<int32_t> hrp((size_t)n + 1);
-    if (dev_in) {
-        CPAA_CUDA(cudaMemcpy(hrp.data(), row_ptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost));
-    } else {
-        std::memcpy(hrp.data(), row_ptr, sizeof(int32_t) * (n + 1));
-    }
-    if (hrp[0] != 0) return fail(CPAA_EINVAL, "row_ptr[0] != 0");
-    if ((int64_t)hrp[n] != nnz) return fail(CPAA_EINVAL, "row_ptr[n] != nnz");
-    for (int64_t u = 0; u < n; ++u) {
-        if (hrp[u + 1] < hrp[u]) return fail(CPAA_EINVAL, "row_ptr decreases at row " + std::to_string(u));
-        if (hrp[u + 1] == hrp[u])
-            return fail(CPAA_EINVAL, "vertex " + std::to_string(u) + " has degree 0 (Sec. 2.1 needs d_i > 0)");
-    }
-
     cpaa_graph *g = new cpaa_graph();
     g->n = n;
     g->nnz = nnz;
@@ -325,16 +337,17 @@ extern "C" cpaa_status cpaa_graph_create(int64_t n, int64_t nnz, const int32_t *
         }
 
         HostLayout L;
-        g->hub_degree = hub_degree(nnz);
-        g->hub_tile = hub_tile_entries(g->hub_degree);
-        host_layout(hrp.data(), n, g->hub_degree, g->hub_tile, L);
+        g->lp = lp;
+        g->hub_degree = lp.hub_degree;
+        g->hub_tile = lp.hub_tile;
+        host_layout(hrp.data(), n, lp, L);
         g->n_hub = L.n_hub;
         g->hub_nnz = L.hub_row_ptr.back();
         g->num_hub_tiles = (int)L.hub_tiles.size();
         g->num_chunks = (int)L.chunk_off.size();
         g->num_long_chunks = 0;
         while (g->num_long_chunks < g->num_chunks &&
-               L.chunk_len[L.chunk_order[g->num_long_chunks]] > (nnz < (int64_t(1) << 22) ? kSmallLongChunk : kLongChunk))
+               L.chunk_len[L.chunk_order[g->num_long_chunks]] > lp.long_chunk)
             ++g->num_long_chunks;
         g->sell_entries = L.sell_entries;
 
@@ -432,6 +445,237 @@ fail_out:
 #undef CK
 }
 
+// ---------------------------------------------------------------------------
+// Autotuning of the layout parameters (CPAA_GRAPH_AUTOTUNE).
+//
+// Coordinate search from the starting parameters: the sort window, then the
+// hub threshold, the hub tile and the long-chunk threshold, each over a few
+// candidates around the current best; every candidate layout is built and
+// kTuneLayoutRounds single-vector rounds of uniform p are timed on it (CUDA
+// events, the second of two runs).  Candidates that give the same layout as
+// one already timed (same hub rows, hub tiles, long chunks and window) are
+// not timed again.  The pick is cached for the process, keyed by device,
+// size, a log2 histogram of the degrees, the timing precision and the start.
+constexpr int kTuneLayoutRounds = 4;
+
+struct TuneKey {
+    int device, precision;
+    int64_t n, nnz;
+    std::vector<int64_t> hist;
+    LayoutParams start;
+    bool operator==(const TuneKey &o) const {
+        return device == o.device && precision == o.precision && n == o.n && nnz == o.nnz && hist == o.hist &&
+               start.hub_degree == o.start.hub_degree && start.hub_tile == o.start.hub_tile &&
+               start.long_chunk == o.start.long_chunk && start.sort_window == o.start.sort_window;
+    }
+};
+static std::mutex g_tune_mu;
+static std::vector<std::pair<TuneKey, std::pair<LayoutParams, int>>> g_tune_cache;
+
+// Device time per round of kTuneLayoutRounds rounds on graph g (uniform p).
+static cpaa_status time_layout(cpaa_graph *g, int prec, const double *d_p, double *d_pi, float *ms_per_round) {
+    cpaa_status s = ensure_workspace(g, prec, 1, kTuneLayoutRounds);
+    if (s != CPAA_OK) return s;
+    TileJob job;
+    job.width = 1;
+    job.precision = prec;
+    job.p[0] = d_p;
+    job.pi[0] = d_pi;
+    job.c[0] = 0.85;
+    std::vector<double> ck;
+    cheb_coeffs(0.85, 0, ck);
+    job.c0half[0] = ck[0] / 2.0;
+    job.rounds[0] = kTuneLayoutRounds;
+    float ms = 0.0f;
+    for (int rep = 0; rep < 2; ++rep) {  // the first run also captures the round graph
+        if ((s = run_tile(g, job, nullptr, false, true)) != CPAA_OK) return s;
+        if ((s = tile_rounds_ms(g, &ms)) != CPAA_OK) return s;
+    }
+    CPAA_CUDA(cudaDeviceSynchronize());
+    *ms_per_round = ms / kTuneLayoutRounds;
+    return CPAA_OK;
+}
+
+static cpaa_status autotune_graph(int64_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
+                                  unsigned flags, const std::vector<int32_t> &hrp, const LayoutParams &start,
+                                  int prec, cpaa_graph **out) {
+    TuneKey key;
+    cudaGetDevice(&key.device);
+    key.precision = prec;
+    key.n = n;
+    key.nnz = nnz;
+    key.hist.assign(32, 0);
+    int maxdeg = 0;
+    for (int64_t u = 0; u < n; ++u) {
+        const int d = hrp[u + 1] - hrp[u];
+        maxdeg = std::max(maxdeg, d);
+        int b = 0;
+        while ((2 << b) <= d && b < 31) ++b;
+        ++key.hist[b];
+    }
+    key.start = start;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (auto &e : g_tune_cache)
+            if (e.first == key) {
+                cpaa_status s = build_graph(n, nnz, row_ptr, col_idx, flags, hrp, e.second.first, out);
+                if (s == CPAA_OK) {
+                    (*out)->tuned = 1;
+                    (*out)->tune_candidates = e.second.second;
+                }
+                return s;
+            }
+    }
+    // uniform p and a scratch output for the timed rounds
+    double *d_p = nullptr, *d_pi = nullptr;
+    CPAA_CUDA(cudaMalloc(&d_p, sizeof(double) * n));
+    if (cudaMalloc(&d_pi, sizeof(double) * n) != cudaSuccess) {
+        cudaFree(d_p);
+        return fail(CPAA_ENOMEM, "autotune: no room for its test vectors");
+    }
+    {
+        std::vector<double> hp((size_t)n, 1.0 / (double)n);
+        cudaMemcpy(d_p, hp.data(), sizeof(double) * n, cudaMemcpyHostToDevice);
+    }
+    struct Timed {
+        LayoutParams lp;
+        int64_t sig[4];
+        float ms;
+    };
+    std::vector<Timed> timed;
+    cpaa_graph *best = nullptr;
+    float best_ms = 0.0f;
+    LayoutParams best_lp = start;
+    cpaa_status st = CPAA_OK;
+    unsigned cand_flags = flags | CPAA_GRAPH_TRUSTED;  // checked once, by the first build
+    auto eval = [&](const LayoutParams &lp) -> cpaa_status {
+        cpaa_graph *g = nullptr;
+        cpaa_status s = build_graph(n, nnz, row_ptr, col_idx, timed.empty() && !best ? flags : cand_flags, hrp,
+                                    lp, &g);
+        if (s != CPAA_OK) return s;
+        const int64_t sig[4] = {g->n_hub, g->num_hub_tiles, g->num_long_chunks, lp.sort_window};
+        float ms = -1.0f;
+        for (auto &t : timed)
+            if (std::equal(sig, sig + 4, t.sig)) ms = t.ms;
+        const bool fresh = ms < 0.0f;
+        if (fresh) {
+            s = time_layout(g, prec, d_p, d_pi, &ms);
+            if (s != CPAA_OK) {
+                release(g);
+                return s;
+            }
+            Timed t;
+            t.lp = lp;
+            std::copy(sig, sig + 4, t.sig);
+            t.ms = ms;
+            timed.push_back(t);
+        }
+        if (!best || ms < best_ms) {
+            if (best) release(best);
+            best = g;
+            best_ms = ms;
+            best_lp = lp;
+        } else {
+            release(g);
+        }
+        return CPAA_OK;
+    };
+    st = eval(start);
+    // the sort window
+    for (int w : {64, 256, 1024, 4096})
+        if (st == CPAA_OK && w != best_lp.sort_window) {
+            LayoutParams lp = best_lp;
+            lp.sort_window = w;
+            st = eval(lp);
+        }
+    // the hub threshold (only thresholds some row exceeds make hub rows)
+    const LayoutParams after_window = best_lp;
+    for (int f : {-2, -1, 1})
+        if (st == CPAA_OK) {
+            LayoutParams lp = after_window;
+            lp.hub_degree = f < 0 ? after_window.hub_degree >> (-f) : after_window.hub_degree << f;
+            if (lp.hub_degree < 32 || lp.hub_degree >= maxdeg) continue;
+            lp.hub_tile = std::min(16384, std::max(512, 2 * lp.hub_degree));
+            st = eval(lp);
+        }
+    // the hub tile (only with hub rows)
+    const LayoutParams after_hub = best_lp;
+    if (best && best->n_hub > 0)
+        for (int f : {-1, 1})
+            if (st == CPAA_OK) {
+                LayoutParams lp = after_hub;
+                lp.hub_tile = f < 0 ? after_hub.hub_tile / 2 : after_hub.hub_tile * 2;
+                if (lp.hub_tile < 256 || lp.hub_tile > 32768) continue;
+                st = eval(lp);
+            }
+    // the long-chunk threshold
+    const LayoutParams after_tile = best_lp;
+    for (int lc : {8, 16, 32, 64})
+        if (st == CPAA_OK && lc != after_tile.long_chunk && lc < std::min(maxdeg, after_tile.hub_degree)) {
+            LayoutParams lp = after_tile;
+            lp.long_chunk = lc;
+            st = eval(lp);
+        }
+    cudaFree(d_p);
+    cudaFree(d_pi);
+    if (st != CPAA_OK) {
+        if (best) release(best);
+        return st;
+    }
+    best->tuned = 1;
+    best->tune_candidates = (int)timed.size();
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache.push_back({key, {best_lp, (int)timed.size()}});
+    }
+    *out = best;
+    return CPAA_OK;
+}
+
+}  // namespace cpaa
+
+using namespace cpaa;
+
+extern "C" cpaa_status cpaa_graph_create_ex(int64_t n, int64_t nnz, const int32_t *row_ptr,
+                                            const int32_t *col_idx, unsigned flags,
+                                            const cpaa_layout_params *params, cpaa_graph **out) {
+    clear_error();
+    if (!out) return fail(CPAA_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n >= (int64_t(1) << 31) - 1) return fail(CPAA_EINVAL, "n out of range [1, 2^31 - 1)");
+    if (nnz < 1 || nnz >= (int64_t(1) << 31)) return fail(CPAA_EINVAL, "nnz out of range [1, 2^31)");
+    if (!row_ptr || !col_idx) return fail(CPAA_EINVAL, "row_ptr / col_idx is NULL");
+    const bool dev_in = (flags & CPAA_GRAPH_DEVICE_INPUT) != 0;
+    LayoutParams lp;
+    cpaa_status s = resolve_layout(params, nnz, &lp);
+    if (s != CPAA_OK) return s;
+    int tune_prec = params ? params->tune_precision : CPAA_F64;
+    if (tune_prec != CPAA_F64 && tune_prec != CPAA_F32 && tune_prec != CPAA_BF16 && tune_prec != CPAA_DF64)
+        return fail(CPAA_EINVAL, "layout tune_precision is not a cpaa_precision");
+
+    // Host copy of row_ptr: the layout is planned on the host.
+    std::vector<int32_t> hrp((size_t)n + 1);
+    if (dev_in) {
+        CPAA_CUDA(cudaMemcpy(hrp.data(), row_ptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost));
+    } else {
+        std::memcpy(hrp.data(), row_ptr, sizeof(int32_t) * (n + 1));
+    }
+    if (hrp[0] != 0) return fail(CPAA_EINVAL, "row_ptr[0] != 0");
+    if ((int64_t)hrp[n] != nnz) return fail(CPAA_EINVAL, "row_ptr[n] != nnz");
+    for (int64_t u = 0; u < n; ++u) {
+        if (hrp[u + 1] < hrp[u]) return fail(CPAA_EINVAL, "row_ptr decreases at row " + std::to_string(u));
+        if (hrp[u + 1] == hrp[u])
+            return fail(CPAA_EINVAL, "vertex " + std::to_string(u) + " has degree 0 (Sec. 2.1 needs d_i > 0)");
+    }
+    if (flags & CPAA_GRAPH_AUTOTUNE) return autotune_graph(n, nnz, row_ptr, col_idx, flags, hrp, lp, tune_prec, out);
+    return build_graph(n, nnz, row_ptr, col_idx, flags, hrp, lp, out);
+}
+
+extern "C" cpaa_status cpaa_graph_create(int64_t n, int64_t nnz, const int32_t *row_ptr,
+                                         const int32_t *col_idx, unsigned flags, cpaa_graph **out) {
+    return cpaa_graph_create_ex(n, nnz, row_ptr, col_idx, flags, nullptr, out);
+}
+
 extern "C" cpaa_status cpaa_graph_destroy(cpaa_graph *g) {
     clear_error();
     if (!g) return CPAA_OK;
@@ -451,6 +695,10 @@ extern "C" cpaa_status cpaa_graph_layout(const cpaa_graph *g, cpaa_layout *out) 
     out->sell_entries = g->sell_entries;
     out->hub_degree = g->hub_degree;
     out->hub_tile = g->hub_tile;
+    out->long_chunk = g->lp.long_chunk;
+    out->sort_window = g->lp.sort_window;
+    out->tuned = g->tuned;
+    out->tune_candidates = g->tune_candidates;
     return CPAA_OK;
 }
 

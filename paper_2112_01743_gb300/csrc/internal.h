@@ -58,6 +58,8 @@ namespace cpaa {
 // entries and long-chunk thresholds of 32 to 128, and on the 10^4-vertex one
 // (FP64), where graphs below 2^22 entries take long chunks above 8 entries
 // and hub tiles down to 512 entries: there a round is a chain of latencies.
+// Every threshold and the sort window are per-graph parameters
+// (cpaa_layout_params); CPAA_GRAPH_AUTOTUNE picks them by timing rounds.
 // ---------------------------------------------------------------------------
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
@@ -106,6 +108,17 @@ constexpr int kDefaultMaxRounds = 2000;
 
 constexpr int kPrepBlocks = 1024;  // CTAs of the fixed-order reductions
 constexpr int kMaxWidth = 16;      // widest tile of vectors a round kernel takes
+
+// Layout parameters of a graph (cpaa_layout_params with every default
+// resolved): hub rows have degree above hub_degree and are cut into tiles of
+// hub_tile entries; SELL chunks whose longest row exceeds long_chunk get a
+// CTA; rows are sorted by degree within windows of sort_window rows.
+struct LayoutParams {
+    int hub_degree = 0;
+    int hub_tile = 0;
+    int long_chunk = 0;
+    int sort_window = 0;
+};
 
 // A double-float value: hi + lo, |lo| <= ulp(hi) / 2 (CPAA_DF64).  The
 // arithmetic is in device_common.cuh.
@@ -207,7 +220,10 @@ struct cpaa_graph {
     int4 *chunk_desc = nullptr;      // [num_chunks] in chunk_order: {chunk, offset / 128, length, longest row}
     int hub_degree = cpaa::kHubDegree;  // rows above this degree are hub rows
     int hub_tile = cpaa::kMaxHubTile;   // entries of a hub tile
-    int num_long_chunks = 0;         // leading chunk_order entries longer than kLongChunk
+    int num_long_chunks = 0;         // leading chunk_order entries longer than lp.long_chunk
+    cpaa::LayoutParams lp;           // the layout's parameters (hub_degree, hub_tile as above)
+    int tuned = 0;                   // 1: lp picked by timing candidates (CPAA_GRAPH_AUTOTUNE)
+    int tune_candidates = 0;         // layouts timed to pick it
     // per-vertex, new order
     double *deg64 = nullptr;         // d_u
     double *inv_deg64 = nullptr;     // 1 / d_u

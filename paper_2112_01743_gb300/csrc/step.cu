@@ -78,7 +78,6 @@ struct StepParams {
     unsigned reduce;
     unsigned first;  // columns in their first round (y_1 = D^-1 P y_0... scaled: s / d)
     int power;       // 1: power-method round y' = c s / d + q, ck[b] = c, q held in rho
-    int hot;         // rows [0, hot) of the iterate: the L2 evict_last ones (CPAA_GATHER_HINT)
 };
 
 // W consecutive values of one row, with the widest loads the row size allows.
@@ -160,89 +159,13 @@ __device__ __forceinline__ df ld_cg(const df *p) {
     return df(v.x, v.y);
 }
 
-// L2 eviction priority of the iterate gathers and of the new iterate's
-// stores (compile-time tuning knobs; the defaults are plain loads and stores).
-//   CPAA_GATHER_HINT 0: ld.global.nc; 1: rows below StepParams::hot with an
-//                    L2 evict_last policy, the others plain; 2: as 1, the
-//                    others evict_first
-//   CPAA_YSTORE      0: plain stores; 1: streaming (evict-first) stores;
-//                    2: streaming stores for rows at or above hot only
-//   CPAA_HOT_BYTES   bytes of the leading (hottest) rows given evict_last
-#ifndef CPAA_GATHER_HINT
-#define CPAA_GATHER_HINT 0
-#endif
-#ifndef CPAA_YSTORE
-#define CPAA_YSTORE 0
-#endif
-#ifndef CPAA_HOT_BYTES
-#define CPAA_HOT_BYTES (64ll << 20)
-#endif
-__device__ __forceinline__ uint64_t policy_evict_last() {
-    uint64_t pol;
-    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-__device__ __forceinline__ uint64_t policy_evict_first() {
-    uint64_t pol;
-    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-__device__ __forceinline__ void ld_hint(const void *a, uint64_t pol, unsigned short &v) {
-    asm("ld.global.nc.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(v) : "l"(a), "l"(pol));
-}
-__device__ __forceinline__ void ld_hint(const void *a, uint64_t pol, unsigned &v) {
-    asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
-}
-__device__ __forceinline__ void ld_hint(const void *a, uint64_t pol, uint2 &v) {
-    asm("ld.global.nc.L2::cache_hint.v2.b32 {%0, %1}, [%2], %3;" : "=r"(v.x), "=r"(v.y) : "l"(a), "l"(pol));
-}
-__device__ __forceinline__ void ld_hint(const void *a, uint64_t pol, uint4 &v) {
-    asm("ld.global.nc.L2::cache_hint.v4.b32 {%0, %1, %2, %3}, [%4], %5;"
-        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-        : "l"(a), "l"(pol));
-}
-template <class T, int W>
-__device__ __forceinline__ void load_row_hint(const T *p, T (&v)[W], uint64_t pol) {
-    constexpr int B = W * (int)sizeof(T);
-    if constexpr (B % 16 == 0) {
-        uint4 raw[B / 16];
-#pragma unroll
-        for (int i = 0; i < B / 16; ++i) ld_hint(reinterpret_cast<const uint4 *>(p) + i, pol, raw[i]);
-        memcpy(v, raw, B);
-    } else if constexpr (B % 8 == 0) {
-        uint2 raw[B / 8];
-#pragma unroll
-        for (int i = 0; i < B / 8; ++i) ld_hint(reinterpret_cast<const uint2 *>(p) + i, pol, raw[i]);
-        memcpy(v, raw, B);
-    } else if constexpr (B % 4 == 0) {
-        unsigned raw[B / 4];
-#pragma unroll
-        for (int i = 0; i < B / 4; ++i) ld_hint(reinterpret_cast<const unsigned *>(p) + i, pol, raw[i]);
-        memcpy(v, raw, B);
-    } else {
-        unsigned short raw;
-        ld_hint(p, pol, raw);
-        memcpy(v, &raw, B);
-    }
-}
-
 // Gathered neighbour row j: W values in arithmetic precision.
 template <int P, int W>
 __device__ __forceinline__ void gather_row(const typename Prec<P>::S *y, int j,
-                                           typename Prec<P>::A (&x)[W], int hot = 0) {
+                                           typename Prec<P>::A (&x)[W]) {
     using S = typename Prec<P>::S;
     S v[W];
-#if CPAA_GATHER_HINT
-    if (j < hot) load_row_hint<S, W>(y + (int64_t)j * W, v, policy_evict_last());
-#if CPAA_GATHER_HINT == 2
-    else load_row_hint<S, W>(y + (int64_t)j * W, v, policy_evict_first());
-#else
-    else load_row<S, W>(y + (int64_t)j * W, v, false);
-#endif
-#else
-    (void)hot;
     load_row<S, W>(y + (int64_t)j * W, v, false);
-#endif
 #pragma unroll
     for (int b = 0; b < W; ++b) x[b] = to_acc(v[b]);
 }
@@ -278,20 +201,6 @@ __device__ __forceinline__ void load_ops(const StepParams<P, W> &p, int64_t r, R
     }
 }
 
-// Whether row r's new iterate is stored with the streaming (evict-first) hint.
-template <int P, int W>
-__device__ __forceinline__ bool ystore_stream(const StepParams<P, W> &p, int64_t r) {
-#if CPAA_YSTORE == 1
-    return true;
-#elif CPAA_YSTORE == 2
-    return r >= p.hot;
-#else
-    (void)p;
-    (void)r;
-    return false;
-#endif
-}
-
 // Row epilogue: new iterates and accumulation; yv receives the new iterates
 // (as stored) for the round's sums.
 template <int P, int W>
@@ -311,7 +220,7 @@ __device__ __forceinline__ void row_finish(const StepParams<P, W> &p, int64_t r,
             store_y(&ys[b], y);
             yv[b] = y;
         }
-        store_row<S, W>(p.y_io + r * W, ys, ystore_stream(p, r));
+        store_row<S, W>(p.y_io + r * W, ys, false);
         return;
     }
 #pragma unroll
@@ -321,7 +230,7 @@ __device__ __forceinline__ void row_finish(const StepParams<P, W> &p, int64_t r,
         if (active >> b & 1u) accumulate<P>(o.rr[b], o.cmp[b], p.ck[b], y);
         yv[b] = y;
     }
-    store_row<S, W>(p.y_io + r * W, ys, ystore_stream(p, r));
+    store_row<S, W>(p.y_io + r * W, ys, false);
     store_row<R, W>(p.rho + r * W, o.rr, true);
     if constexpr (Prec<P>::kKahan) store_row<R, W>(p.comp + r * W, o.cmp, true);
 }
@@ -406,10 +315,10 @@ __device__ __forceinline__ void hub_tile(const StepParams<P, W> &p, int4 t, unsi
         const int4 q = ld_stream4(p.hub_col + e);
         A x0[W], x1[W], x2[W], x3[W];
         // entries outside [c0, c1) gather the sentinel row n, which holds zeros
-        gather_row<P, W>(p.y_src, (e >= c0 && e < c1) ? q.x : (int)p.n, x0, p.hot);
-        gather_row<P, W>(p.y_src, (e + 1 >= c0 && e + 1 < c1) ? q.y : (int)p.n, x1, p.hot);
-        gather_row<P, W>(p.y_src, (e + 2 >= c0 && e + 2 < c1) ? q.z : (int)p.n, x2, p.hot);
-        gather_row<P, W>(p.y_src, (e + 3 >= c0 && e + 3 < c1) ? q.w : (int)p.n, x3, p.hot);
+        gather_row<P, W>(p.y_src, (e >= c0 && e < c1) ? q.x : (int)p.n, x0);
+        gather_row<P, W>(p.y_src, (e + 1 >= c0 && e + 1 < c1) ? q.y : (int)p.n, x1);
+        gather_row<P, W>(p.y_src, (e + 2 >= c0 && e + 2 < c1) ? q.z : (int)p.n, x2);
+        gather_row<P, W>(p.y_src, (e + 3 >= c0 && e + 3 < c1) ? q.w : (int)p.n, x3);
 #pragma unroll
         for (int b = 0; b < W; ++b) acc[b] += ((x0[b] + x1[b]) + (x2[b] + x3[b]));
     }
@@ -474,10 +383,10 @@ __device__ __forceinline__ void sum_groups(const StepParams<P, W> &p, const int3
     A x[U][4][W];
 #pragma unroll
     for (int k = 0; k < U; ++k) {
-        gather_row<P, W>(p.y_src, jj[k].x, x[k][0], p.hot);
-        gather_row<P, W>(p.y_src, jj[k].y, x[k][1], p.hot);
-        gather_row<P, W>(p.y_src, jj[k].z, x[k][2], p.hot);
-        gather_row<P, W>(p.y_src, jj[k].w, x[k][3], p.hot);
+        gather_row<P, W>(p.y_src, jj[k].x, x[k][0]);
+        gather_row<P, W>(p.y_src, jj[k].y, x[k][1]);
+        gather_row<P, W>(p.y_src, jj[k].z, x[k][2]);
+        gather_row<P, W>(p.y_src, jj[k].w, x[k][3]);
     }
 #pragma unroll
     for (int k = 0; k < U; ++k)
@@ -505,26 +414,24 @@ __device__ __forceinline__ void chunk_sum(const StepParams<P, W> &p, const int32
     constexpr int U = Unroll<W>::value;  // groups of four entries in flight per lane
     constexpr int G = kChunkRows * kSellVec;
     if (tail) {
+        // all four loads at once (slots past the longest row hold the zero
+        // sentinel), so their latencies overlap; only the additions depend on
+        // the tail's length
         const int4 j = ld_stream4(col + (int64_t)q1 * G);
-        gather_row<P, W>(p.y_src, j.x, acc, p.hot);
-        if (tail > 1) {
-            A x[W];
-            gather_row<P, W>(p.y_src, j.y, x, p.hot);
+        A x1[W], x2[W], x3[W];
+        gather_row<P, W>(p.y_src, j.x, acc);
+        gather_row<P, W>(p.y_src, j.y, x1);
+        gather_row<P, W>(p.y_src, j.z, x2);
+        gather_row<P, W>(p.y_src, j.w, x3);
+        if (tail > 1)
 #pragma unroll
-            for (int b = 0; b < W; ++b) acc[b] += x[b];
-        }
-        if (tail > 2) {
-            A x[W];
-            gather_row<P, W>(p.y_src, j.z, x, p.hot);
+            for (int b = 0; b < W; ++b) acc[b] += x1[b];
+        if (tail > 2)
 #pragma unroll
-            for (int b = 0; b < W; ++b) acc[b] += x[b];
-        }
-        if (tail > 3) {
-            A x[W];
-            gather_row<P, W>(p.y_src, j.w, x, p.hot);
+            for (int b = 0; b < W; ++b) acc[b] += x2[b];
+        if (tail > 3)
 #pragma unroll
-            for (int b = 0; b < W; ++b) acc[b] += x[b];
-        }
+            for (int b = 0; b < W; ++b) acc[b] += x3[b];
     } else {
 #pragma unroll
         for (int b = 0; b < W; ++b) acc[b] = A(0);
@@ -538,7 +445,7 @@ __device__ __forceinline__ void chunk_sum(const StepParams<P, W> &p, const int32
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 A x[W];
-                gather_row<P, W>(p.y_src, jj[e], x, p.hot);
+                gather_row<P, W>(p.y_src, jj[e], x);
 #pragma unroll
                 for (int b = 0; b < W; ++b) acc[b] += x[b];
             }
@@ -832,7 +739,6 @@ static void fill_params(const StepLaunch &s, StepParams<P, W> &p) {
     p.reduce = s.reduce;
     p.first = s.first;
     p.power = s.power;
-    p.hot = (int)std::min<int64_t>(g->n + 1, CPAA_HOT_BYTES / ((int64_t)W * (int64_t)sizeof(S)));
 }
 
 // The two fixed-order sum kernels of a round that takes sums.  The item

@@ -32,7 +32,8 @@ def test_header_constants_match_the_binding(L):
     """The flag and limit macros of include/cpaa.h have the binding's values."""
     src = open(os.path.join(ROOT, "include", "cpaa.h")).read()
     names = ("CPAA_GRAPH_DEVICE_INPUT", "CPAA_GRAPH_VALIDATE", "CPAA_GRAPH_TRUSTED", "CPAA_DEVICE_IO",
-             "CPAA_TIME_ROUNDS", "CPAA_SERVER_FUSED", "CPAA_NOALLOC_MAX_N", "CPAA_SERVER_MAX_SEEDS")
+             "CPAA_TIME_ROUNDS", "CPAA_SERVER_FUSED", "CPAA_NOALLOC_MAX_N", "CPAA_SERVER_MAX_SEEDS",
+             "CPAA_GRAPH_AUTOTUNE")
     for name in names:
         m = re.search(r"#define\s+%s\s+(\d+)u?\b" % name, src)
         assert m, name
@@ -93,7 +94,8 @@ def test_struct_layouts_match_the_header(L, tmp_path):
     if cc is None:
         pytest.skip("no host C compiler")
     structs = {"cpaa_options": L.CpaaOptions, "cpaa_info": L.CpaaInfo,
-               "cpaa_server_stats": L.CpaaServerStats, "cpaa_layout": L.CpaaLayout}
+               "cpaa_server_stats": L.CpaaServerStats, "cpaa_layout": L.CpaaLayout,
+               "cpaa_layout_params": L.CpaaLayoutParams}
     lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "cpaa.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (name, name))
@@ -177,6 +179,21 @@ def test_graph_create_rejects_bad_csr_before_any_device_work(L):
     for n, nnz, rp, cx, why in cases:
         with pytest.raises(L.CpaaError) as e:
             L.cpaa_graph_create(n, nnz, rp, cx)
+        assert e.value.status == L.CPAA_EINVAL, why
+        assert why in str(e.value), (why, str(e.value))
+
+
+def test_layout_params_checked_before_any_device_work(L):
+    """cpaa_graph_create_ex rejects out-of-range layout parameters (and an
+    unknown tuning precision) on the host, before its first CUDA call."""
+    rp, cx = np.asarray([0, 1, 2], dtype=np.int32), np.asarray([1, 0], dtype=np.int32)
+    bad = [({"hub_degree": 31}, "hub_degree"), ({"hub_degree": -1}, "hub_degree"),
+           ({"hub_tile": 100}, "hub_tile"), ({"hub_tile": 1026}, "hub_tile"), ({"hub_tile": 1 << 21}, "hub_tile"),
+           ({"long_chunk": -3}, "long_chunk"), ({"sort_window": 48}, "sort_window"),
+           ({"sort_window": 1 << 21}, "sort_window"), ({"tune_precision": 9}, "tune_precision")]
+    for params, why in bad:
+        with pytest.raises(L.CpaaError) as e:
+            L.cpaa_graph_create_ex(2, 2, rp, cx, 0, params)
         assert e.value.status == L.CPAA_EINVAL, why
         assert why in str(e.value), (why, str(e.value))
 
