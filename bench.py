@@ -368,9 +368,44 @@ def run_grid(pkg, args, stream):
                      / measured_peak_gbs()[0]}
     for name in ("f32", "bf16", "df64"):
         out[name]["l1_vs_f64"] = float((res[name] - res["f64"]).abs().sum().item())
+    out["frontier_one_seed_f64"] = one_seed_frontier(pkg, G, n, pkg.CPAA_F64, reps=10)
     G.close()
     return {"workload": "4096x4096 lattice, 20% of edges deleted (seed 0, spanning tree kept); "
                         "c=0.85, uniform p, tol 1e-6", "n": n, "nnz": nnz, **out}
+
+
+def one_seed_frontier(pkg, G, n, precision, reps=20, c=0.85, tol=1e-6):
+    """Mean device time of one-seed solves (seeds spread over the id range)
+    with and without CPAA_SPARSE_FRONTIER, and whether the results agree bit
+    for bit."""
+    import torch
+    seeds = np.linspace(0, n - 1, reps).astype(np.int64)
+    out = {}
+    res = {}
+    for fr in (False, True):
+        p = torch.zeros(n, dtype=torch.float64, device="cuda")
+        pi = torch.empty_like(p)
+        p[int(seeds[0])] = 1.0
+        G.solve(p, c, tol, pi, precision=precision, frontier=fr)  # warm-up (and graph capture)
+        torch.cuda.synchronize()
+        ms = []
+        last = None
+        for sd in seeds:
+            p.zero_()
+            p[int(sd)] = 1.0
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            info = G.solve(p, c, tol, pi, precision=precision, frontier=fr)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            last = info.rounds
+        res[fr] = pi.clone()
+        out["frontier" if fr else "plain"] = {"ms_per_solve_mean": float(np.mean(ms)),
+                                             "ms_per_solve_median": float(np.median(ms)), "rounds_last": last}
+    out["same_bits"] = bool(torch.equal(res[False], res[True]))
+    out["speedup"] = out["plain"]["ms_per_solve_mean"] / out["frontier"]["ms_per_solve_mean"]
+    return out
 
 
 def run_serving(pkg, args):
@@ -402,8 +437,8 @@ def run_serving(pkg, args):
             out.append((gi, seeds, float(rng.choice([0.5, 0.85, 0.95]))))
         return out
 
-    def run(queries, rate, stop_rule=pkg.CPAA_STOP_RIGOROUS, fused=False):
-        S = pkg.Server(64 << 30, stop_rule=stop_rule, fused=fused)
+    def run(queries, rate, stop_rule=pkg.CPAA_STOP_RIGOROUS, fused=False, frontier=False):
+        S = pkg.Server(64 << 30, stop_rule=stop_rule, fused=fused, frontier=frontier)
         ids = [S.add_graph(x, 16) for x in G]
         tickets = []
         lock = threading.Condition()
@@ -468,6 +503,17 @@ def run_serving(pkg, args):
                       "p50_ms": s["p50_us"] / 1e3, "p99_ms": s["p99_us"] / 1e3,
                       "mean_width": s["mean_width"], "relayouts": s["relayouts"],
                       "failed": s["failed"]})
+    # the sparse frontier (early rounds on the seeds' k-hop balls) at low load,
+    # where tiles often start from empty
+    frontier_sweep = []
+    for load in (0.3, 0.5):
+        count = max(1, args.serve_queries // 8)
+        q, s_ = run(make(count), load * sat_qps, frontier=True)
+        frontier_sweep.append({"load": load, "rate_qps": load * sat_qps, "queries": count, "achieved_qps": q,
+                               "p50_ms": s_["p50_us"] / 1e3, "p99_ms": s_["p99_us"] / 1e3,
+                               "mean_width": s_["mean_width"], "failed": s_["failed"]})
+    # one-seed solves on the 8M-vertex graph with and without the frontier
+    frontier_solve = one_seed_frontier(pkg, G[-1], sizes[-1], pkg.CPAA_F32)
     for x in G:
         x.close()
     return {"workload": "8 Chung-Lu graphs (n = 10k..8M, mean degree 16, gamma 2.1) resident; "
@@ -486,7 +532,8 @@ def run_serving(pkg, args):
             "fused_saturated_qps": fused_qps, "fused_saturated_p50_ms": fused_st["p50_us"] / 1e3,
             "fused_saturated_p99_ms": fused_st["p99_us"] / 1e3,
             "fused_saturated_effective_gteps": fused_st["effective_gteps"],
-            "poisson_sweep": sweep}
+            "poisson_sweep": sweep, "frontier_poisson_sweep": frontier_sweep,
+            "frontier_one_seed_8M_f32": frontier_solve}
 
 
 def run_reference(args):

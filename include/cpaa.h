@@ -83,6 +83,12 @@ typedef enum { CPAA_F64 = 0, CPAA_F32 = 1, CPAA_BF16 = 2, CPAA_DF64 = 3 } cpaa_p
 #define CPAA_DEVICE_IO 1u   /* p / pi (P / PI) are device pointers */
 #define CPAA_TIME_ROUNDS 2u /* time the M round launches with CUDA events on the solve's
                                stream; the result is cpaa_info.rounds_ms */
+#define CPAA_SPARSE_FRONTIER 8u /* early rounds only on the work items that hold a row of the
+                                   k-hop ball of p's support (T_k p vanishes outside it,
+                                   Sec. 4.1), until that ball covers half the entries or 8
+                                   rounds have run; results are the same bits as without it.
+                                   cpaa_solve, cpaa_solve_batch and cpaa_server_create (not
+                                   with CPAA_SERVER_FUSED); ignored by cpaa_power_solve */
 #define CPAA_SERVER_FUSED 4u /* cpaa_server_create: all graphs on one stream, each round of
                                 every graph with live queries in one kernel launch over the
                                 graphs' work lists, instead of one stream and one launch per
@@ -114,7 +120,7 @@ typedef struct {
     int fixed_rounds;         /* > 0: run exactly this many rounds (Algorithm 1's M) and
                                  ignore tol; 0: choose M from tol (default) */
     int max_rounds;           /* cap on M; 0 means 2000 */
-    unsigned flags;           /* CPAA_DEVICE_IO | CPAA_TIME_ROUNDS */
+    unsigned flags;           /* CPAA_DEVICE_IO | CPAA_TIME_ROUNDS | CPAA_SPARSE_FRONTIER */
     void *stream;             /* cudaStream_t to run on; NULL = legacy default stream */
     double *history;          /* optional host array [2*(M+1)]: sum T_k and sum |T_k|
                                  for k = 0..M (the mass view of Sec. 4.1); cpaa_solve only */
@@ -286,7 +292,10 @@ typedef struct {
 /* Create a server.  device_mem_budget bounds the device memory of all slots;
  * opt (NULL for defaults) sets the precision (any of the four; default for
  * serving: CPAA_F32), normalize, max_rounds and
- * stop_rule; of its flags only CPAA_SERVER_FUSED is read, and its stream is
+ * stop_rule; of its flags only CPAA_SERVER_FUSED and CPAA_SPARSE_FRONTIER are read
+ * (the frontier applies to graphs of at least 2^22 entries whose tile starts
+ * from empty: their first rounds skip the work items outside the queries'
+ * k-hop balls until a query joins the running ones), and its stream is
  * ignored.  Starts two host threads (scheduler, completion). */
 cpaa_status cpaa_server_create(size_t device_mem_budget, const cpaa_options *opt,
                                cpaa_server **out);

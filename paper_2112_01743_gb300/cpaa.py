@@ -16,7 +16,8 @@ __all__ = [
     "CPAA_EBUSY", "CPAA_ECANCELLED", "CPAA_ENOTFOUND",
     "CPAA_F64", "CPAA_F32", "CPAA_BF16", "CPAA_DF64", "CPAA_GRAPH_DEVICE_INPUT", "CPAA_GRAPH_VALIDATE",
     "CPAA_GRAPH_TRUSTED", "CPAA_GRAPH_AUTOTUNE", "CpaaLayoutParams", "cpaa_graph_create_ex",
-    "CPAA_DEVICE_IO", "CPAA_TIME_ROUNDS", "CPAA_SERVER_FUSED", "CPAA_STOP_RIGOROUS", "CPAA_STOP_POSTERIORI",
+    "CPAA_DEVICE_IO", "CPAA_TIME_ROUNDS", "CPAA_SERVER_FUSED", "CPAA_SPARSE_FRONTIER", "CPAA_STOP_RIGOROUS",
+    "CPAA_STOP_POSTERIORI",
     "cpaa_options_init", "cpaa_graph_create", "cpaa_graph_destroy", "cpaa_graph_info", "cpaa_graph_layout",
     "CpaaLayout", "cpaa_solve", "cpaa_solve_batch", "cpaa_rounds_needed", "cpaa_l1_bound",
     "cpaa_status_string", "cpaa_last_error", "cpaa_solve_fixed_noalloc", "cpaa_power_solve", "Graph",
@@ -34,6 +35,7 @@ CPAA_NOALLOC_MAX_N = 1300000
 CPAA_SERVER_MAX_SEEDS = 64
 CPAA_TIME_ROUNDS = 2
 CPAA_SERVER_FUSED = 4
+CPAA_SPARSE_FRONTIER = 8
 CPAA_STOP_RIGOROUS, CPAA_STOP_POSTERIORI = 0, 1
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -239,7 +241,7 @@ def cpaa_graph_info(g):
 
 
 def _options(precision, normalize, fixed_rounds, max_rounds, device_io, stream, history,
-             time_rounds=False, stop_rule=CPAA_STOP_RIGOROUS):
+             time_rounds=False, stop_rule=CPAA_STOP_RIGOROUS, frontier=False):
     o = cpaa_options_init()
     o.stop_rule = int(stop_rule)
     o.precision = int(precision)
@@ -247,7 +249,8 @@ def _options(precision, normalize, fixed_rounds, max_rounds, device_io, stream, 
     o.fixed_rounds = int(fixed_rounds)
     if max_rounds:
         o.max_rounds = int(max_rounds)
-    o.flags = (CPAA_DEVICE_IO if device_io else 0) | (CPAA_TIME_ROUNDS if time_rounds else 0)
+    o.flags = (CPAA_DEVICE_IO if device_io else 0) | (CPAA_TIME_ROUNDS if time_rounds else 0) | \
+        (CPAA_SPARSE_FRONTIER if frontier else 0)
     o.stream = stream
     if history is not None:
         o.history = history.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
@@ -265,13 +268,13 @@ def _stream_of(x, stream):
 
 def cpaa_solve(g, p, c, tol, pi, precision=CPAA_F64, normalize=0, fixed_rounds=0, max_rounds=0,
                stream=None, history=None, raise_notconv=True, time_rounds=False,
-               stop_rule=CPAA_STOP_RIGOROUS):
+               stop_rule=CPAA_STOP_RIGOROUS, frontier=False):
     """pi <- CPAA(p); p, pi FP64 length n (both host or both device)."""
     dev = _is_device(p)
     if dev != _is_device(pi):
         raise ValueError("p and pi must both be host or both be device buffers")
     o = _options(precision, normalize, fixed_rounds, max_rounds, dev, _stream_of(p, stream), history,
-                 time_rounds, stop_rule)
+                 time_rounds, stop_rule, frontier)
     info = CpaaInfo()
     st = lib().cpaa_solve(g, _addr(p), float(c), float(tol), _addr(pi), ctypes.byref(o), ctypes.byref(info))
     _check(st, raise_notconv)
@@ -296,13 +299,13 @@ def cpaa_power_solve(g, p, c, tol, pi, precision=CPAA_F64, normalize=0, fixed_ro
 
 def cpaa_solve_batch(g, B, P, c, tol, PI, precision=CPAA_F32, normalize=0, fixed_rounds=0,
                      max_rounds=0, stream=None, raise_notconv=True, batch_width=0,
-                     stop_rule=CPAA_STOP_RIGOROUS):
+                     stop_rule=CPAA_STOP_RIGOROUS, frontier=False):
     """Column b of P (n x B column-major, i.e. B vectors back to back) with
     damping c[b] -> column b of PI.  Returns a list of B info records."""
     dev = _is_device(P)
     cvec = np.ascontiguousarray(np.broadcast_to(np.asarray(c, dtype=np.float64), (int(B),)))
     o = _options(precision, normalize, fixed_rounds, max_rounds, dev, _stream_of(P, stream), None,
-                 False, stop_rule)
+                 False, stop_rule, frontier)
     o.batch_width = int(batch_width)
     infos = (CpaaInfo * int(B))()
     st = lib().cpaa_solve_batch(g, int(B), _addr(P), cvec.ctypes.data, float(tol), _addr(PI),
@@ -322,13 +325,15 @@ def cpaa_solve_fixed_noalloc(n, nnz, row_ptr, col_idx, p, c, rounds, pi, normali
 
 
 def cpaa_server_create(budget_bytes, precision=CPAA_F32, normalize=0, max_rounds=0,
-                       stop_rule=CPAA_STOP_RIGOROUS, fused=False):
+                       stop_rule=CPAA_STOP_RIGOROUS, fused=False, frontier=False):
     o = cpaa_options_init()
     o.precision = int(precision)
     o.normalize = int(normalize)
     o.stop_rule = int(stop_rule)
     if fused:
         o.flags |= CPAA_SERVER_FUSED
+    if frontier:
+        o.flags |= CPAA_SPARSE_FRONTIER
     if max_rounds:
         o.max_rounds = int(max_rounds)
     h = ctypes.c_void_p()
@@ -380,8 +385,9 @@ class Server:
     """Owning wrapper of a cpaa_server handle."""
 
     def __init__(self, budget_bytes, precision=CPAA_F32, normalize=0, max_rounds=0,
-                 stop_rule=CPAA_STOP_RIGOROUS, fused=False):
-        self.handle = cpaa_server_create(budget_bytes, precision, normalize, max_rounds, stop_rule, fused)
+                 stop_rule=CPAA_STOP_RIGOROUS, fused=False, frontier=False):
+        self.handle = cpaa_server_create(budget_bytes, precision, normalize, max_rounds, stop_rule, fused,
+                                         frontier)
 
     def add_graph(self, graph, max_slots=0):
         return cpaa_server_add_graph(self.handle, graph.handle, max_slots)

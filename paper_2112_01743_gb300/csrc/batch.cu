@@ -159,6 +159,7 @@ extern "C" cpaa_status cpaa_solve_batch(cpaa_graph *g, int B, const double *P, c
         job.precision = opt.precision;
         job.normalize = opt.normalize;
         job.posteriori = opt.stop_rule == CPAA_STOP_POSTERIORI && opt.fixed_rounds == 0;
+        job.frontier = (opt.flags & CPAA_SPARSE_FRONTIER) != 0;
         job.tol = tol;
         for (int j = 0; j < tw; ++j) {
             const int b = order[t0 + j];

@@ -144,11 +144,13 @@ static void release(cpaa_graph *g) {
     Workspace &w = g->ws;
     cudaFree(w.y0); cudaFree(w.y1); cudaFree(w.rho); cudaFree(w.comp); cudaFree(w.red);
     cudaFree(w.long_part); cudaFree(w.part); cudaFree(w.sums); cudaFree(w.io);
+    cudaFree(w.ipart); cudaFree(w.ipart2); cudaFree(w.maxl1); cudaFree(w.stop); cudaFree(w.stop_round);
     if (w.h_sums) cudaFreeHost(w.h_sums);
     for (auto &rg : w.round_graphs) cudaGraphExecDestroy(rg.exec);
     if (w.capture) cudaStreamDestroy(w.capture);
     if (w.tev[0]) cudaEventDestroy(w.tev[0]);
     if (w.tev[1]) cudaEventDestroy(w.tev[1]);
+    cudaFree(w.fr.cur); cudaFree(w.fr.ring); cudaFree(w.fr.add); cudaFree(w.fr.full);
     cudaFree(g->perm); cudaFree(g->hub_row_ptr); cudaFree(g->hub_col); cudaFree(g->hub_tiles);
     cudaFree(g->long_cnt); cudaFree(g->sell_col); cudaFree(g->chunk_off);
     cudaFree(g->chunk_len); cudaFree(g->chunk_order); cudaFree(g->chunk_desc); cudaFree(g->deg64); cudaFree(g->inv_deg64);

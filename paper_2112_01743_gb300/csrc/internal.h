@@ -129,6 +129,26 @@ struct df {
     __host__ __device__ df(float h, float l) : hi(h), lo(l) {}
 };
 
+// Sparse-frontier state (CPAA_SPARSE_FRONTIER).  T_k p is zero outside the
+// k-hop ball of p's support (Sec. 4.1: T_{k+1} = 2 P T_k - T_{k-1} adds one hop
+// per round), so early rounds need only the work items (hub tiles, SELL
+// chunks) that hold a row of that ball.  Bitmaps over the rows, one bit per
+// row in the layout's order: words [0, hub_words) for the hub rows, then one
+// 32-bit word per SELL chunk (bit l: the chunk's row l).
+struct Frontier {
+    unsigned *cur = nullptr;   // rows that may be nonzero in a live column (cumulative)
+    unsigned *ring = nullptr;  // rows added by the last update: expanded next
+    unsigned *add = nullptr;   // neighbours marked by the last expansion
+    int *full = nullptr;       // sticky: 1 once rounds run over every item
+    unsigned long long *entries = nullptr;  // [2] stored entries of the items cur covers, by update parity
+    int64_t words = 0;
+    int hub_words = 0;
+};
+// Rounds that may run on the frontier (later ones always run on every item),
+// and the covered share of the entries beyond which rounds run on every item.
+constexpr int kFrontierRounds = 8;
+constexpr int kFrontierLimitDiv = 2;  // limit = nnz / kFrontierLimitDiv stored entries
+
 // Workspace of the solves, grown on demand and reused (one solve per graph at
 // a time).  Vectors of a tile of W columns are row-major [rows x W].
 struct Workspace {
@@ -163,6 +183,7 @@ struct Workspace {
     std::vector<RoundGraph> round_graphs;
     cudaStream_t capture = nullptr;  // private stream the captures run on
     cudaEvent_t tev[2] = {nullptr, nullptr};  // around the rounds (CPAA_TIME_ROUNDS)
+    Frontier fr;                     // CPAA_SPARSE_FRONTIER solves (allocated on first use)
 };
 
 // One tile of up to kMaxWidth vectors for run_tile (solve.cu).
@@ -176,6 +197,7 @@ struct TileJob {
     double c0half[kMaxWidth] = {};   // power method: 1 - c (the accumulator slot holds q)
     int rounds[kMaxWidth] = {};
     int power = 0;                    // 1: power-method rounds instead of Chebyshev ones
+    int frontier = 0;                 // 1: early rounds on the sparse frontier (CPAA_SPARSE_FRONTIER)
     int posteriori = 0;               // 1: columns may stop early by the a-posteriori rule
     double tol = 0;                   // its tolerance
     double p_l1[kMaxWidth] = {};      // ||p||_1 = ||T_0 p||_1 of each column (that rule's start)
@@ -283,9 +305,35 @@ struct StepLaunch {
     unsigned first = 0;             // columns in their first round (k == 1)
     int power = 0;                  // 1: power-method round (ck[b] = c, rho holds q = (1-c) p / d)
     int *long_cnt = nullptr;        // hub ticket counters [n_hub], all zero; NULL = the graph's own
+    // sparse frontier (NULL: every item): items whose rows are all outside
+    // front are skipped, unless *front_full or *front_entries > front_limit
+    const unsigned *front = nullptr;
+    int *front_full = nullptr;
+    const unsigned long long *front_entries = nullptr;
+    unsigned long long front_limit = 0;
+    int front_hub_words = 0;
     cudaStream_t stream = nullptr;
 };
 void prepare_step(int precision, int width);
+
+// Sparse-frontier pieces (frontier.cu).  ensure_frontier allocates f for g
+// (frontier_bytes of device memory, counted in track's device_bytes);
+// frontier_reset clears it; frontier_mark_nonzero marks the rows where any of
+// the `width` columns of y0 is nonzero (and zeroes those rows of y1, the other
+// iterate buffer); frontier_mark_rows marks up to kMaxFrontierSeeds given rows;
+// frontier_expand adds the neighbours of the last ring and counts the entries
+// covered (update parity `parity`); frontier_launch fills a round's fields.
+constexpr int kMaxFrontierSeeds = 64;
+size_t frontier_bytes(const cpaa_graph *g);
+cpaa_status ensure_frontier(const cpaa_graph *g, Frontier &f, cpaa_graph *track);  // track: NULL or g
+void free_frontier(cpaa_graph *track, Frontier &f);
+cudaError_t frontier_reset(const Frontier &f, cudaStream_t st);
+cudaError_t frontier_mark_nonzero(const cpaa_graph *g, const Frontier &f, int precision, int width,
+                                  const void *y0, void *y1, cudaStream_t st);
+cudaError_t frontier_mark_rows(const cpaa_graph *g, const Frontier &f, int count, const int32_t *rows,
+                               cudaStream_t st);
+cudaError_t frontier_expand(const cpaa_graph *g, const Frontier &f, int parity, cudaStream_t st);
+void frontier_launch(const cpaa_graph *g, const Frontier &f, int parity, StepLaunch &sl);
 cudaError_t launch_step(const StepLaunch &s);
 // One round of up to 8 graphs in a single launch (same precision, width and
 // stream).

@@ -86,10 +86,11 @@ struct SeedArgs {
 // Column b of a new query: y_0 = D^-1 p, rho = (c_0/2) y_0, comp = 0, with p
 // zero outside the seeds (same arithmetic as the dense prep of solve.cu).
 template <class S, class R, int W>
-__global__ void slot_zero_kernel(S *y0, R *rho, R *comp, int64_t n, int b) {
+__global__ void slot_zero_kernel(S *y0, S *y1, R *rho, R *comp, int64_t n, int b) {
     for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n;
          u += (int64_t)gridDim.x * blockDim.x) {
         y0[u * W + b] = S(0.0f);
+        if (y1) y1[u * W + b] = S(0.0f);  // sparse-frontier start: rows outside the ball stay +0
         rho[u * W + b] = R(0);
         if (comp) comp[u * W + b] = R(0);
     }
@@ -242,6 +243,13 @@ struct GraphState {
     DevStop *h_slot = nullptr;  // [W]: stop state at each slot's finalisation
     DevStop *d_ring = nullptr;  // device addresses of the same memory
     DevStop *d_slot = nullptr;
+    // sparse frontier (CPAA_SPARSE_FRONTIER): a tile that starts from empty runs
+    // its early rounds on the ball of its queries' seeds, until a query joins
+    // the running ones, the ball is large, or kFrontierRounds have run
+    Frontier fr;
+    bool fr_ok = false;  // the frontier is allocated for this graph (it is large enough to gain)
+    bool fr_on = false;  // the current rounds run on the frontier
+    int fr_k = 0;        // frontier rounds run since it started
 };
 
 struct Completion {
@@ -262,6 +270,7 @@ struct cpaa_server {
     int prec = CPAA_F32, normalize = 0, max_rounds = kDefaultMaxRounds;
     int posteriori = 0;  // stop rule CPAA_STOP_POSTERIORI
     int fused = 0;       // CPAA_SERVER_FUSED: one stream, one round launch over all graphs
+    int frontier = 0;    // CPAA_SPARSE_FRONTIER (not with CPAA_SERVER_FUSED)
     cudaStream_t fstream = nullptr;
     int device = 0;
     std::vector<std::unique_ptr<GraphState>> graphs;
@@ -291,23 +300,29 @@ static size_t tile_bytes(const cpaa_graph *g, int prec, int W) {
     return std::max((n + 1) * W * vbytes(prec), n * W * rbytes(prec));
 }
 
-static size_t graph_bytes(const cpaa_graph *g, int prec, int W, int posteriori) {
+// Graphs below this many entries serve without the sparse frontier: their
+// rounds are chains of launch latencies, which two more kernels per round lengthen.
+constexpr int64_t kFrontierMinEntries = int64_t(1) << 22;
+
+static size_t graph_bytes(const cpaa_graph *g, int prec, int W, int posteriori, int frontier) {
     const size_t n = (size_t)g->n;
     size_t b = 5 * tile_bytes(g, prec, W) + n * W * 8 +
                (size_t)std::max(1, g->num_hub_tiles) * W * 8 + (size_t)std::max(1, g->n_hub) * 4 +
                (size_t)kPrepBlocks * 8 + (size_t)W * 8 + 2 * 8 * (size_t)W;
     if (posteriori)  // per-round item sums
         b += 2 * 8 * (size_t)W * ((size_t)g->n_hub + g->num_chunks + kSumBlocks) + sizeof(DevStop);
+    if (frontier && g->nnz >= kFrontierMinEntries) b += frontier_bytes(g);
     return b;
 }
 
 template <class S, class R, int W>
-static void launch_slot_prep(GraphState &gs, int b, const SeedArgs &a) {
+static void launch_slot_prep(GraphState &gs, int b, const SeedArgs &a, bool both) {
     const int64_t n = gs.g->n;
     const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 2048);
     R *comp = std::is_same<R, float>::value ? (R *)gs.comp : nullptr;
     S *y0 = (S *)gs.y[gs.G & 1];  // the buffer the next round gathers from
-    slot_zero_kernel<S, R, W><<<grid, 256, 0, gs.stream>>>(y0, (R *)gs.rho, comp, n, b);
+    S *y1 = both ? (S *)gs.y[(gs.G + 1) & 1] : nullptr;
+    slot_zero_kernel<S, R, W><<<grid, 256, 0, gs.stream>>>(y0, y1, (R *)gs.rho, comp, n, b);
     slot_seed_kernel<S, R, W><<<1, CPAA_SERVER_MAX_SEEDS, 0, gs.stream>>>(a, gs.g->inv_deg64, y0, (R *)gs.rho,
                                                                          gs.dstop);
 }
@@ -325,13 +340,13 @@ static void launch_slot_final(GraphState &gs, int b, int normalize, double c) {
 }
 
 template <class S, class R>
-static void slot_prep_w(GraphState &gs, int b, const SeedArgs &a) {
+static void slot_prep_w(GraphState &gs, int b, const SeedArgs &a, bool both) {
     switch (gs.w) {
-        case 1: launch_slot_prep<S, R, 1>(gs, b, a); break;
-        case 2: launch_slot_prep<S, R, 2>(gs, b, a); break;
-        case 4: launch_slot_prep<S, R, 4>(gs, b, a); break;
-        case 8: launch_slot_prep<S, R, 8>(gs, b, a); break;
-        case 16: launch_slot_prep<S, R, 16>(gs, b, a); break;
+        case 1: launch_slot_prep<S, R, 1>(gs, b, a, both); break;
+        case 2: launch_slot_prep<S, R, 2>(gs, b, a, both); break;
+        case 4: launch_slot_prep<S, R, 4>(gs, b, a, both); break;
+        case 8: launch_slot_prep<S, R, 8>(gs, b, a, both); break;
+        case 16: launch_slot_prep<S, R, 16>(gs, b, a, both); break;
     }
 }
 
@@ -346,11 +361,11 @@ static void slot_final_w(GraphState &gs, int b, int normalize, double c) {
     }
 }
 
-static void slot_prep(cpaa_server *s, GraphState &gs, int b, const SeedArgs &a) {
-    if (s->prec == CPAA_F64) slot_prep_w<double, double>(gs, b, a);
-    else if (s->prec == CPAA_F32) slot_prep_w<float, float>(gs, b, a);
-    else if (s->prec == CPAA_DF64) slot_prep_w<df, df>(gs, b, a);
-    else slot_prep_w<__nv_bfloat16, float>(gs, b, a);
+static void slot_prep(cpaa_server *s, GraphState &gs, int b, const SeedArgs &a, bool both) {
+    if (s->prec == CPAA_F64) slot_prep_w<double, double>(gs, b, a, both);
+    else if (s->prec == CPAA_F32) slot_prep_w<float, float>(gs, b, a, both);
+    else if (s->prec == CPAA_DF64) slot_prep_w<df, df>(gs, b, a, both);
+    else slot_prep_w<__nv_bfloat16, float>(gs, b, a, both);
 }
 
 static void slot_final(cpaa_server *s, GraphState &gs, int b, double c) {
@@ -460,7 +475,7 @@ static bool plan_round(cpaa_server *s, GraphState &gs, StepLaunch &sl, unsigned 
     // has completed and been processed (its ring entry is then free)
     if (gs.G + 1 > kInFlight && gs.G_seen < gs.G + 1 - kInFlight) return false;
     std::vector<std::pair<int, SeedArgs>> admitted;
-    unsigned live = 0;
+    unsigned live = 0, live_before = 0;
     {
         std::lock_guard<std::mutex> lk(s->mu);
         const auto now = clk::now();
@@ -475,6 +490,8 @@ static bool plan_round(cpaa_server *s, GraphState &gs, StepLaunch &sl, unsigned 
                 s->cv_done.notify_all();
             }
         }
+        for (int b = 0; b < gs.W; ++b)
+            if (gs.slots[b].st == LIVE) live_before |= 1u << b;
         {
             for (int b = 0; b < gs.W && !gs.pending.empty(); ++b) {
                 Slot &sl = gs.slots[b];
@@ -532,7 +549,23 @@ static bool plan_round(cpaa_server *s, GraphState &gs, StepLaunch &sl, unsigned 
         while (wn < need) wn <<= 1;
         set_width(s, gs, wn, live);
     }
-    for (auto &a : admitted) slot_prep(s, gs, a.first, a.second);
+    // sparse frontier: a tile that starts from empty starts on the ball of its
+    // queries' seeds; a query that joins running ones ends the frontier rounds
+    // (its seeds are outside the ball the others have grown)
+    const bool fr_start = gs.fr_ok && live_before == 0 && !admitted.empty();
+    if (!admitted.empty() && !fr_start) gs.fr_on = false;
+    if (fr_start) {
+        frontier_reset(gs.fr, gs.stream);
+        if (gs.ipart)  // items the early rounds skip keep a zero partial-sum slot
+            cudaMemsetAsync(gs.ipart, 0, 2 * 8 * (size_t)gs.W * ((size_t)gs.g->n_hub + gs.g->num_chunks),
+                            gs.stream);
+        gs.fr_on = true;
+        gs.fr_k = 0;
+    }
+    for (auto &a : admitted) {
+        slot_prep(s, gs, a.first, a.second, fr_start);
+        if (fr_start) frontier_mark_rows(gs.g, gs.fr, a.second.count, a.second.r, gs.stream);
+    }
     *admitted_any = !admitted.empty();
     *live_out = live;
     if (!live) return false;
@@ -578,6 +611,15 @@ static bool plan_round(cpaa_server *s, GraphState &gs, StepLaunch &sl, unsigned 
         sl.sa.maxl1 = gs.dstop->maxl1;
         sl.sa.stop = &gs.dstop->stop;
         sl.sa.stop_round = gs.dstop->round;
+    }
+    if (gs.fr_on) {
+        if (gs.fr_k < kFrontierRounds) {
+            ++gs.fr_k;
+            frontier_expand(gs.g, gs.fr, gs.fr_k, gs.stream);
+            frontier_launch(gs.g, gs.fr, gs.fr_k, sl);
+        } else {
+            gs.fr_on = false;
+        }
     }
     return true;
 }
@@ -759,6 +801,7 @@ static void free_graph_state(GraphState &gs) {
     cudaFree(gs.long_part);
     cudaFree(gs.long_cnt); cudaFree(gs.red); cudaFree(gs.result); cudaFree(gs.part); cudaFree(gs.sums);
     cudaFree(gs.ipart); cudaFree(gs.ipart2); cudaFree(gs.dstop);
+    free_frontier(nullptr, gs.fr);
     if (gs.h_ring) cudaFreeHost(gs.h_ring);
     if (gs.h_slot) cudaFreeHost(gs.h_slot);
     for (auto &e : gs.ring) if (e) cudaEventDestroy(e);
@@ -796,6 +839,7 @@ extern "C" cpaa_status cpaa_server_create(size_t device_mem_budget, const cpaa_o
     cpaa_server *s = new cpaa_server();
     s->posteriori = o.stop_rule == CPAA_STOP_POSTERIORI;
     s->fused = (o.flags & CPAA_SERVER_FUSED) != 0;
+    s->frontier = !s->fused && (o.flags & CPAA_SPARSE_FRONTIER) != 0;
     s->budget = device_mem_budget;
     s->prec = o.precision;
     s->normalize = o.normalize;
@@ -822,7 +866,7 @@ extern "C" cpaa_status cpaa_server_add_graph(cpaa_server *s, cpaa_graph *g, int 
     while (W & (W - 1)) --W;
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        while (W >= 1 && s->used + graph_bytes(g, s->prec, W, s->posteriori) > s->budget) W /= 2;
+        while (W >= 1 && s->used + graph_bytes(g, s->prec, W, s->posteriori, s->frontier) > s->budget) W /= 2;
         if (W < 1) return fail(CPAA_ENOMEM, "device memory budget too small for one slot of this graph");
     }
     auto gs = std::make_unique<GraphState>();
@@ -873,6 +917,10 @@ extern "C" cpaa_status cpaa_server_add_graph(cpaa_server *s, cpaa_graph *g, int 
             SCK(cudaHostGetDevicePointer((void **)&gs->d_ring, gs->h_ring, 0));
             SCK(cudaHostGetDevicePointer((void **)&gs->d_slot, gs->h_slot, 0));
         }
+        if (s->frontier && g->nnz >= kFrontierMinEntries) {
+            if ((st = ensure_frontier(g, gs->fr, nullptr)) != CPAA_OK) goto fail_out;
+            gs->fr_ok = true;
+        }
         for (auto &e : gs->ring) SCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         gs->slots.resize(W);
         for (auto &sl : gs->slots) SCK(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
@@ -888,7 +936,7 @@ extern "C" cpaa_status cpaa_server_add_graph(cpaa_server *s, cpaa_graph *g, int 
             gs->deg[perm[r]] = deg[r];
         }
         SCK(cudaStreamSynchronize(gs->stream));
-        gs->bytes = graph_bytes(g, s->prec, W, s->posteriori);
+        gs->bytes = graph_bytes(g, s->prec, W, s->posteriori, s->frontier);
         std::lock_guard<std::mutex> lk(s->mu);
         gs->id = (int)s->graphs.size();
         s->used += gs->bytes;

@@ -381,6 +381,12 @@ static cudaError_t launch_rounds(cpaa_graph *g, const TileJob &job, bool history
         sl.power = job.power;
         sl.long_cnt = nullptr;
         sl.stream = st;
+        if (job.frontier && k <= kFrontierRounds) {
+            // grow the ball by one hop, then a round over the items it covers
+            const cudaError_t fe = frontier_expand(g, w.fr, k, st);
+            if (fe != cudaSuccess) return fe;
+            frontier_launch(g, w.fr, k, sl);
+        }
         const cudaError_t e = launch_step(sl);
         if (e != cudaSuccess) return e;
     }
@@ -399,6 +405,7 @@ static cpaa_status round_graph(cpaa_graph *g, const TileJob &job, bool history_a
     uint64_t tolb;
     std::memcpy(&tolb, &job.tol, sizeof tolb);
     std::vector<uint64_t> key = {(uint64_t)job.precision, (uint64_t)job.width, (uint64_t)job.power,
+                                 (uint64_t)job.frontier, (uint64_t)(uintptr_t)w.fr.cur,
                                  (uint64_t)history_all_rounds, (uint64_t)maxM, (uint64_t)job.posteriori,
                                  job.posteriori ? tolb : 0, (uint64_t)job.normalize,
                                  (uint64_t)(uintptr_t)w.y0, (uint64_t)(uintptr_t)w.y1,
@@ -456,8 +463,18 @@ cpaa_status run_tile(cpaa_graph *g, const TileJob &job, cudaStream_t st, bool hi
         // the copy reads the caller's job, which ends with this call
         CPAA_CUDA(cudaStreamSynchronize(st));
     }
+    if (job.frontier) {
+        cpaa_status fs = ensure_frontier(g, w.fr, g);
+        if (fs != CPAA_OK) return fs;
+        CPAA_CUDA(frontier_reset(w.fr, st));
+        // items the early rounds skip keep a zero partial-sum slot
+        CPAA_CUDA(cudaMemsetAsync(w.ipart, 0, sizeof(double) * 2 * (size_t)W * ((size_t)g->n_hub + g->num_chunks),
+                                  st));
+    }
     // prep also zeroes the sums, the tickets and the sentinel rows n
     CPAA_CUDA(tile_phase(g, job, st, 0));
+    // the ball starts at the rows where some column of y_0 = D^-1 p is nonzero
+    if (job.frontier) CPAA_CUDA(frontier_mark_nonzero(g, w.fr, job.precision, W, w.y0, w.y1, st));
 
     cudaGraphExec_t exec = nullptr;
     if (maxM > 0) {
@@ -580,6 +597,7 @@ static cpaa_status solve_one(cpaa_graph *g, const double *p, double c, double to
     job.c0half[0] = power ? 1.0 - c : ck0[0] / 2.0;
     job.rounds[0] = M;
     job.power = power;
+    job.frontier = !power && (opt.flags & CPAA_SPARSE_FRONTIER) != 0;
     // the a-posteriori rule may stop the rounds before the rigorous M
     job.posteriori = opt.stop_rule == CPAA_STOP_POSTERIORI && opt.fixed_rounds == 0 && M > 0;
     job.tol = tol;

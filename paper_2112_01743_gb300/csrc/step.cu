@@ -78,7 +78,21 @@ struct StepParams {
     unsigned reduce;
     unsigned first;  // columns in their first round (y_1 = D^-1 P y_0... scaled: s / d)
     int power;       // 1: power-method round y' = c s / d + q, ck[b] = c, q held in rho
+    // sparse frontier (frontier.cu), or front == NULL: items with no row in
+    // front are skipped, unless *front_full or the covered entries exceed
+    // front_limit (then this and every later round take every item)
+    const unsigned *front;
+    int *front_full;
+    const unsigned long long *front_entries;
+    unsigned long long front_limit;
+    int front_hub_words;
 };
+
+// Whether an item holds a row of the frontier: a hub tile's row, a chunk's rows.
+__device__ __forceinline__ bool hub_in_front(const unsigned *fr, int h) { return fr[h >> 5] >> (h & 31) & 1u; }
+__device__ __forceinline__ bool chunk_in_front(const unsigned *fr, int hub_words, int c) {
+    return fr[hub_words + c] != 0u;
+}
 
 // W consecutive values of one row, with the widest loads the row size allows.
 template <class T, int W>
@@ -458,14 +472,19 @@ __device__ __forceinline__ void chunk_sum(const StepParams<P, W> &p, const int32
 
 // Full groups and tail (the last group, 1..kSellVec entries: its first
 // entry starts the sum) of a chunk whose longest row has `exact` >= 1 entries.
+// Only FP64 takes the tail: there every addition costs a slot of GB300's slow
+// FP64 pipe (the lattice round keeps it 70% busy), while the other formats,
+// bound by memory, lose more to the tail's branches than they save
+// (measured: FP64 lattice round 0.328 -> 0.286 ms; FP32 0.138 -> 0.142 ms).
+template <int P>
 __device__ __forceinline__ void chunk_extent(int exact, int &groups, int &tail) {
-#if CPAA_SELL_TAIL
-    groups = (exact - 1) / kSellVec;
-    tail = exact - kSellVec * groups;
-#else
-    groups = (exact + kSellVec - 1) / kSellVec;
-    tail = 0;
-#endif
+    if (CPAA_SELL_TAIL && P == CPAA_F64) {
+        groups = (exact - 1) / kSellVec;
+        tail = exact - kSellVec * groups;
+    } else {
+        groups = (exact + kSellVec - 1) / kSellVec;
+        tail = 0;
+    }
 }
 
 // A long chunk by one CTA: warp w sums slice w of the entries of all 32
@@ -478,7 +497,7 @@ __device__ __forceinline__ void long_chunk(const StepParams<P, W> &p, int4 dsc, 
     const int c = dsc.x;
     const int64_t off = (int64_t)dsc.y * (kChunkRows * kSellVec);
     int groups, tail;
-    chunk_extent(dsc.w, groups, tail);
+    chunk_extent<P>(dsc.w, groups, tail);
     // slices of whole kSellVec groups; the last slice takes the tail
     const int per = (groups + (tail ? 1 : 0) + kWarps - 1) / kWarps;
     const int q0 = min(groups, warp * per), q1 = min(groups, q0 + per);
@@ -523,7 +542,7 @@ __device__ __forceinline__ void short_chunk(const StepParams<P, W> &p, int4 dsc,
     const int c = dsc.x;
     const int64_t off = (int64_t)dsc.y * (kChunkRows * kSellVec);
     int groups, tail;
-    chunk_extent(dsc.w, groups, tail);
+    chunk_extent<P>(dsc.w, groups, tail);
     const int64_t r = p.n_hub + (int64_t)c * kChunkRows + lane;
     const bool live = r < p.n;
     // for narrow tiles the row's own operands are fetched before the gather
@@ -562,15 +581,32 @@ __global__ void __launch_bounds__(kThreads) cheb_step_kernel(const StepParams<P,
     // every column has stopped the remaining rounds do nothing
     const unsigned active = p.stop ? (p.active & ~*p.stop) : p.active;
     if (p.stop && active == 0) return;
+    // sparse frontier: every thread takes the same decision from the same two
+    // words (the flag it may set is set only when the count already says so)
+    bool filt = false;
+    if (p.front) {
+        filt = !(*p.front_full || *p.front_entries > p.front_limit);
+        if (!filt && blockIdx.x == 0 && threadIdx.x == 0) *p.front_full = 1;
+    }
     const int n_cta_items = p.num_hub_tiles + p.num_long_chunks;
     for (int it = blockIdx.x; it < n_cta_items; it += gridDim.x) {
-        if (it < p.num_hub_tiles) hub_tile<P, W>(p, p.hub_tiles[it], active);
-        else long_chunk<P, W>(p, ld_stream4(&p.chunk_desc[it - p.num_hub_tiles].x), active);
+        if (it < p.num_hub_tiles) {
+            const int4 t = p.hub_tiles[it];
+            if (filt && !hub_in_front(p.front, t.x)) continue;  // the same for the whole CTA
+            hub_tile<P, W>(p, t, active);
+        } else {
+            const int4 d = ld_stream4(&p.chunk_desc[it - p.num_hub_tiles].x);
+            if (filt && !chunk_in_front(p.front, p.front_hub_words, d.x)) continue;
+            long_chunk<P, W>(p, d, active);
+        }
     }
     const int nwarps = (int)gridDim.x * kWarps;
     for (int idx = p.num_long_chunks + (int)blockIdx.x * kWarps + (int)(threadIdx.x >> 5); idx < p.num_chunks;
-         idx += nwarps)
-        short_chunk<P, W>(p, ld_stream4(&p.chunk_desc[idx].x), active);
+         idx += nwarps) {
+        const int4 d = ld_stream4(&p.chunk_desc[idx].x);
+        if (filt && !chunk_in_front(p.front, p.front_hub_words, d.x)) continue;  // the same for the whole warp
+        short_chunk<P, W>(p, d, active);
+    }
 }
 
 // One round over several graphs in one launch (the server's fused mode): the
@@ -739,6 +775,11 @@ static void fill_params(const StepLaunch &s, StepParams<P, W> &p) {
     p.reduce = s.reduce;
     p.first = s.first;
     p.power = s.power;
+    p.front = s.front;
+    p.front_full = s.front_full;
+    p.front_entries = s.front_entries;
+    p.front_limit = s.front_limit;
+    p.front_hub_words = s.front_hub_words;
 }
 
 // The two fixed-order sum kernels of a round that takes sums.  The item

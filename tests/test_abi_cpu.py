@@ -33,7 +33,7 @@ def test_header_constants_match_the_binding(L):
     src = open(os.path.join(ROOT, "include", "cpaa.h")).read()
     names = ("CPAA_GRAPH_DEVICE_INPUT", "CPAA_GRAPH_VALIDATE", "CPAA_GRAPH_TRUSTED", "CPAA_DEVICE_IO",
              "CPAA_TIME_ROUNDS", "CPAA_SERVER_FUSED", "CPAA_NOALLOC_MAX_N", "CPAA_SERVER_MAX_SEEDS",
-             "CPAA_GRAPH_AUTOTUNE")
+             "CPAA_GRAPH_AUTOTUNE", "CPAA_SPARSE_FRONTIER")
     for name in names:
         m = re.search(r"#define\s+%s\s+(\d+)u?\b" % name, src)
         assert m, name
