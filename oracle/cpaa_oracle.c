@@ -91,7 +91,8 @@ int orc_rounds_needed(double c, double tol, double kappa, int normalize, int max
 /* ------------------------------------------------------------------ */
 
 typedef struct {
-    int kind; /* 0: first round, 1: later round, 2: power-method round */
+    int kind; /* 0: first round, 1: later round, 2: power-method round,
+                 3 / 4: first / later round of the interval form (below) */
     int64_t n, lo, hi;
     const int32_t *row_ptr, *col_idx;
     const double *T;   /* T_{k-1} (or the power iterate) */
@@ -100,6 +101,7 @@ typedef struct {
     double *pibar;
     double ck, c;
     const double *p;
+    double mid, half;  /* interval form: centre and half-width of [lambda_lo, 1] */
 } orc_job;
 
 static void *orc_worker(void *arg) {
@@ -125,13 +127,31 @@ static void *orc_worker(void *arg) {
             s = 2.0 * s - j->T[u];
             j->Tpp[u] = s;
             j->pibar[u] = j->pibar[u] + j->ck * s;
-        } else {
+        } else if (j->kind == 2) {
             /* power method (Jacobi) round: x'_u = c sum_v x_v / deg(v) + (1-c) p_u */
             for (int32_t e = rp[u]; e < rp[u + 1]; ++e) {
                 int32_t v = ci[e];
                 s = s + j->T[v] / (double)(rp[v + 1] - rp[v]);
             }
             j->Tpp[u] = j->c * s + (1.0 - j->c) * j->p[u];
+        } else if (j->kind == 3) {
+            /* interval form, k = 1: T'_u = ((P T)_u - mid T_u) / half */
+            for (int32_t e = rp[u]; e < rp[u + 1]; ++e) {
+                int32_t v = ci[e];
+                s = s + j->T[v] / (double)(rp[v + 1] - rp[v]);
+            }
+            s = (s - j->mid * j->T[u]) / j->half;
+            j->Tpp[u] = s;
+            j->pibar[u] = j->pibar[u] + j->ck * s;
+        } else {
+            /* interval form, k >= 2: T''_u = 2 ((P T')_u - mid T'_u) / half - T_u */
+            for (int32_t e = rp[u]; e < rp[u + 1]; ++e) {
+                int32_t v = ci[e];
+                s = s + j->Tp[v] / (double)(rp[v + 1] - rp[v]);
+            }
+            s = 2.0 * (s - j->mid * j->Tp[u]) / j->half - j->T[u];
+            j->Tpp[u] = s;
+            j->pibar[u] = j->pibar[u] + j->ck * s;
         }
     }
     return NULL;
@@ -218,6 +238,136 @@ int orc_cpaa(int64_t n, const int32_t *row_ptr, const int32_t *col_idx, const do
             if (mass) mass[k] = m;
             if (l1) l1[k] = a;
         }
+        if (k >= 2) { /* rotate: T <- T', T' <- T'' */
+            double *t = T; T = Tp; Tp = Tpp; Tpp = t;
+        }
+    }
+    if (normalize == 0) {
+        double s = 0.0;
+        for (int64_t i = 0; i < n; ++i) s += pibar[i];
+        for (int64_t i = 0; i < n; ++i) pi[i] = pibar[i] / s;
+    } else {
+        for (int64_t i = 0; i < n; ++i) pi[i] = (1.0 - c) * pibar[i];
+    }
+    free(ck); free(T); free(Tp); free(Tpp);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Chebyshev series on a narrower interval [lambda_lo, 1]                */
+/* (the general-interval series of Sec. 2.2; Sec. 6 names other        */
+/*  approximations as future work)                                      */
+/* ------------------------------------------------------------------ */
+/*
+ * Sec. 2.2 gives the Chebyshev series of f on a general interval [a, b]: the
+ * expansion variable is t = (2x - (a+b)) / (b-a), which maps [a, b] onto
+ * [-1, 1], and the coefficients are the integrals printed there.  Reading
+ * (the printed series writes T_k(x) for T_k(t), and its coefficient integral
+ * lacks the 1/pi of the [-1, 1] case given right after it): with the centre
+ * mid = (a+b)/2 and half-width half = (b-a)/2, x = mid + half cos(theta),
+ *     c_k = (2/pi) int_0^pi f(mid + half cos theta) cos(k theta) d theta.
+ * Here [a, b] = [lambda_lo, 1] holds the whole spectrum of P (real, Lemma 2),
+ * and f(x) = 1/(1 - c x) becomes
+ *     f(mid + half cos theta) = 1/(1 - c mid) * 1/(1 - chat cos theta),
+ *     chat = c half / (1 - c mid)  (< c when lambda_lo > -1),
+ * so c_k = c_k(chat) / (1 - c mid) with the [-1, 1] coefficients of chat, and
+ * the recurrence runs on Q = (P - mid I) / half, whose spectrum lies in
+ * [-1, 1]: T_0 = p, T_1 = Q p, T_{k+1} = 2 Q T_k - T_{k-1}.  lambda_lo = -1
+ * gives back Algorithm 1 exactly (mid = 0, half = 1, chat = c).
+ */
+static void orc_interval(double c, double lambda_lo, double *mid, double *half, double *chat) {
+    *mid = 0.5 * (1.0 + lambda_lo);
+    *half = 0.5 * (1.0 - lambda_lo);
+    *chat = c * *half / (1.0 - c * *mid);
+}
+
+/* c_0 .. c_M of 1/(1 - c x) expanded on [lambda_lo, 1]. */
+void orc_cheb_coeffs_interval(double c, double lambda_lo, int M, double *ck) {
+    double mid, half, chat;
+    orc_interval(c, lambda_lo, &mid, &half, &chat);
+    orc_cheb_coeffs(chat, M, ck);
+    for (int k = 0; k <= M; ++k) ck[k] = ck[k] / (1.0 - c * mid);
+}
+
+/* The interval form's ERR_M: (1-c) sum_{k>M} c_k, the mass the truncation
+ * leaves out (every T_k(Q) keeps e^T p, because e^T Q = e^T).  With
+ * c_k = c_0 betahat^k this is (1-c) c_0 betahat^(M+1) / (1 - betahat). */
+double orc_err_bound_interval(double c, double lambda_lo, int M) {
+    double mid, half, chat;
+    orc_interval(c, lambda_lo, &mid, &half, &chat);
+    double bh = orc_beta(chat);
+    double c0 = 2.0 / sqrt(1.0 - chat * chat) / (1.0 - c * mid);
+    return (1.0 - c) * c0 * pow(bh, (double)(M + 1)) / (1.0 - bh);
+}
+
+/* The L1 bound of orc_l1_bound with the interval form's ERR_M: kappa still
+ * bounds ||T_k(Q) p||_1, since Q is similar to the symmetric
+ * (S - mid I) / half, whose spectrum lies in [-1, 1]. */
+double orc_l1_bound_interval(double c, double lambda_lo, int M, double kappa, int normalize) {
+    double E = orc_err_bound_interval(c, lambda_lo, M);
+    if (normalize == 1) return E * kappa;
+    return E * kappa + (1.0 + E * kappa) * E / (1.0 - E);
+}
+
+int orc_rounds_needed_interval(double c, double lambda_lo, double tol, double kappa, int normalize,
+                               int max_rounds) {
+    for (int M = 1; M <= max_rounds; ++M)
+        if (orc_l1_bound_interval(c, lambda_lo, M, kappa, normalize) < tol) return M;
+    return -1;
+}
+
+/* A lower bound on the spectrum of S = D^-1/2 A D^-1/2 (hence of P) that holds
+ * for every graph with a self-loop on every vertex: A = A' + I and D = D' + I
+ * with the loop-free A', D', and D' + A' is positive semidefinite (its
+ * quadratic form is the sum over edges of (x_i + x_j)^2), so A + D >= 2I and
+ * S + I = D^-1/2 (A + D) D^-1/2 >= 2 D^-1 >= (2 / d_max) I.  Returns
+ * -1 + 2 / d_max, or -1 (no bound beyond Lemma 2's) when a vertex has no loop. */
+double orc_lambda_lo_loops(int64_t n, const int32_t *row_ptr, const int32_t *col_idx) {
+    int32_t dmax = 0;
+    for (int64_t u = 0; u < n; ++u) {
+        int loop = 0;
+        for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e)
+            if (col_idx[e] == (int32_t)u) loop = 1;
+        if (!loop) return -1.0;
+        if (row_ptr[u + 1] - row_ptr[u] > dmax) dmax = row_ptr[u + 1] - row_ptr[u];
+    }
+    return -1.0 + 2.0 / (double)dmax;
+}
+
+/* CPAA on [lambda_lo, 1]: Algorithm 1 with the coefficients and the
+ * recurrence above (same readings as orc_cpaa; lambda_lo = -1 is orc_cpaa).
+ * normalize = 1 scales by (1-c) (Sec. 2.1), as the coefficients already hold
+ * the 1/(1 - c mid). */
+int orc_cpaa_interval(int64_t n, const int32_t *row_ptr, const int32_t *col_idx, const double *p,
+                      double c, double lambda_lo, int M, int normalize, int nthreads, double *pi) {
+    if (n <= 0 || M < 0 || !(c > 0.0 && c < 1.0) || !(lambda_lo >= -1.0 && lambda_lo < 1.0)) return -1;
+    double mid, half, chat;
+    orc_interval(c, lambda_lo, &mid, &half, &chat);
+    double *ck = (double *)malloc(sizeof(double) * (size_t)(M + 1));
+    double *T = (double *)malloc(sizeof(double) * (size_t)n);
+    double *Tp = (double *)malloc(sizeof(double) * (size_t)n);
+    double *Tpp = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!ck || !T || !Tp || !Tpp) {
+        free(ck); free(T); free(Tp); free(Tpp);
+        return -1;
+    }
+    orc_cheb_coeffs_interval(c, lambda_lo, M, ck);
+    double *pibar = pi;
+    for (int64_t i = 0; i < n; ++i) {
+        T[i] = p[i];
+        pibar[i] = ck[0] / 2.0 * T[i];
+    }
+    for (int k = 1; k <= M; ++k) {
+        orc_job job;
+        memset(&job, 0, sizeof(job));
+        job.n = n; job.row_ptr = row_ptr; job.col_idx = col_idx;
+        job.pibar = pibar; job.ck = ck[k]; job.mid = mid; job.half = half;
+        if (k == 1) {
+            job.kind = 3; job.T = T; job.Tpp = Tp;
+        } else {
+            job.kind = 4; job.T = T; job.Tp = Tp; job.Tpp = Tpp;
+        }
+        orc_round(job, nthreads);
         if (k >= 2) { /* rotate: T <- T', T' <- T'' */
             double *t = T; T = Tp; Tp = Tpp; Tpp = t;
         }

@@ -60,6 +60,18 @@ def configure(L):
         L.orc_power.argtypes = [_i64, _pi32, _pi32, _pf64, _dbl, _dbl, _int, _int, _pf64]
         L.orc_dense_pagerank.restype = _int
         L.orc_dense_pagerank.argtypes = [_i64, _pi32, _pi32, _pf64, _dbl, _pf64]
+        L.orc_cheb_coeffs_interval.restype = None
+        L.orc_cheb_coeffs_interval.argtypes = [_dbl, _dbl, _int, _pf64]
+        L.orc_err_bound_interval.restype = _dbl
+        L.orc_err_bound_interval.argtypes = [_dbl, _dbl, _int]
+        L.orc_l1_bound_interval.restype = _dbl
+        L.orc_l1_bound_interval.argtypes = [_dbl, _dbl, _int, _dbl, _int]
+        L.orc_rounds_needed_interval.restype = _int
+        L.orc_rounds_needed_interval.argtypes = [_dbl, _dbl, _dbl, _dbl, _int, _int]
+        L.orc_lambda_lo_loops.restype = _dbl
+        L.orc_lambda_lo_loops.argtypes = [_i64, _pi32, _pi32]
+        L.orc_cpaa_interval.restype = _int
+        L.orc_cpaa_interval.argtypes = [_i64, _pi32, _pi32, _pf64, _dbl, _dbl, _int, _int, _int, _pf64]
     return L
 
 
@@ -190,6 +202,48 @@ def solve(row_ptr, col_idx, p, c, tol, normalize=0, nthreads=None):
     return cpaa(row_ptr, col_idx, p, c, M, normalize, nthreads), M
 
 
+# -- the series on a narrower interval [lambda_lo, 1] (Sec. 2.2's general
+#    interval; see cpaa_oracle.c) ------------------------------------------------
+
+def cheb_coeffs_interval(c, lambda_lo, M):
+    out = np.empty(M + 1, dtype=np.float64)
+    lib().orc_cheb_coeffs_interval(float(c), float(lambda_lo), int(M), out.ctypes.data_as(_pf64))
+    return out
+
+
+def err_bound_interval(c, lambda_lo, M):
+    return lib().orc_err_bound_interval(float(c), float(lambda_lo), int(M))
+
+
+def l1_bound_interval(c, lambda_lo, M, kap, normalize=0):
+    return lib().orc_l1_bound_interval(float(c), float(lambda_lo), int(M), float(kap), int(normalize))
+
+
+def rounds_needed_interval(c, lambda_lo, tol, kap, normalize=0, max_rounds=10000):
+    return lib().orc_rounds_needed_interval(float(c), float(lambda_lo), float(tol), float(kap),
+                                            int(normalize), int(max_rounds))
+
+
+def lambda_lo_loops(row_ptr, col_idx):
+    """-1 + 2/d_max when every vertex has a self-loop, else -1."""
+    rp, rpp = _i32(row_ptr)
+    ci, cip = _i32(col_idx)
+    return lib().orc_lambda_lo_loops(len(rp) - 1, rpp, cip)
+
+
+def cpaa_interval(row_ptr, col_idx, p, c, lambda_lo, M, normalize=0, nthreads=None):
+    """CPAA after M rounds of the series on [lambda_lo, 1]."""
+    rp, rpp = _i32(row_ptr)
+    ci, cip = _i32(col_idx)
+    pv, pvp = _f64(p)
+    n = len(rp) - 1
+    pi = np.empty(n, dtype=np.float64)
+    if lib().orc_cpaa_interval(n, rpp, cip, pvp, float(c), float(lambda_lo), int(M), int(normalize),
+                               int(nthreads or default_threads()), pi.ctypes.data_as(_pf64)) != 0:
+        raise ValueError("orc_cpaa_interval failed")
+    return pi
+
+
 # -- numpy cross-checks (independent of the C code) ---------------------------
 
 def dense_matrix_P(row_ptr, col_idx):
@@ -240,3 +294,35 @@ def quadrature_coeffs(c, M, nodes=8192):
     w[0] = w[-1] = np.pi / (2 * nodes)
     g = 1.0 / (1.0 - c * np.cos(t))
     return np.array([(2.0 / np.pi) * np.sum(w * np.cos(k * t) * g) for k in range(M + 1)])
+
+
+def quadrature_coeffs_interval(c, lambda_lo, M, nodes=8192):
+    """c_k = (2/pi) int_0^pi f(mid + half cos t) cos(kt) dt for f(x) = 1/(1 - cx)
+    on [lambda_lo, 1] (Sec. 2.2's general interval), composite trapezoid rule;
+    independent of the reduction to 1/(1 - chat cos t) the C code uses."""
+    mid, half = 0.5 * (1.0 + lambda_lo), 0.5 * (1.0 - lambda_lo)
+    t = np.linspace(0.0, np.pi, nodes + 1)
+    w = np.full(nodes + 1, np.pi / nodes)
+    w[0] = w[-1] = np.pi / (2 * nodes)
+    g = 1.0 / (1.0 - c * (mid + half * np.cos(t)))
+    return np.array([(2.0 / np.pi) * np.sum(w * np.cos(k * t) * g) for k in range(M + 1)])
+
+
+def eig_truncation_interval(row_ptr, col_idx, p, c, lambda_lo, M, normalize=0):
+    """The exact M-term truncation on [lambda_lo, 1] through eigh of S: each
+    eigenvalue lambda enters as c_0/2 + sum_k c_k T_k((lambda - mid)/half),
+    T_k(t) = cos(k arccos t), coefficients by quadrature."""
+    _, A, d = dense_matrix_P(row_ptr, col_idx)
+    s = 1.0 / np.sqrt(d)
+    S = s[:, None] * A * s[None, :]
+    lam, U = np.linalg.eigh(S)
+    mid, half = 0.5 * (1.0 + lambda_lo), 0.5 * (1.0 - lambda_lo)
+    t = np.clip((lam - mid) / half, -1.0, 1.0)
+    ck = quadrature_coeffs_interval(c, lambda_lo, M)
+    theta = np.arccos(t)
+    f = ck[0] / 2.0 + sum(ck[k] * np.cos(k * theta) for k in range(1, M + 1))
+    q = U.T @ (s * np.asarray(p, dtype=np.float64))
+    v = np.sqrt(d) * (U @ (f * q))
+    if normalize == 0:
+        return v / v.sum()
+    return (1.0 - c) * v

@@ -47,6 +47,79 @@ MUTANTS = {
 }
 
 
+# Slips in the series on [lambda_lo, 1] (the interval form): each must fail
+# the interval pins below.
+INTERVAL_MUTANTS = {
+    "interval_first_round_no_shift": ("s = (s - j->mid * j->T[u]) / j->half;", "s = s / j->half;"),
+    "interval_later_round_no_scale": ("s = 2.0 * (s - j->mid * j->Tp[u]) / j->half - j->T[u];",
+                                      "s = 2.0 * (s - j->mid * j->Tp[u]) - j->T[u];"),
+    "interval_shift_of_older_iterate": ("s = 2.0 * (s - j->mid * j->Tp[u]) / j->half - j->T[u];",
+                                        "s = 2.0 * (s - j->mid * j->T[u]) / j->half - j->T[u];"),
+    "interval_coeff_factor_dropped": ("for (int k = 0; k <= M; ++k) ck[k] = ck[k] / (1.0 - c * mid);",
+                                      "for (int k = 0; k <= M; ++k) ck[k] = ck[k];"),
+    "interval_chat_unscaled": ("*chat = c * *half / (1.0 - c * *mid);", "*chat = c * *half;"),
+    "interval_err_tail_sign": ("pow(bh, (double)(M + 1)) / (1.0 - bh);", "pow(bh, (double)(M + 1)) / (1.0 + bh);"),
+    "loops_bound_factor": ("return -1.0 + 2.0 / (double)dmax;", "return -1.0 + 4.0 / (double)dmax;"),
+    "loops_missing_loop_ignored": ("if (!loop) return -1.0;", "if (!loop) continue;"),
+}
+
+
+def _interval_pins():
+    """The interval pins on a few cases (O._lib as it is); names that failed."""
+    from tests.test_oracle_interval_pins import lam_min, looped_graphs, with_loops
+    failed = []
+    c, lo = 0.85, -0.6
+    mid, half = 0.5 * (1 + lo), 0.5 * (1 - lo)
+    if np.abs(O.cheb_coeffs_interval(c, lo, 12) - O.quadrature_coeffs_interval(c, lo, 12)).max() > 1e-12:
+        failed.append("interval_coeffs")
+    ck = O.cheb_coeffs_interval(c, lo, 4000)
+    for M in (1, 5):
+        if abs(O.err_bound_interval(c, lo, M) - (1 - c) * ck[M + 1:].sum()) > 1e-12:
+            failed.append("interval_err")
+            break
+    for g in looped_graphs()[:4]:
+        rp, cx = g.numpy()
+        l = O.lambda_lo_loops(rp, cx)
+        if not (lam_min(g) >= l - 1e-12) or l != -1.0 + 2.0 / np.diff(rp).max():
+            failed.append("interval_certified")
+        p = np.zeros(g.n)
+        p[g.n // 2] = 1.0
+        for M in (1, 2, 5):
+            if np.abs(O.cpaa_interval(rp, cx, p, c, l, M) - O.eig_truncation_interval(rp, cx, p, c, l, M)).sum() > 1e-12:
+                failed.append("interval_eig")
+    g = with_loops(ci.cycle(5))
+    rp, cx = g.numpy()
+    rows = np.repeat(np.arange(g.n), np.diff(rp))
+    keep = ~((rows == 2) & (cx == 2))
+    rp2, cx2 = ci.from_edges(g.n, np.stack([rows[keep], cx[keep]], 1)).numpy()
+    if O.lambda_lo_loops(rp2, cx2) != -1.0:
+        failed.append("interval_no_loop")
+    return failed
+
+
+def test_unmutated_oracle_passes_interval_pins():
+    assert _interval_pins() == []
+
+
+@pytest.mark.parametrize("name", sorted(INTERVAL_MUTANTS))
+def test_planted_mistake_in_interval_form_is_caught(name, tmp_path):
+    old, new = INTERVAL_MUTANTS[name]
+    src = open(B.SRC).read()
+    assert src.count(old) == 1, "mutation anchor not unique: " + name
+    path = tmp_path / "mutant.c"
+    path.write_text(src.replace(old, new))
+    so = tmp_path / "libmutant.so"
+    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off",
+                    "-o", str(so), str(path), "-lm", "-lpthread"], check=True)
+    saved = O._lib
+    try:
+        O._lib = O.configure(ctypes.CDLL(str(so)))
+        failed = _interval_pins()
+    finally:
+        O._lib = saved
+    assert failed, "planted mistake %r passed every interval pin" % name
+
+
 def _pins():
     """Run the core pins against whatever library O._lib holds; return the
     names of the pins that failed."""
