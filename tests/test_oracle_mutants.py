@@ -37,8 +37,10 @@ MUTANTS = {
                            "a[i * n + j] -= c / (double)(row_ptr[i + 1] - row_ptr[i]);"),
     "power_restart": ("job.T = x; job.Tpp = y; job.c = c; job.p = p;",
                       "job.T = p; job.Tpp = y; job.c = c; job.p = p;"),
-    "bound_normalisation_term_dropped": ("return E * kappa + (1.0 + E * kappa) * E / (1.0 - E);",
-                                         "return E * kappa;"),
+    "bound_normalisation_term_dropped": (
+        "double E = orc_err_bound(c, M);\n    if (normalize == 1) return E * kappa;\n"
+        "    return E * kappa + (1.0 + E * kappa) * E / (1.0 - E);",
+        "double E = orc_err_bound(c, M);\n    if (normalize == 1) return E * kappa;\n    return E * kappa;"),
     "rounds_needed_one_late": ("if (orc_l1_bound(c, M, kappa, normalize) < tol) return M;",
                                "if (orc_l1_bound(c, M, kappa, normalize) < tol) return M + 1;"),
     "power_stop_without_factor": ("if (c / (1.0 - c) * diff < tol) break;", "if (diff < tol) break;"),
@@ -174,13 +176,31 @@ def test_unmutated_oracle_passes_core_pins():
     assert _pins() == []
 
 
+def _interval_spans(src):
+    """Where the interval form's code sits (its two worker branches and its
+    section): the core mutants are planted outside these spans, where lines
+    the interval copy repeats appear once."""
+    a = src.index("} else if (j->kind == 3) {")
+    b = src.index("    return NULL;", a)
+    c = src.index("/* Chebyshev series on a narrower interval")
+    d = src.index("/* Power method (the paper's SPI baseline")
+    return [(a, b), (c, d)]
+
+
+def _plant_outside_interval(src, old, new, name):
+    spans = _interval_spans(src)
+    hits = [i for i in range(len(src)) if src.startswith(old, i) and not any(a <= i < b for a, b in spans)]
+    assert len(hits) == 1, "mutation anchor not unique: " + name
+    i = hits[0]
+    return src[:i] + new + src[i + len(old):]
+
+
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_planted_mistake_is_caught(name, tmp_path):
     old, new = MUTANTS[name]
     src = open(B.SRC).read()
-    assert src.count(old) == 1, "mutation anchor not unique: " + name
     path = tmp_path / "mutant.c"
-    path.write_text(src.replace(old, new))
+    path.write_text(_plant_outside_interval(src, old, new, name))
     so = tmp_path / "libmutant.so"
     subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off",
                     "-o", str(so), str(path), "-lm", "-lpthread"], check=True)
