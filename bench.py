@@ -202,9 +202,13 @@ def measured_peak_gbs():
 
 
 def step_kernel_hash():
-    src = os.path.join(ROOT, "paper_2112_01743_gb300", "csrc", "step.cu")
-    with open(src, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """Hash of the round kernel's source (its implementation header and the
+    per-row arithmetic it includes)."""
+    h = hashlib.sha256()
+    for name in ("step_impl.cuh", "device_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2112_01743_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def profiled_traffic(prec, wl):
@@ -216,7 +220,7 @@ def profiled_traffic(prec, wl):
     except OSError:
         return None
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    h = re.search(r"step_cu_sha256_16:\s*([0-9a-f]+)", txt)
+    h = re.search(r"kernel_src_sha256_16:\s*([0-9a-f]+)", txt)
     if not m or not h or h.group(1) != step_kernel_hash():
         return None
     return float(m.group(1))

@@ -89,6 +89,11 @@ typedef enum { CPAA_F64 = 0, CPAA_F32 = 1, CPAA_BF16 = 2, CPAA_DF64 = 3 } cpaa_p
                                    rounds have run; results are the same bits as without it.
                                    cpaa_solve, cpaa_solve_batch and cpaa_server_create (not
                                    with CPAA_SERVER_FUSED); ignored by cpaa_power_solve */
+#define CPAA_INTERVAL 16u /* run the series on [cpaa_options.lambda_lo, 1]: the caller
+                             certifies that every eigenvalue of P is >= lambda_lo */
+#define CPAA_CERTIFY_INTERVAL 32u /* run it on [b, 1] with b the lower bound the graph
+                                     certifies by itself (cpaa_graph_spectrum_bound); with
+                                     CPAA_INTERVAL too, the larger of b and lambda_lo */
 #define CPAA_SERVER_FUSED 4u /* cpaa_server_create: all graphs on one stream, each round of
                                 every graph with live queries in one kernel launch over the
                                 graphs' work lists, instead of one stream and one launch per
@@ -120,7 +125,8 @@ typedef struct {
     int fixed_rounds;         /* > 0: run exactly this many rounds (Algorithm 1's M) and
                                  ignore tol; 0: choose M from tol (default) */
     int max_rounds;           /* cap on M; 0 means 2000 */
-    unsigned flags;           /* CPAA_DEVICE_IO | CPAA_TIME_ROUNDS | CPAA_SPARSE_FRONTIER */
+    unsigned flags;           /* CPAA_DEVICE_IO | CPAA_TIME_ROUNDS | CPAA_SPARSE_FRONTIER |
+                                 CPAA_INTERVAL | CPAA_CERTIFY_INTERVAL */
     void *stream;             /* cudaStream_t to run on; NULL = legacy default stream */
     double *history;          /* optional host array [2*(M+1)]: sum T_k and sum |T_k|
                                  for k = 0..M (the mass view of Sec. 4.1); cpaa_solve only */
@@ -129,6 +135,17 @@ typedef struct {
                                  graph times a few rounds at every width on its own columns
                                  and keeps the fastest per column for that graph */
     cpaa_stop_rule stop_rule; /* default CPAA_STOP_RIGOROUS; cpaa_solve and cpaa_solve_batch */
+    double lambda_lo;         /* with CPAA_INTERVAL: the lower end of an interval [lambda_lo, 1]
+                                 that holds every eigenvalue of P (they are real and >= -1,
+                                 Lemma 2); default -1, read only under that flag.  The series
+                                 of Sec. 2.2 then runs on the narrower interval: the recurrence
+                                 on Q = (P - mid I) / half (mid, half the interval's centre and
+                                 half-width) with coefficients c_k(chat) / (1 - c mid),
+                                 chat = c half / (1 - c mid) < c, so it converges faster and
+                                 fewer rounds reach tol.  Must lie in [-1, 1).  A value above
+                                 the true smallest eigenvalue gives wrong results: it must be
+                                 a proven bound.  cpaa_solve and cpaa_solve_batch; the server
+                                 rejects both interval flags and the power method ignores them */
 } cpaa_options;
 
 typedef struct {
@@ -140,6 +157,7 @@ typedef struct {
     double l1;        /* sum_u |T_M[u]| */
     double sum_pibar; /* sum_u pibar[u] before normalisation */
     double rounds_ms; /* device time of the M round launches (CPAA_TIME_ROUNDS), else 0 */
+    double lambda_lo; /* lower end of the interval the series ran on (-1: Algorithm 1's) */
 } cpaa_info;
 
 typedef struct cpaa_graph cpaa_graph;
@@ -378,6 +396,23 @@ int cpaa_rounds_needed(double c, double tol, double kappa, int normalize, int ma
 
 /* The bound itself for a given M. */
 double cpaa_l1_bound(double c, int M, double kappa, int normalize);
+
+/* The same two for the series on [lambda_lo, 1] (cpaa_options.lambda_lo): Eq. 41's
+ * ERR_M becomes the mass the truncated interval series leaves out,
+ * (1 - c) sum_{k>M} c_k, which kappa turns into an L1 bound as before (Q is
+ * similar to a symmetric matrix whose spectrum lies in [-1, 1]).  lambda_lo =
+ * -1 gives the functions above.  -1 (rounds) or NaN (bound) for arguments out
+ * of range. */
+int cpaa_rounds_needed_interval(double c, double lambda_lo, double tol, double kappa, int normalize,
+                                int max_rounds);
+double cpaa_l1_bound_interval(double c, double lambda_lo, int M, double kappa, int normalize);
+
+/* The lower bound on P's spectrum that the graph certifies by itself: with a
+ * self-loop on every vertex, D' + A' (the loop-free degree and adjacency
+ * matrices) is positive semidefinite, so A + D >= 2I and every eigenvalue of
+ * D^-1/2 A D^-1/2 is at least -1 + 2 / d_max; otherwise -1 (Lemma 2's).  No
+ * paper counterpart: the paper's series is on [-1, 1]. */
+cpaa_status cpaa_graph_spectrum_bound(const cpaa_graph *g, double *lambda_lo);
 
 /* Human-readable name of a status. */
 const char *cpaa_status_string(cpaa_status s);

@@ -16,7 +16,9 @@ __all__ = [
     "CPAA_EBUSY", "CPAA_ECANCELLED", "CPAA_ENOTFOUND",
     "CPAA_F64", "CPAA_F32", "CPAA_BF16", "CPAA_DF64", "CPAA_GRAPH_DEVICE_INPUT", "CPAA_GRAPH_VALIDATE",
     "CPAA_GRAPH_TRUSTED", "CPAA_GRAPH_AUTOTUNE", "CpaaLayoutParams", "cpaa_graph_create_ex",
-    "CPAA_DEVICE_IO", "CPAA_TIME_ROUNDS", "CPAA_SERVER_FUSED", "CPAA_SPARSE_FRONTIER", "CPAA_STOP_RIGOROUS",
+    "CPAA_DEVICE_IO", "CPAA_TIME_ROUNDS", "CPAA_SERVER_FUSED", "CPAA_SPARSE_FRONTIER", "CPAA_INTERVAL",
+    "CPAA_CERTIFY_INTERVAL", "cpaa_rounds_needed_interval", "cpaa_l1_bound_interval", "cpaa_graph_spectrum_bound",
+    "CPAA_STOP_RIGOROUS",
     "CPAA_STOP_POSTERIORI",
     "cpaa_options_init", "cpaa_graph_create", "cpaa_graph_destroy", "cpaa_graph_info", "cpaa_graph_layout",
     "CpaaLayout", "cpaa_solve", "cpaa_solve_batch", "cpaa_rounds_needed", "cpaa_l1_bound",
@@ -36,6 +38,8 @@ CPAA_SERVER_MAX_SEEDS = 64
 CPAA_TIME_ROUNDS = 2
 CPAA_SERVER_FUSED = 4
 CPAA_SPARSE_FRONTIER = 8
+CPAA_INTERVAL = 16
+CPAA_CERTIFY_INTERVAL = 32
 CPAA_STOP_RIGOROUS, CPAA_STOP_POSTERIORI = 0, 1
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -48,6 +52,7 @@ EXPORTED_SYMBOLS = [
     "cpaa_status_string", "cpaa_last_error", "cpaa_solve_fixed_noalloc", "cpaa_power_solve",
     "cpaa_server_create", "cpaa_server_add_graph", "cpaa_server_submit", "cpaa_server_wait",
     "cpaa_server_cancel", "cpaa_server_get_stats", "cpaa_server_destroy",
+    "cpaa_rounds_needed_interval", "cpaa_l1_bound_interval", "cpaa_graph_spectrum_bound",
 ]
 
 
@@ -75,13 +80,13 @@ class CpaaOptions(ctypes.Structure):
                 ("fixed_rounds", ctypes.c_int), ("max_rounds", ctypes.c_int),
                 ("flags", ctypes.c_uint), ("stream", ctypes.c_void_p),
                 ("history", ctypes.POINTER(ctypes.c_double)), ("batch_width", ctypes.c_int),
-                ("stop_rule", ctypes.c_int)]
+                ("stop_rule", ctypes.c_int), ("lambda_lo", ctypes.c_double)]
 
 
 class CpaaInfo(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_int), ("bound", ctypes.c_double), ("kappa", ctypes.c_double),
                 ("mass", ctypes.c_double), ("l1", ctypes.c_double), ("sum_pibar", ctypes.c_double),
-                ("rounds_ms", ctypes.c_double)]
+                ("rounds_ms", ctypes.c_double), ("lambda_lo", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -152,6 +157,12 @@ def lib():
     L.cpaa_server_get_stats.argtypes = [vp, ctypes.POINTER(CpaaServerStats)]
     L.cpaa_server_destroy.restype = cint
     L.cpaa_server_destroy.argtypes = [vp]
+    L.cpaa_rounds_needed_interval.restype = cint
+    L.cpaa_rounds_needed_interval.argtypes = [dbl, dbl, dbl, dbl, cint, cint]
+    L.cpaa_l1_bound_interval.restype = dbl
+    L.cpaa_l1_bound_interval.argtypes = [dbl, dbl, cint, dbl, cint]
+    L.cpaa_graph_spectrum_bound.restype = cint
+    L.cpaa_graph_spectrum_bound.argtypes = [vp, ctypes.POINTER(dbl)]
     L.cpaa_status_string.restype = ctypes.c_char_p
     L.cpaa_status_string.argtypes = [cint]
     L.cpaa_last_error.restype = ctypes.c_char_p
@@ -241,8 +252,11 @@ def cpaa_graph_info(g):
 
 
 def _options(precision, normalize, fixed_rounds, max_rounds, device_io, stream, history,
-             time_rounds=False, stop_rule=CPAA_STOP_RIGOROUS, frontier=False):
+             time_rounds=False, stop_rule=CPAA_STOP_RIGOROUS, frontier=False, lambda_lo=None,
+             certify_interval=False):
     o = cpaa_options_init()
+    if lambda_lo is not None:
+        o.lambda_lo = float(lambda_lo)
     o.stop_rule = int(stop_rule)
     o.precision = int(precision)
     o.normalize = int(normalize)
@@ -250,7 +264,8 @@ def _options(precision, normalize, fixed_rounds, max_rounds, device_io, stream, 
     if max_rounds:
         o.max_rounds = int(max_rounds)
     o.flags = (CPAA_DEVICE_IO if device_io else 0) | (CPAA_TIME_ROUNDS if time_rounds else 0) | \
-        (CPAA_SPARSE_FRONTIER if frontier else 0)
+        (CPAA_SPARSE_FRONTIER if frontier else 0) | (CPAA_INTERVAL if lambda_lo is not None else 0) | \
+        (CPAA_CERTIFY_INTERVAL if certify_interval else 0)
     o.stream = stream
     if history is not None:
         o.history = history.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
@@ -268,13 +283,15 @@ def _stream_of(x, stream):
 
 def cpaa_solve(g, p, c, tol, pi, precision=CPAA_F64, normalize=0, fixed_rounds=0, max_rounds=0,
                stream=None, history=None, raise_notconv=True, time_rounds=False,
-               stop_rule=CPAA_STOP_RIGOROUS, frontier=False):
-    """pi <- CPAA(p); p, pi FP64 length n (both host or both device)."""
+               stop_rule=CPAA_STOP_RIGOROUS, frontier=False, lambda_lo=None, certify_interval=False):
+    """pi <- CPAA(p); p, pi FP64 length n (both host or both device).
+    lambda_lo (a certified lower bound on P's spectrum) sets CPAA_INTERVAL;
+    certify_interval sets CPAA_CERTIFY_INTERVAL."""
     dev = _is_device(p)
     if dev != _is_device(pi):
         raise ValueError("p and pi must both be host or both be device buffers")
     o = _options(precision, normalize, fixed_rounds, max_rounds, dev, _stream_of(p, stream), history,
-                 time_rounds, stop_rule, frontier)
+                 time_rounds, stop_rule, frontier, lambda_lo, certify_interval)
     info = CpaaInfo()
     st = lib().cpaa_solve(g, _addr(p), float(c), float(tol), _addr(pi), ctypes.byref(o), ctypes.byref(info))
     _check(st, raise_notconv)
@@ -299,13 +316,13 @@ def cpaa_power_solve(g, p, c, tol, pi, precision=CPAA_F64, normalize=0, fixed_ro
 
 def cpaa_solve_batch(g, B, P, c, tol, PI, precision=CPAA_F32, normalize=0, fixed_rounds=0,
                      max_rounds=0, stream=None, raise_notconv=True, batch_width=0,
-                     stop_rule=CPAA_STOP_RIGOROUS, frontier=False):
+                     stop_rule=CPAA_STOP_RIGOROUS, frontier=False, lambda_lo=None, certify_interval=False):
     """Column b of P (n x B column-major, i.e. B vectors back to back) with
     damping c[b] -> column b of PI.  Returns a list of B info records."""
     dev = _is_device(P)
     cvec = np.ascontiguousarray(np.broadcast_to(np.asarray(c, dtype=np.float64), (int(B),)))
     o = _options(precision, normalize, fixed_rounds, max_rounds, dev, _stream_of(P, stream), None,
-                 False, stop_rule, frontier)
+                 False, stop_rule, frontier, lambda_lo, certify_interval)
     o.batch_width = int(batch_width)
     infos = (CpaaInfo * int(B))()
     st = lib().cpaa_solve_batch(g, int(B), _addr(P), cvec.ctypes.data, float(tol), _addr(PI),
@@ -424,6 +441,21 @@ def cpaa_l1_bound(c, M, kappa, normalize=0):
     return lib().cpaa_l1_bound(float(c), int(M), float(kappa), int(normalize))
 
 
+def cpaa_rounds_needed_interval(c, lambda_lo, tol, kappa, normalize=0, max_rounds=2000):
+    return lib().cpaa_rounds_needed_interval(float(c), float(lambda_lo), float(tol), float(kappa),
+                                             int(normalize), int(max_rounds))
+
+
+def cpaa_l1_bound_interval(c, lambda_lo, M, kappa, normalize=0):
+    return lib().cpaa_l1_bound_interval(float(c), float(lambda_lo), int(M), float(kappa), int(normalize))
+
+
+def cpaa_graph_spectrum_bound(g):
+    v = ctypes.c_double()
+    _check(lib().cpaa_graph_spectrum_bound(g, ctypes.byref(v)))
+    return v.value
+
+
 def cpaa_status_string(s):
     return lib().cpaa_status_string(int(s)).decode()
 
@@ -453,6 +485,9 @@ class Graph:
 
     def layout(self):
         return cpaa_graph_layout(self.handle)
+
+    def spectrum_bound(self):
+        return cpaa_graph_spectrum_bound(self.handle)
 
     def solve(self, p, c, tol, pi, **kw):
         return cpaa_solve(self.handle, p, c, tol, pi, **kw)

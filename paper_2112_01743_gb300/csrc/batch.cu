@@ -114,6 +114,8 @@ extern "C" cpaa_status cpaa_solve_batch(cpaa_graph *g, int B, const double *P, c
     std::vector<double> hs(3 * (size_t)B);
     CPAA_CUDA(cudaMemcpyAsync(hs.data(), dstats, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost, st));
     CPAA_CUDA(cudaStreamSynchronize(st));
+    double lo = -1.0;
+    if ((s = resolve_interval(g, opt, &lo)) != CPAA_OK) return s;
     std::vector<double> kappa(B);
     std::vector<int> M(B);
     std::vector<char> notconv(B, 0);
@@ -122,7 +124,7 @@ extern "C" cpaa_status cpaa_solve_batch(cpaa_graph *g, int B, const double *P, c
             return fail(s, "column " + std::to_string(b) + ": " + cpaa_last_error());
         M[b] = opt.fixed_rounds;
         if (M[b] == 0) {
-            M[b] = cpaa_rounds_needed(c[b], tol, kappa[b], opt.normalize, max_rounds);
+            M[b] = cpaa_rounds_needed_interval(c[b], lo, tol, kappa[b], opt.normalize, max_rounds);
             if (M[b] < 0) {
                 M[b] = max_rounds;
                 notconv[b] = 1;
@@ -160,11 +162,12 @@ extern "C" cpaa_status cpaa_solve_batch(cpaa_graph *g, int B, const double *P, c
         job.normalize = opt.normalize;
         job.posteriori = opt.stop_rule == CPAA_STOP_POSTERIORI && opt.fixed_rounds == 0;
         job.frontier = (opt.flags & CPAA_SPARSE_FRONTIER) != 0;
+        job.lambda_lo = lo;
         job.tol = tol;
         for (int j = 0; j < tw; ++j) {
             const int b = order[t0 + j];
             std::vector<double> ck0;
-            cheb_coeffs(c[b], 0, ck0);
+            cheb_coeffs_on(c[b], lo, 0, ck0);
             job.p[j] = dP + (size_t)b * n;
             job.pi[j] = dPI + (size_t)b * n;
             job.c[j] = c[b];
@@ -205,10 +208,11 @@ extern "C" cpaa_status cpaa_solve_batch(cpaa_graph *g, int B, const double *P, c
                         round_sums(tw, j, k, h, &t, &a);
                         ml = std::max(ml, a);
                     }
-                    in.bound = cpaa_l1_bound(c[b], M[b], 2.0 * ml, opt.normalize);
+                    in.bound = cpaa_l1_bound_interval(c[b], lo, M[b], 2.0 * ml, opt.normalize);
                 } else {
-                    in.bound = cpaa_l1_bound(c[b], M[b], kappa[b], opt.normalize);
+                    in.bound = cpaa_l1_bound_interval(c[b], lo, M[b], kappa[b], opt.normalize);
                 }
+                in.lambda_lo = lo;
                 round_sums(tw, j, M[b], h, &in.mass, &in.l1);
                 in.sum_pibar = w.h_sums[j];
                 in.rounds_ms = 0.0;

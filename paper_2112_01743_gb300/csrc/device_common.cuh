@@ -132,6 +132,24 @@ __device__ __forceinline__ typename Prec<P>::A new_iterate(typename Prec<P>::A s
     return round_y(y, (const S *)nullptr);
 }
 
+// The same on the interval [lambda_lo, 1] (Sec. 2.2's general interval): the
+// recurrence on Q = (P - mid I) / half, scaled by D^-1 like the rest, with
+// ia = 1 / half, ib = mid / half and y_cur the row's current iterate y_k[u]:
+//   k = 1:  y_1 = ia (s / d) - ib y_0
+//   k >= 2: y_{k+1} = ia (2 s / d) - 2 ib y_k - y_{k-1}.
+template <int P, class S = typename Prec<P>::S>
+__device__ __forceinline__ typename Prec<P>::A interval_iterate(typename Prec<P>::A s, typename Prec<P>::A inv2,
+                                                                typename Prec<P>::A y_cur,
+                                                                typename Prec<P>::A y_old, int first,
+                                                                typename Prec<P>::A ia,
+                                                                typename Prec<P>::A ib) {
+    using A = typename Prec<P>::A;
+    const A t = mul_rn(s, inv2);
+    const A y = first ? fma_rn(mul_rn(t, A(0.5)), ia, -mul_rn(ib, y_cur))
+                      : fma_rn(t, ia, -fma_rn(add_rn(ib, ib), y_cur, y_old));
+    return round_y(y, (const S *)nullptr);
+}
+
 // One power-method round in scaled space (the paper's SPI baseline, Sec. 5.1):
 // x' = c P x + (1 - c) p  ->  y' = c s / d + q,  q = (1 - c) p / d.
 template <int P, class S = typename Prec<P>::S>

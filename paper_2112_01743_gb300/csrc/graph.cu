@@ -105,9 +105,11 @@ __global__ void build_sell_kernel(const int32_t *__restrict__ row_ptr,
                                   const int32_t *__restrict__ rcol,
                                   const int32_t *__restrict__ perm, int64_t n, int n_hub,
                                   int num_chunks, const int64_t *__restrict__ chunk_off,
-                                  const int32_t *__restrict__ chunk_len, int32_t *sell) {
+                                  const int32_t *__restrict__ chunk_len, int32_t *sell,
+                                  unsigned long long *loops) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long nloop = 0;
     for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < num_chunks;
          c += nwarps) {
         const int64_t r = n_hub + c * kChunkRows + lane;
@@ -119,10 +121,15 @@ __global__ void build_sell_kernel(const int32_t *__restrict__ row_ptr,
         }
         const int64_t off = chunk_off[c];
         const int len = chunk_len[c];
-        for (int i = 0; i < len; ++i)
-            sell[off + (int64_t)(i / kSellVec) * (kChunkRows * kSellVec) + lane * kSellVec + i % kSellVec] =
-                (i < d) ? rcol[e0 + i] : (int32_t)n;
+        bool loop = false;
+        for (int i = 0; i < len; ++i) {
+            const int32_t v = (i < d) ? rcol[e0 + i] : (int32_t)n;
+            loop |= (i < d && v == r);
+            sell[off + (int64_t)(i / kSellVec) * (kChunkRows * kSellVec) + lane * kSellVec + i % kSellVec] = v;
+        }
+        nloop += loop ? 1 : 0;
     }
+    if (nloop) atomicAdd(loops, nloop);  // rows with a self-loop
 }
 
 // One CTA per hub row: a copy of its relabelled, sorted entries.
@@ -130,12 +137,16 @@ __global__ void build_hub_kernel(const int32_t *__restrict__ row_ptr,
                                  const int32_t *__restrict__ rcol,
                                  const int32_t *__restrict__ perm,
                                  const int32_t *__restrict__ hub_row_ptr, int n_hub,
-                                 int32_t *hub_col) {
+                                 int32_t *hub_col, unsigned long long *loops) {
     for (int h = blockIdx.x; h < n_hub; h += gridDim.x) {
         const int32_t u = perm[h];
         const int e0 = row_ptr[u], d = row_ptr[u + 1] - e0;
         const int o = hub_row_ptr[h];
-        for (int i = threadIdx.x; i < d; i += blockDim.x) hub_col[o + i] = rcol[e0 + i];
+        for (int i = threadIdx.x; i < d; i += blockDim.x) {
+            const int32_t v = rcol[e0 + i];
+            hub_col[o + i] = v;
+            if (v == h) atomicAdd(loops, 1ull);  // the row's self-loop (a row holds each id once)
+        }
     }
 }
 
@@ -300,6 +311,7 @@ static cpaa_status build_graph(int64_t n, int64_t nnz, const int32_t *row_ptr, c
     cpaa_status st;
     int32_t *d_rp = nullptr, *d_ci = nullptr, *d_inv = nullptr, *d_rs = nullptr;
     unsigned long long *d_bad = nullptr;  // [0..2] validate_kernel, [3] relabel_kernel
+    unsigned long long *d_loops = nullptr;  // rows with a self-loop
     void *d_tmp = nullptr;
     size_t rp_bytes = sizeof(int32_t) * (n + 1), ci_bytes = sizeof(int32_t) * nnz, tmp_bytes = 0;
 #define ALLOC(ptr, bytes)                                                      \
@@ -393,6 +405,8 @@ static cpaa_status build_graph(int64_t n, int64_t nnz, const int32_t *row_ptr, c
         d_ci = d_rs;
         d_rs = nullptr;
 
+        ALLOC(d_loops, sizeof(unsigned long long));
+        CK(cudaMemset(d_loops, 0, sizeof(unsigned long long)));
         ALLOC(g->hub_row_ptr, sizeof(int32_t) * (L.n_hub + 1));
         CK(cudaMemcpy(g->hub_row_ptr, L.hub_row_ptr.data(), sizeof(int32_t) * (L.n_hub + 1),
                       cudaMemcpyHostToDevice));
@@ -400,7 +414,7 @@ static cpaa_status build_graph(int64_t n, int64_t nnz, const int32_t *row_ptr, c
         CK(cudaMemset(g->hub_col, 0, sizeof(int32_t) * (g->hub_nnz + 4)));
         if (L.n_hub > 0) {
             build_hub_kernel<<<std::min(L.n_hub, 4096), 256>>>(d_rp, d_ci, g->perm, g->hub_row_ptr, L.n_hub,
-                                                                g->hub_col);
+                                                                g->hub_col, d_loops);
             CK(cudaGetLastError());
         }
         ALLOC(g->hub_tiles, sizeof(int4) * std::max<size_t>(1, L.hub_tiles.size()));
@@ -424,10 +438,19 @@ static cpaa_status build_graph(int64_t n, int64_t nnz, const int32_t *row_ptr, c
             CK(cudaMemcpy(g->chunk_desc, L.chunk_desc.data(), sizeof(int4) * g->num_chunks,
                           cudaMemcpyHostToDevice));
             build_sell_kernel<<<(unsigned)std::min<int64_t>(((int64_t)g->num_chunks * 32 + 255) / 256, 16384), 256>>>(
-                d_rp, d_ci, g->perm, n, L.n_hub, g->num_chunks, g->chunk_off, g->chunk_len, g->sell_col);
+                d_rp, d_ci, g->perm, n, L.n_hub, g->num_chunks, g->chunk_off, g->chunk_len, g->sell_col, d_loops);
             CK(cudaGetLastError());
         }
         CK(cudaDeviceSynchronize());
+        {
+            unsigned long long nl = 0;
+            CK(cudaMemcpy(&nl, d_loops, sizeof(nl), cudaMemcpyDeviceToHost));
+            g->loops_all = (int64_t)nl == n;
+            int dmax = 0;
+            for (int64_t u = 0; u < n; ++u) dmax = std::max(dmax, hrp[u + 1] - hrp[u]);
+            g->dmax = dmax;
+        }
+        dev_free(g, (void **)&d_loops, sizeof(unsigned long long));
         dev_free(g, (void **)&d_inv, sizeof(int32_t) * n);
         dev_free(g, (void **)&d_ci, ci_bytes);
         dev_free(g, (void **)&d_rp, rp_bytes);
@@ -436,6 +459,7 @@ static cpaa_status build_graph(int64_t n, int64_t nnz, const int32_t *row_ptr, c
     }
 fail_out:
     if (d_bad) dev_free(g, (void **)&d_bad, 4 * sizeof(unsigned long long));
+    if (d_loops) dev_free(g, (void **)&d_loops, sizeof(unsigned long long));
     if (d_tmp) dev_free(g, &d_tmp, std::max<size_t>(tmp_bytes, 16));
     if (d_rs) dev_free(g, (void **)&d_rs, ci_bytes);
     if (d_inv) dev_free(g, (void **)&d_inv, sizeof(int32_t) * n);
@@ -701,6 +725,22 @@ extern "C" cpaa_status cpaa_graph_layout(const cpaa_graph *g, cpaa_layout *out) 
     out->sort_window = g->lp.sort_window;
     out->tuned = g->tuned;
     out->tune_candidates = g->tune_candidates;
+    return CPAA_OK;
+}
+
+namespace cpaa {
+// Every vertex with a self-loop makes D' + A' (the loop-free degree and
+// adjacency matrices) positive semidefinite, so A + D >= 2I and
+// D^-1/2 A D^-1/2 + I >= 2 D^-1 >= (2 / d_max) I.
+double graph_lambda_lo(const cpaa_graph *g) {
+    return g->loops_all && g->dmax > 0 ? -1.0 + 2.0 / (double)g->dmax : -1.0;
+}
+}  // namespace cpaa
+
+extern "C" cpaa_status cpaa_graph_spectrum_bound(const cpaa_graph *g, double *lambda_lo) {
+    clear_error();
+    if (!g || !lambda_lo) return fail(CPAA_EINVAL, "graph or lambda_lo is NULL");
+    *lambda_lo = graph_lambda_lo(g);
     return CPAA_OK;
 }
 

@@ -198,6 +198,7 @@ struct TileJob {
     int rounds[kMaxWidth] = {};
     int power = 0;                    // 1: power-method rounds instead of Chebyshev ones
     int frontier = 0;                 // 1: early rounds on the sparse frontier (CPAA_SPARSE_FRONTIER)
+    double lambda_lo = -1.0;          // the series' interval [lambda_lo, 1] (-1: Algorithm 1's)
     int posteriori = 0;               // 1: columns may stop early by the a-posteriori rule
     double tol = 0;                   // its tolerance
     double p_l1[kMaxWidth] = {};      // ||p||_1 = ||T_0 p||_1 of each column (that rule's start)
@@ -244,6 +245,8 @@ struct cpaa_graph {
     int hub_tile = cpaa::kMaxHubTile;   // entries of a hub tile
     int num_long_chunks = 0;         // leading chunk_order entries longer than lp.long_chunk
     cpaa::LayoutParams lp;           // the layout's parameters (hub_degree, hub_tile as above)
+    int loops_all = 0;               // 1: every vertex has a self-loop
+    int dmax = 0;                    // largest degree
     int tuned = 0;                   // 1: lp picked by timing candidates (CPAA_GRAPH_AUTOTUNE)
     int tune_candidates = 0;         // layouts timed to pick it
     // per-vertex, new order
@@ -284,6 +287,19 @@ double err_bound(double c, int M);
 // Host-side coefficient table c_0..c_M (Sec. 2.2, Proposition 1).
 void cheb_coeffs(double c, int M, std::vector<double> &ck);
 
+// The series on [lo, 1] (cpaa_options.lambda_lo; status.cpp): centre, half-width,
+// the reduced damping chat and the coefficient scale 1 / (1 - c mid).
+struct IntervalMap {
+    double mid, half, chat, scale;
+};
+IntervalMap interval_map(double c, double lo);
+void cheb_coeffs_on(double c, double lo, int M, std::vector<double> &ck);  // lo = -1: cheb_coeffs
+double err_bound_on(double c, double lo, int M);                           // lo = -1: err_bound
+// The graph's own certified lower end (-1 + 2 / d_max with a loop on every
+// vertex, else -1; graph.cu), and the interval a solve runs on (solve.cu).
+double graph_lambda_lo(const cpaa_graph *g);
+cpaa_status resolve_interval(const cpaa_graph *g, const cpaa_options &opt, double *lo);
+
 // Round launcher (step.cu): one round for a tile of `width` vectors.
 struct StepLaunch {
     const cpaa_graph *g = nullptr;
@@ -304,6 +320,8 @@ struct StepLaunch {
     unsigned reduce = 0;            // nonzero: take this round's sums
     unsigned first = 0;             // columns in their first round (k == 1)
     int power = 0;                  // 1: power-method round (ck[b] = c, rho holds q = (1-c) p / d)
+    int interval = 0;               // 1: the recurrence on Q = (P - mid I) / half
+    double ia = 1.0, ib = 0.0;      // its 1 / half and mid / half
     int *long_cnt = nullptr;        // hub ticket counters [n_hub], all zero; NULL = the graph's own
     // sparse frontier (NULL: every item): items whose rows are all outside
     // front are skipped, unless *front_full or *front_entries > front_limit
@@ -314,7 +332,11 @@ struct StepLaunch {
     int front_hub_words = 0;
     cudaStream_t stream = nullptr;
 };
-void prepare_step(int precision, int width);
+void prepare_step(int precision, int width, bool interval = false);
+// The series on [lambda_lo, 1] (step_interval.cu; launch_step forwards there
+// when StepLaunch::interval is set).
+void prepare_step_interval(int precision, int width);
+cudaError_t launch_step_interval(const StepLaunch &s);
 
 // Sparse-frontier pieces (frontier.cu).  ensure_frontier allocates f for g
 // (frontier_bytes of device memory, counted in track's device_bytes);

@@ -836,6 +836,8 @@ extern "C" cpaa_status cpaa_server_create(size_t device_mem_budget, const cpaa_o
     if (o.normalize != 0 && o.normalize != 1) return fail(CPAA_EINVAL, "normalize must be 0 or 1");
     if (o.stop_rule != CPAA_STOP_RIGOROUS && o.stop_rule != CPAA_STOP_POSTERIORI)
         return fail(CPAA_EINVAL, "unknown stop_rule");
+    if (o.flags & (CPAA_INTERVAL | CPAA_CERTIFY_INTERVAL))
+        return fail(CPAA_EINVAL, "the server runs the series on [-1, 1] only (no CPAA_INTERVAL / CPAA_CERTIFY_INTERVAL)");
     cpaa_server *s = new cpaa_server();
     s->posteriori = o.stop_rule == CPAA_STOP_POSTERIORI;
     s->fused = (o.flags & CPAA_SERVER_FUSED) != 0;

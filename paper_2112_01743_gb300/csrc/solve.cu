@@ -336,7 +336,9 @@ static cudaError_t launch_rounds(cpaa_graph *g, const TileJob &job, bool history
     Workspace &w = g->ws;
     const int W = job.width;
     std::vector<std::vector<double>> ck(W);
-    for (int b = 0; b < W; ++b) cheb_coeffs(job.c[b], job.rounds[b], ck[b]);
+    for (int b = 0; b < W; ++b) cheb_coeffs_on(job.c[b], job.lambda_lo, job.rounds[b], ck[b]);
+    const bool interval = job.lambda_lo > -1.0 && !job.power;
+    const IntervalMap im = interval_map(0.5, job.lambda_lo);  // mid and half depend on the interval alone
     void *buf[2] = {w.y0, w.y1};
     for (int k = 1; k <= maxM; ++k) {
         StepLaunch sl;
@@ -368,7 +370,7 @@ static cudaError_t launch_rounds(cpaa_graph *g, const TileJob &job, bool history
             sl.sa.decide = sl.active;
             for (int b = 0; b < W; ++b) {
                 sl.sa.k[b] = k;
-                sl.sa.err[b] = err_bound(job.c[b], k);
+                sl.sa.err[b] = err_bound_on(job.c[b], job.lambda_lo, k);
                 sl.sa.tol[b] = job.tol;
             }
             sl.sa.normalize = job.normalize;
@@ -379,6 +381,11 @@ static cudaError_t launch_rounds(cpaa_graph *g, const TileJob &job, bool history
         }
         sl.first = (k == 1) ? (1u << W) - 1u : 0u;
         sl.power = job.power;
+        if (interval) {
+            sl.interval = 1;
+            sl.ia = 1.0 / im.half;
+            sl.ib = im.mid / im.half;
+        }
         sl.long_cnt = nullptr;
         sl.stream = st;
         if (job.frontier && k <= kFrontierRounds) {
@@ -402,10 +409,11 @@ constexpr size_t kMaxRoundGraphs = 8;
 static cpaa_status round_graph(cpaa_graph *g, const TileJob &job, bool history_all_rounds, int maxM,
                                cudaGraphExec_t *out) {
     Workspace &w = g->ws;
-    uint64_t tolb;
+    uint64_t tolb, lob;
     std::memcpy(&tolb, &job.tol, sizeof tolb);
+    std::memcpy(&lob, &job.lambda_lo, sizeof lob);
     std::vector<uint64_t> key = {(uint64_t)job.precision, (uint64_t)job.width, (uint64_t)job.power,
-                                 (uint64_t)job.frontier, (uint64_t)(uintptr_t)w.fr.cur,
+                                 (uint64_t)job.frontier, (uint64_t)(uintptr_t)w.fr.cur, lob,
                                  (uint64_t)history_all_rounds, (uint64_t)maxM, (uint64_t)job.posteriori,
                                  job.posteriori ? tolb : 0, (uint64_t)job.normalize,
                                  (uint64_t)(uintptr_t)w.y0, (uint64_t)(uintptr_t)w.y1,
@@ -424,7 +432,7 @@ static cpaa_status round_graph(cpaa_graph *g, const TileJob &job, bool history_a
             return CPAA_OK;
         }
     if (!w.capture) CPAA_CUDA(cudaStreamCreateWithFlags(&w.capture, cudaStreamNonBlocking));
-    prepare_step(job.precision, job.width);
+    prepare_step(job.precision, job.width, job.lambda_lo > -1.0);
     CPAA_CUDA(cudaStreamBeginCapture(w.capture, cudaStreamCaptureModeThreadLocal));
     const cudaError_t le = launch_rounds(g, job, history_all_rounds, maxM, w.capture);
     cudaGraph_t graph = nullptr;
@@ -527,6 +535,23 @@ static int power_rounds(double c, double tol, int max_rounds) {
     return -1;
 }
 
+namespace cpaa {
+
+// The interval [lo, 1] a solve's series runs on: -1 unless CPAA_INTERVAL
+// (the caller's lambda_lo) or CPAA_CERTIFY_INTERVAL (the graph's own bound)
+// raise it.
+cpaa_status resolve_interval(const cpaa_graph *g, const cpaa_options &opt, double *lo) {
+    *lo = -1.0;
+    if (opt.flags & CPAA_INTERVAL) {
+        if (!(opt.lambda_lo >= -1.0 && opt.lambda_lo < 1.0)) return fail(CPAA_EINVAL, "lambda_lo must lie in [-1, 1)");
+        *lo = opt.lambda_lo;
+    }
+    if (opt.flags & CPAA_CERTIFY_INTERVAL) *lo = std::max(*lo, graph_lambda_lo(g));
+    return CPAA_OK;
+}
+
+}  // namespace cpaa
+
 static cpaa_status solve_one(cpaa_graph *g, const double *p, double c, double tol, double *pi,
                              const cpaa_options *opt_in, cpaa_info *info, int power) {
     clear_error();
@@ -549,6 +574,12 @@ static cpaa_status solve_one(cpaa_graph *g, const double *p, double c, double to
         return fail(CPAA_EINVAL, "the power method has its own stopping rule (2 c^T < tol)");
     const int max_rounds = opt.max_rounds > 0 ? opt.max_rounds : kDefaultMaxRounds;
     if (opt.fixed_rounds > max_rounds) return fail(CPAA_EINVAL, "fixed_rounds > max_rounds");
+    double lo = -1.0;
+    {
+        cpaa_status ls = resolve_interval(g, opt, &lo);
+        if (ls != CPAA_OK) return ls;
+    }
+    if (power) lo = -1.0;  // the power method is not a Chebyshev series
     const bool host_io = (opt.flags & CPAA_DEVICE_IO) == 0;
     cudaStream_t st = (cudaStream_t)opt.stream;
     const int64_t n = g->n;
@@ -579,15 +610,17 @@ static cpaa_status solve_one(cpaa_graph *g, const double *p, double c, double to
     cpaa_status result = CPAA_OK;
     int M = opt.fixed_rounds;
     if (M == 0) {
-        M = power ? power_rounds(c, tol, max_rounds) : cpaa_rounds_needed(c, tol, kappa, opt.normalize, max_rounds);
+        M = power ? power_rounds(c, tol, max_rounds)
+                  : cpaa_rounds_needed_interval(c, lo, tol, kappa, opt.normalize, max_rounds);
         if (M < 0) {
             M = max_rounds;
             result = CPAA_ENOTCONV;
         }
     }
     std::vector<double> ck0;
-    cheb_coeffs(c, 0, ck0);
+    cheb_coeffs_on(c, lo, 0, ck0);
     TileJob job;
+    job.lambda_lo = lo;
     job.width = 1;
     job.precision = opt.precision;
     job.normalize = opt.normalize;
@@ -641,10 +674,11 @@ static cpaa_status solve_one(cpaa_graph *g, const double *p, double c, double to
                     round_sums(1, 0, k, h, &t, &a);
                     ml = std::max(ml, a);
                 }
-                info->bound = cpaa_l1_bound(c, M, 2.0 * ml, opt.normalize);
+                info->bound = cpaa_l1_bound_interval(c, lo, M, 2.0 * ml, opt.normalize);
             } else {
-                info->bound = cpaa_l1_bound(c, M, kappa, opt.normalize);
+                info->bound = cpaa_l1_bound_interval(c, lo, M, kappa, opt.normalize);
             }
+            info->lambda_lo = lo;
             if (M == 0) {
                 info->mass = info->l1 = sum_p;
             } else {

@@ -61,6 +61,35 @@ double err_bound(double c, int M) {
     return 2.0 * std::pow(beta, (double)(M + 1)) / (1.0 + beta);
 }
 
+// The series on [lo, 1] (Sec. 2.2's general interval): x = mid + half cos t
+// turns 1 / (1 - c x) into (1 / (1 - c mid)) / (1 - chat cos t) with
+// chat = c half / (1 - c mid), so its coefficients are the [-1, 1] ones of
+// chat times 1 / (1 - c mid).  lo = -1 is the paper's series exactly.
+IntervalMap interval_map(double c, double lo) {
+    IntervalMap m;
+    m.mid = 0.5 * (1.0 + lo);
+    m.half = 0.5 * (1.0 - lo);
+    m.chat = c * m.half / (1.0 - c * m.mid);
+    m.scale = 1.0 / (1.0 - c * m.mid);
+    return m;
+}
+
+void cheb_coeffs_on(double c, double lo, int M, std::vector<double> &ck) {
+    if (lo == -1.0) return cheb_coeffs(c, M, ck);
+    const IntervalMap m = interval_map(c, lo);
+    cheb_coeffs(m.chat, M, ck);
+    for (double &v : ck) v *= m.scale;
+}
+
+// (1 - c) sum_{k>M} c_k with c_k = c_0 betahat^k: (1 - c) c_0 betahat^(M+1) / (1 - betahat).
+double err_bound_on(double c, double lo, int M) {
+    if (lo == -1.0) return err_bound(c, M);
+    const IntervalMap m = interval_map(c, lo);
+    const double s = std::sqrt(1.0 - m.chat * m.chat);
+    const double bh = (1.0 - s) / m.chat;
+    return (1.0 - c) * (2.0 / s) * m.scale * std::pow(bh, (double)(M + 1)) / (1.0 - bh);
+}
+
 }  // namespace cpaa
 
 extern "C" {
@@ -89,6 +118,7 @@ void cpaa_options_init(cpaa_options *opt) {
     opt->normalize = 0;
     opt->fixed_rounds = 0;
     opt->max_rounds = cpaa::kDefaultMaxRounds;
+    opt->lambda_lo = -1.0;
 }
 
 // Tail of the series after M rounds.  With (1 - c) scaling the error is
@@ -107,6 +137,22 @@ int cpaa_rounds_needed(double c, double tol, double kappa, int normalize, int ma
     if (!(c > 0.0 && c < 1.0) || !(tol > 0.0) || max_rounds < 1) return -1;
     for (int M = 1; M <= max_rounds; ++M)
         if (cpaa_l1_bound(c, M, kappa, normalize) < tol) return M;
+    return -1;
+}
+
+double cpaa_l1_bound_interval(double c, double lambda_lo, int M, double kappa, int normalize) {
+    if (!(c > 0.0 && c < 1.0) || !(lambda_lo >= -1.0 && lambda_lo < 1.0) || M < 0) return NAN;
+    const double E = cpaa::err_bound_on(c, lambda_lo, M);
+    if (normalize == 1) return E * kappa;
+    return E * kappa + (1.0 + E * kappa) * E / (1.0 - E);
+}
+
+int cpaa_rounds_needed_interval(double c, double lambda_lo, double tol, double kappa, int normalize,
+                                int max_rounds) {
+    if (!(c > 0.0 && c < 1.0) || !(lambda_lo >= -1.0 && lambda_lo < 1.0) || !(tol > 0.0) || max_rounds < 1)
+        return -1;
+    for (int M = 1; M <= max_rounds; ++M)
+        if (cpaa_l1_bound_interval(c, lambda_lo, M, kappa, normalize) < tol) return M;
     return -1;
 }
 

@@ -1,6 +1,7 @@
 """CPU-only checks of the C ABI: the library loads, exports every function
 include/cpaa.h declares, and its host-side stopping rule agrees with the
 oracle's.  No GPU call is made."""
+import math
 import os
 import re
 
@@ -33,7 +34,7 @@ def test_header_constants_match_the_binding(L):
     src = open(os.path.join(ROOT, "include", "cpaa.h")).read()
     names = ("CPAA_GRAPH_DEVICE_INPUT", "CPAA_GRAPH_VALIDATE", "CPAA_GRAPH_TRUSTED", "CPAA_DEVICE_IO",
              "CPAA_TIME_ROUNDS", "CPAA_SERVER_FUSED", "CPAA_NOALLOC_MAX_N", "CPAA_SERVER_MAX_SEEDS",
-             "CPAA_GRAPH_AUTOTUNE", "CPAA_SPARSE_FRONTIER")
+             "CPAA_GRAPH_AUTOTUNE", "CPAA_SPARSE_FRONTIER", "CPAA_INTERVAL", "CPAA_CERTIFY_INTERVAL")
     for name in names:
         m = re.search(r"#define\s+%s\s+(\d+)u?\b" % name, src)
         assert m, name
@@ -67,6 +68,28 @@ def test_stopping_rule_matches_oracle(L, c, kappa, norm):
         for M in (1, 7, 30):
             a, b = L.cpaa_l1_bound(c, M, kappa, norm), O.l1_bound(c, M, kappa, norm)
             assert abs(a - b) <= 1e-14 * abs(b)
+
+
+@pytest.mark.parametrize("c", [0.5, 0.85, 0.95])
+@pytest.mark.parametrize("lo", [-1.0, -0.9, -0.6, 0.0, 0.5])
+@pytest.mark.parametrize("norm", [0, 1])
+def test_interval_stopping_rule_matches_oracle(L, c, lo, norm):
+    """The library's own bound and rounds for the series on [lambda_lo, 1]
+    equal the oracle's (written separately from it); lambda_lo = -1 gives the
+    plain rule."""
+    from oracle import oracle as O
+    for kappa in (1.0, 74.0, 1.6e4):
+        for tol in (1e-3, 1e-6, 1e-10):
+            assert L.cpaa_rounds_needed_interval(c, lo, tol, kappa, norm) == \
+                O.rounds_needed_interval(c, lo, tol, kappa, norm)
+            if lo == -1.0:
+                assert L.cpaa_rounds_needed_interval(c, lo, tol, kappa, norm) == L.cpaa_rounds_needed(c, tol, kappa, norm)
+        for M in (1, 7, 30):
+            a, b = L.cpaa_l1_bound_interval(c, lo, M, kappa, norm), O.l1_bound_interval(c, lo, M, kappa, norm)
+            assert abs(a - b) <= 1e-13 * abs(b)
+    assert L.cpaa_rounds_needed_interval(c, 1.0, 1e-6, 1.0) == -1
+    assert L.cpaa_rounds_needed_interval(c, -1.5, 1e-6, 1.0) == -1
+    assert math.isnan(L.cpaa_l1_bound_interval(c, 1.0, 3, 1.0))
 
 
 def test_stopping_rule_rejects_bad_args(L):
@@ -196,6 +219,19 @@ def test_layout_params_checked_before_any_device_work(L):
             L.cpaa_graph_create_ex(2, 2, rp, cx, 0, params)
         assert e.value.status == L.CPAA_EINVAL, why
         assert why in str(e.value), (why, str(e.value))
+
+
+def test_server_rejects_the_interval_flags(L):
+    """The server runs the series on [-1, 1] only: either interval flag is
+    EINVAL at creation, before any device work."""
+    import ctypes
+    for flag in (L.CPAA_INTERVAL, L.CPAA_CERTIFY_INTERVAL):
+        o = L.cpaa_options_init()
+        o.flags = flag
+        h = ctypes.c_void_p()
+        st = L.lib().cpaa_server_create(1 << 20, ctypes.byref(o), ctypes.byref(h))
+        assert st == L.CPAA_EINVAL and not h.value
+        assert "[-1, 1]" in L.cpaa_last_error()
 
 
 def test_host_side_argument_checks(L):
