@@ -250,7 +250,10 @@ def run_batch(pkg, args, stream):
     import cpaa_inputs as ci
     g = ci.chung_lu(1 << 22, 64_000_000, seed=0, device="cuda", distinct=True)
     n, nnz = g.n, g.nnz
-    G = pkg.Graph(g.row_ptr, g.col_idx, n=n)
+    G = pkg.Graph(g.row_ptr, g.col_idx, n=n, autotune=not args.no_autotune,
+                  layout={"tune_precision": pkg.CPAA_F32})
+    blayout = {k: v for k, v in G.layout().items()
+               if k in ("hub_degree", "hub_tile", "long_chunk", "sort_window", "tuned", "tune_candidates")}
     del g
     B = 256
     seeds = ci.seed_vectors(n, B, max_seeds=16, seed=0)
@@ -295,7 +298,7 @@ def run_batch(pkg, args, stream):
     rounds2 = [i.rounds for i in infos2]
     return {"workload": "Chung-Lu n=2^22, 64M distinct undirected edges, gamma=2.1, seed 0, + ring; 256 "
                         "vectors uniform over 1-16 seeds; c=0.85; tol 1e-6 L1",
-            "n": n, "nnz": nnz, "B": B, "precision": "f32",
+            "n": n, "nnz": nnz, "B": B, "precision": "f32", "layout": blayout,
             "ms_batch": t_batch, "ms_per_query_batched_f32": t_batch / B,
             "ms_per_query_single_f64": t_single,
             "speedup_batched_f32_vs_single_f64": t_single / (t_batch / B),
@@ -589,8 +592,11 @@ def run_ours(args):
     g, gen_s = make_graph(args.workload, "cuda")
     n, nnz = g.n, g.nnz
     t = time.time()
-    G = pkg.Graph(g.row_ptr, g.col_idx, n=n, validate=True)
+    # layout parameters picked by the library's autotuner, timed in the main precision
+    G = pkg.Graph(g.row_ptr, g.col_idx, n=n, validate=True, autotune=not args.no_autotune,
+                  layout={"tune_precision": PREC[prec]})
     create_s = time.time() - t
+    layout = G.layout()
     cpu_graph = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu_graph = g.numpy()
@@ -760,6 +766,8 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (col_idx %.2f GB), no flush" % (4 * nnz / 1e9),
                    "graph_gen_s": round(gen_s, 2), "graph_create_s": round(create_s, 2),
+                   "layout": {k: layout[k] for k in ("hub_degree", "hub_tile", "long_chunk", "sort_window",
+                                                     "tuned", "tune_candidates")},
                    "step_ms": [round(x, 3) for x in step_ms]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": profiled_traffic(prec, args.workload),
@@ -800,6 +808,7 @@ def main(argv=None):
     ap.add_argument("--skip-power", action="store_true")
     ap.add_argument("--serve-queries", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="default layout parameters")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
