@@ -377,6 +377,33 @@ def run_grid(pkg, args, stream):
         out[name]["l1_vs_f64"] = float((res[name] - res["f64"]).abs().sum().item())
     out["frontier_one_seed_f64"] = one_seed_frontier(pkg, G, n, pkg.CPAA_F64, reps=10)
     G.close()
+    del G
+    torch.cuda.empty_cache()
+    # the series on [lambda_lo, 1]: the same lattice with a self-loop on every
+    # vertex certifies lambda_lo = -1 + 2/d_max = -0.6
+    gl = ci.with_self_loops(ci.grid_deleted(4096, 4096, 0.2, seed=0, device="cuda"))
+    GL = pkg.Graph(gl.row_ptr, gl.col_idx, n=gl.n)
+    del gl
+    iv = {"workload": "the same lattice with a self-loop on every vertex; FP64, c=0.85, uniform p, tol 1e-6",
+          "lambda_lo_certified": GL.spectrum_bound()}
+    piv = {}
+    for name, cert in (("plain", False), ("interval", True)):
+        pi = torch.empty_like(p)
+        for _ in range(3):
+            GL.solve(p, 0.85, 1e-6, pi, certify_interval=cert)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        infos = [GL.solve(p, 0.85, 1e-6, pi, certify_interval=cert, time_rounds=True) for _ in range(args.steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        iv[name] = {"rounds": infos[0].rounds, "ms_per_solve": e0.elapsed_time(e1) / args.steps,
+                    "round_ms": sum(i.rounds_ms for i in infos) / sum(i.rounds for i in infos),
+                    "bound": infos[0].bound, "lambda_lo": infos[0].lambda_lo}
+        piv[name] = pi
+    iv["l1_interval_vs_plain"] = float((piv["interval"] - piv["plain"]).abs().sum().item())
+    iv["speedup"] = iv["plain"]["ms_per_solve"] / iv["interval"]["ms_per_solve"]
+    out["interval_looped"] = iv
+    GL.close()
     return {"workload": "4096x4096 lattice, 20% of edges deleted (seed 0, spanning tree kept); "
                         "c=0.85, uniform p, tol 1e-6", "n": n, "nnz": nnz, **out}
 

@@ -174,6 +174,22 @@ def grid_deleted(rows, cols, frac=0.2, seed=0, device="cpu"):
                                      % (R, C, frac, seed))
 
 
+def with_self_loops(g):
+    """The same graph with a self-loop added on every vertex that lacks one
+    (rows stay ascending; a loop is one entry of its row)."""
+    n = g.n
+    dev = g.row_ptr.device
+    rp = g.row_ptr.to(torch.int64)
+    rows = torch.repeat_interleave(torch.arange(n, device=dev), rp[1:] - rp[:-1])
+    keys = torch.cat([rows * n + g.col_idx.to(torch.int64), torch.arange(n, device=dev) * (n + 1)])
+    keys = torch.unique(keys)
+    r = keys // n
+    counts = torch.bincount(r, minlength=n)
+    row_ptr = torch.zeros(n + 1, dtype=torch.int64, device=dev)
+    row_ptr[1:] = torch.cumsum(counts, 0)
+    return Csr(n, row_ptr.to(torch.int32), (keys % n).to(torch.int32), g.name + "+loops")
+
+
 def shuffled(g, seed=0):
     """The same graph with its vertex ids permuted by a seeded random
     permutation (rows re-sorted, columns ascending): a stand-in for inputs whose

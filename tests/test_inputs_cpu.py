@@ -86,3 +86,16 @@ def test_chung_lu_distinct_keeps_the_first_distinct_pairs():
     assert got == set(order) | ring
     h = ci.chung_lu(n, E, seed=3, distinct=True, chunk=1 << 15)
     assert torch.equal(g.row_ptr, h.row_ptr) and torch.equal(g.col_idx, h.col_idx)
+
+
+def test_with_self_loops_adds_one_loop_per_vertex():
+    """Every vertex gains exactly one self-loop (none doubled where one was
+    already present); the other entries are unchanged."""
+    g = ci.from_edges(6, [(0, 1), (1, 2), (2, 2), (3, 4), (4, 5), (5, 0)])
+    h = ci.with_self_loops(g)
+    rp, cx = g.numpy()
+    rp2, cx2 = h.numpy()
+    for u in range(g.n):
+        old = set(cx[rp[u]:rp[u + 1]].tolist())
+        new = cx2[rp2[u]:rp2[u + 1]].tolist()
+        assert new == sorted(old | {u})

@@ -22,11 +22,7 @@ from oracle import oracle as O
 
 def with_loops(g):
     """The same graph with a self-loop added on every vertex."""
-    rp, cx = g.numpy()
-    rows = np.repeat(np.arange(g.n), np.diff(rp))
-    keep = rows < cx
-    e = np.concatenate([np.stack([rows[keep], cx[keep]], 1), np.stack([np.arange(g.n)] * 2, 1)])
-    return ci.from_edges(g.n, e, name=g.name + "+loops")
+    return ci.with_self_loops(g)
 
 
 def looped_graphs():
