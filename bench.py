@@ -384,24 +384,28 @@ def run_grid(pkg, args, stream):
     gl = ci.with_self_loops(ci.grid_deleted(4096, 4096, 0.2, seed=0, device="cuda"))
     GL = pkg.Graph(gl.row_ptr, gl.col_idx, n=gl.n)
     del gl
-    iv = {"workload": "the same lattice with a self-loop on every vertex; FP64, c=0.85, uniform p, tol 1e-6",
+    iv = {"workload": "the same lattice with a self-loop on every vertex; c=0.85, uniform p, tol 1e-6",
           "lambda_lo_certified": GL.spectrum_bound()}
-    piv = {}
-    for name, cert in (("plain", False), ("interval", True)):
-        pi = torch.empty_like(p)
-        for _ in range(3):
-            GL.solve(p, 0.85, 1e-6, pi, certify_interval=cert)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        infos = [GL.solve(p, 0.85, 1e-6, pi, certify_interval=cert, time_rounds=True) for _ in range(args.steps)]
-        e1.record(stream)
-        torch.cuda.synchronize()
-        iv[name] = {"rounds": infos[0].rounds, "ms_per_solve": e0.elapsed_time(e1) / args.steps,
-                    "round_ms": sum(i.rounds_ms for i in infos) / sum(i.rounds for i in infos),
-                    "bound": infos[0].bound, "lambda_lo": infos[0].lambda_lo}
-        piv[name] = pi
-    iv["l1_interval_vs_plain"] = float((piv["interval"] - piv["plain"]).abs().sum().item())
-    iv["speedup"] = iv["plain"]["ms_per_solve"] / iv["interval"]["ms_per_solve"]
+    for prec_name in ("f64", "f32", "df64"):
+        ivp = {}
+        piv = {}
+        for name, cert in (("plain", False), ("interval", True)):
+            pi = torch.empty_like(p)
+            for _ in range(3):
+                GL.solve(p, 0.85, 1e-6, pi, precision=PREC[prec_name], certify_interval=cert)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            infos = [GL.solve(p, 0.85, 1e-6, pi, precision=PREC[prec_name], certify_interval=cert, time_rounds=True)
+                     for _ in range(args.steps)]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ivp[name] = {"rounds": infos[0].rounds, "ms_per_solve": e0.elapsed_time(e1) / args.steps,
+                         "round_ms": sum(i.rounds_ms for i in infos) / sum(i.rounds for i in infos),
+                         "bound": infos[0].bound, "lambda_lo": infos[0].lambda_lo}
+            piv[name] = pi
+        ivp["l1_interval_vs_plain"] = float((piv["interval"] - piv["plain"]).abs().sum().item())
+        ivp["speedup"] = ivp["plain"]["ms_per_solve"] / ivp["interval"]["ms_per_solve"]
+        iv[prec_name] = ivp
     out["interval_looped"] = iv
     GL.close()
     return {"workload": "4096x4096 lattice, 20% of edges deleted (seed 0, spanning tree kept); "

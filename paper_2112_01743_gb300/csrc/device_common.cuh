@@ -105,6 +105,12 @@ __device__ __forceinline__ df ld_once(const df *p) {
     const float2 v = __ldcs(reinterpret_cast<const float2 *>(p));
     return df(v.x, v.y);
 }
+// Small read-only tables read by every round (kept in cache).
+template <class T> __device__ __forceinline__ T ld_ro(const T *p) { return __ldg(p); }
+__device__ __forceinline__ df ld_ro(const df *p) {
+    const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+    return df(v.x, v.y);
+}
 
 // Explicitly rounded arithmetic (no contraction differences between kernels).
 __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
@@ -134,19 +140,19 @@ __device__ __forceinline__ typename Prec<P>::A new_iterate(typename Prec<P>::A s
 
 // The same on the interval [lambda_lo, 1] (Sec. 2.2's general interval): the
 // recurrence on Q = (P - mid I) / half, scaled by D^-1 like the rest, with
-// ia = 1 / half, ib = mid / half and y_cur the row's current iterate y_k[u]:
-//   k = 1:  y_1 = ia (s / d) - ib y_0
-//   k >= 2: y_{k+1} = ia (2 s / d) - 2 ib y_k - y_{k-1}.
+// iv = ia 2 / d (ia = 1 / half; the caller's factor), mb = -2 mid / half and
+// y_cur the row's current iterate y_k[u]:
+//   k = 1:  y_1 = ia (s / d) - (mid / half) y_0 = (iv s) / 2 + (mb / 2) y_0
+//   k >= 2: y_{k+1} = ia (2 s / d) - 2 (mid / half) y_k - y_{k-1}
+//                   = iv s + (mb y_k - y_{k-1})      (two fused multiply-adds)
 template <int P, class S = typename Prec<P>::S>
-__device__ __forceinline__ typename Prec<P>::A interval_iterate(typename Prec<P>::A s, typename Prec<P>::A inv2,
+__device__ __forceinline__ typename Prec<P>::A interval_iterate(typename Prec<P>::A s, typename Prec<P>::A iv,
                                                                 typename Prec<P>::A y_cur,
                                                                 typename Prec<P>::A y_old, int first,
-                                                                typename Prec<P>::A ia,
-                                                                typename Prec<P>::A ib) {
+                                                                typename Prec<P>::A mb) {
     using A = typename Prec<P>::A;
-    const A t = mul_rn(s, inv2);
-    const A y = first ? fma_rn(mul_rn(t, A(0.5)), ia, -mul_rn(ib, y_cur))
-                      : fma_rn(t, ia, -fma_rn(add_rn(ib, ib), y_cur, y_old));
+    const A y = first ? fma_rn(mul_rn(mb, A(0.5)), y_cur, mul_rn(mul_rn(s, iv), A(0.5)))
+                      : fma_rn(s, iv, fma_rn(mb, y_cur, -y_old));
     return round_y(y, (const S *)nullptr);
 }
 

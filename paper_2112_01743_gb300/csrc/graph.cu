@@ -57,7 +57,8 @@ __global__ void validate_kernel(const int32_t *__restrict__ row_ptr,
 __global__ void vertex_arrays_kernel(const int32_t *__restrict__ row_ptr,
                                      const int32_t *__restrict__ perm, int64_t n, double *deg64,
                                      double *inv64, double *inv2_64, float *deg32, float *inv32,
-                                     float *inv2_32, df *deg_df, df *inv_df, df *inv2_df, int32_t *inv_perm) {
+                                     float *inv2_32, df *deg_df, df *inv_df, df *inv2_df, uint16_t *deg16,
+                                     int32_t *inv_perm) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
          r += (int64_t)gridDim.x * blockDim.x) {
         const int32_t u = perm[r];
@@ -71,6 +72,7 @@ __global__ void vertex_arrays_kernel(const int32_t *__restrict__ row_ptr,
         deg_df[r] = df((double)d);
         inv_df[r] = df(1.0 / (double)d);
         inv2_df[r] = df(2.0 / (double)d);
+        deg16[r] = (uint16_t)min(d, 65535);
         inv_perm[u] = (int32_t)r;
     }
 }
@@ -167,6 +169,7 @@ static void release(cpaa_graph *g) {
     cudaFree(g->chunk_len); cudaFree(g->chunk_order); cudaFree(g->chunk_desc); cudaFree(g->deg64); cudaFree(g->inv_deg64);
     cudaFree(g->deg32); cudaFree(g->inv_deg32); cudaFree(g->inv2_deg64); cudaFree(g->inv2_deg32);
     cudaFree(g->deg_df); cudaFree(g->inv_deg_df); cudaFree(g->inv2_deg_df);
+    cudaFree(g->tab64); cudaFree(g->tab32); cudaFree(g->tab_df); cudaFree(g->deg16); cudaFree(w.ivtab);
     delete g;
 }
 
@@ -361,7 +364,7 @@ static cpaa_status build_graph(int64_t n, int64_t nnz, const int32_t *row_ptr, c
         g->num_chunks = (int)L.chunk_off.size();
         g->num_long_chunks = 0;
         while (g->num_long_chunks < g->num_chunks &&
-               L.chunk_len[L.chunk_order[g->num_long_chunks]] > lp.long_chunk)
+               L.chunk_len[L.chunk_order[g->num_long_chunks]] > std::min(lp.long_chunk, kMaxShortRow))
             ++g->num_long_chunks;
         g->sell_entries = L.sell_entries;
 
@@ -377,10 +380,41 @@ static cpaa_status build_graph(int64_t n, int64_t nnz, const int32_t *row_ptr, c
         ALLOC(g->deg_df, sizeof(df) * n);
         ALLOC(g->inv_deg_df, sizeof(df) * n);
         ALLOC(g->inv2_deg_df, sizeof(df) * n);
+        ALLOC(g->deg16, sizeof(uint16_t) * n);
         vertex_arrays_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 8192), 256>>>(
             d_rp, g->perm, n, g->deg64, g->inv_deg64, g->inv2_deg64, g->deg32, g->inv_deg32, g->inv2_deg32,
-            g->deg_df, g->inv_deg_df, g->inv2_deg_df, d_inv);
+            g->deg_df, g->inv_deg_df, g->inv2_deg_df, g->deg16, d_inv);
         CK(cudaGetLastError());
+        {
+            // the same factors by degree for the short chunks' rows, by the
+            // same expressions (IEEE division and conversions give the same
+            // bits on host and device)
+            int dmax = 0;
+            for (int64_t u = 0; u < n; ++u) dmax = std::max(dmax, hrp[u + 1] - hrp[u]);
+            g->dmax = dmax;
+            const int T = std::min(std::min(dmax, lp.hub_degree), std::min(lp.long_chunk, kMaxShortRow)) + 1;
+            std::vector<double> t64(3 * (size_t)T, 0.0);
+            std::vector<float> t32(3 * (size_t)T, 0.0f);
+            std::vector<df> tdf(3 * (size_t)T, df(0.0));
+            for (int d = 1; d < T; ++d) {
+                t64[d] = (double)d;
+                t64[T + d] = 1.0 / (double)d;
+                t64[2 * T + d] = 2.0 / (double)d;
+                t32[d] = (float)d;
+                t32[T + d] = 1.0f / (float)d;
+                t32[2 * T + d] = 2.0f / (float)d;
+                tdf[d] = df((double)d);
+                tdf[T + d] = df(1.0 / (double)d);
+                tdf[2 * T + d] = df(2.0 / (double)d);
+            }
+            ALLOC(g->tab64, sizeof(double) * 3 * T);
+            ALLOC(g->tab32, sizeof(float) * 3 * T);
+            ALLOC(g->tab_df, sizeof(df) * 3 * T);
+            CK(cudaMemcpy(g->tab64, t64.data(), sizeof(double) * 3 * T, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(g->tab32, t32.data(), sizeof(float) * 3 * T, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(g->tab_df, tdf.data(), sizeof(df) * 3 * T, cudaMemcpyHostToDevice));
+            g->tab_n = T;
+        }
 
         // the relabelled graph's CSR: every caller row's entries in new ids,
         // sorted ascending (the order in which the round adds them)
@@ -446,9 +480,6 @@ static cpaa_status build_graph(int64_t n, int64_t nnz, const int32_t *row_ptr, c
             unsigned long long nl = 0;
             CK(cudaMemcpy(&nl, d_loops, sizeof(nl), cudaMemcpyDeviceToHost));
             g->loops_all = (int64_t)nl == n;
-            int dmax = 0;
-            for (int64_t u = 0; u < n; ++u) dmax = std::max(dmax, hrp[u + 1] - hrp[u]);
-            g->dmax = dmax;
         }
         dev_free(g, (void **)&d_loops, sizeof(unsigned long long));
         dev_free(g, (void **)&d_inv, sizeof(int32_t) * n);

@@ -108,6 +108,10 @@ constexpr int kDefaultMaxRounds = 2000;
 
 constexpr int kPrepBlocks = 1024;  // CTAs of the fixed-order reductions
 constexpr int kMaxWidth = 16;      // widest tile of vectors a round kernel takes
+// Longest row a short (warp) SELL chunk may hold: its rows read their degree
+// as a 2-byte word, so chunks with longer rows are long (CTA) chunks whatever
+// the long-chunk threshold.
+constexpr int kMaxShortRow = 65532;
 
 // Layout parameters of a graph (cpaa_layout_params with every default
 // resolved): hub rows have degree above hub_degree and are cut into tiles of
@@ -184,6 +188,9 @@ struct Workspace {
     cudaStream_t capture = nullptr;  // private stream the captures run on
     cudaEvent_t tev[2] = {nullptr, nullptr};  // around the rounds (CPAA_TIME_ROUNDS)
     Frontier fr;                     // CPAA_SPARSE_FRONTIER solves (allocated on first use)
+    // the interval series' factor ia * 2 / d by degree (tab_n entries of the
+    // solve's arithmetic type; filled per solve on [lambda_lo, 1])
+    void *ivtab = nullptr;
 };
 
 // One tile of up to kMaxWidth vectors for run_tile (solve.cu).
@@ -259,6 +266,17 @@ struct cpaa_graph {
     float *deg32 = nullptr;
     float *inv_deg32 = nullptr;
     float *inv2_deg32 = nullptr;
+    // the same three values by degree d in [0, tab_n), rows of tab_n entries:
+    // d, 1 / d, 2 / d (entry 0 unused).  A short SELL chunk's rows hold at
+    // most min(long_chunk, kMaxShortRow, hub_degree, d_max) = tab_n - 1
+    // entries, so the round kernel reads their degree as a 2-byte word
+    // (deg16, every vertex: min(d, 65535)) and looks the factors up here
+    // instead of reading an 8-byte one
+    uint16_t *deg16 = nullptr;
+    double *tab64 = nullptr;
+    cpaa::df *tab_df = nullptr;
+    float *tab32 = nullptr;
+    int tab_n = 0;
     int64_t device_bytes = 0;
     int tuned_width[4] = {0, 0, 0, 0};  // batch tile width picked by the autotuner, per precision
     cpaa::Workspace ws;
@@ -316,12 +334,22 @@ struct StepLaunch {
     const unsigned *stop = nullptr; // stopped columns (a-posteriori rule), or NULL
     StopArgs sa;                    // the rule's test after this round (sa.decide == 0: none)
     double ck[kMaxWidth] = {};
+    // Deferred accumulation: a column's term c_k y_k may be added one round
+    // late, from the stored y_k, together with c_{k+1} y_{k+1}; the
+    // accumulator then takes the same fused operations in the same order, so
+    // the result is the same bits, and rounds with no term to add neither read
+    // nor write it.  pend: columns whose last round's term is added now (with
+    // ck_prev); defer: columns whose term this round is left for the next.
+    double ck_prev[kMaxWidth] = {};
+    unsigned pend = 0;
+    unsigned defer = 0;
+    const void *ivtab = nullptr;    // the interval series' factor table (Workspace::ivtab)
     unsigned active = 0;            // columns that still accumulate
     unsigned reduce = 0;            // nonzero: take this round's sums
     unsigned first = 0;             // columns in their first round (k == 1)
     int power = 0;                  // 1: power-method round (ck[b] = c, rho holds q = (1-c) p / d)
     int interval = 0;               // 1: the recurrence on Q = (P - mid I) / half
-    double ia = 1.0, ib = 0.0;      // its 1 / half and mid / half
+    double ia = 1.0, mb = 0.0;      // its 1 / half and -2 mid / half
     int *long_cnt = nullptr;        // hub ticket counters [n_hub], all zero; NULL = the graph's own
     // sparse frontier (NULL: every item): items whose rows are all outside
     // front are skipped, unless *front_full or *front_entries > front_limit
@@ -337,6 +365,16 @@ void prepare_step(int precision, int width, bool interval = false);
 // when StepLaunch::interval is set).
 void prepare_step_interval(int precision, int width);
 cudaError_t launch_step_interval(const StepLaunch &s);
+// The interval series' factor table ia 2 / d by degree, in precision's
+// arithmetic type, into out (g->tab_n entries; step_interval.cu).
+cudaError_t launch_ivtab(const cpaa_graph *g, int precision, double ia, void *out, cudaStream_t st);
+// The deferred-accumulation masks of round k for columns with rounds[b]
+// rounds and coefficients ck[b] (solve.cu).
+void defer_terms(int k, const int *rounds, int W, const std::vector<std::vector<double>> &ck, StepLaunch &sl);
+// Whether the round kernel form for this precision and width takes deferred
+// terms (step_impl.cuh, deferred_form): the single-vector FP32, BF16 and DF64
+// forms.
+inline bool defer_supported(int precision, int width) { return width == 1 && precision != CPAA_F64; }
 
 // Sparse-frontier pieces (frontier.cu).  ensure_frontier allocates f for g
 // (frontier_bytes of device memory, counted in track's device_bytes);

@@ -584,6 +584,8 @@ static bool plan_round(cpaa_server *s, GraphState &gs, StepLaunch &sl, unsigned 
     sl.reduce = 0;
     sl.first = ~live & ((1u << gs.w) - 1u);
     sl.power = 0;
+    // no deferred accumulation (StepLaunch::pend): a tile's width, and with it
+    // the kernel form, may change between two rounds of a query
     sl.long_cnt = gs.long_cnt;
     sl.stream = gs.stream;
     for (int b = 0; b < kMaxWidth; ++b) sl.ck[b] = 0.0;

@@ -232,6 +232,7 @@ static cpaa_status ensure_workspace_buffers(cpaa_graph *g, int prec, int width, 
     if (!w.ipart2) {
         if ((st = dev_alloc(g, (void **)&w.ipart2, sizeof(double) * 2 * kMaxWidth * kSumBlocks)) != CPAA_OK)
             return st;
+        if ((st = dev_alloc(g, &w.ivtab, sizeof(double) * (size_t)g->tab_n)) != CPAA_OK) return st;
         if ((st = dev_alloc(g, (void **)&w.maxl1, sizeof(double) * kMaxWidth)) != CPAA_OK) return st;
         if ((st = dev_alloc(g, (void **)&w.stop, sizeof(unsigned))) != CPAA_OK) return st;
         if ((st = dev_alloc(g, (void **)&w.stop_round, sizeof(int) * kMaxWidth)) != CPAA_OK) return st;
@@ -293,6 +294,8 @@ static cudaError_t tile_kernels(cpaa_graph *g, const TileJob &job, cudaStream_t 
         prep_kernel<S, R, W><<<grid, kThreads, 0, st>>>(cols, g->perm, n, g->inv_deg64, (S *)w.y0,
                                                         (R *)w.rho,
                                                         std::is_same<R, float>::value ? (R *)w.comp : nullptr, z);
+        if (job.lambda_lo > -1.0 && !job.power)
+            launch_ivtab(g, job.precision, 1.0 / interval_map(0.5, job.lambda_lo).half, w.ivtab, st);
     } else {
         // the accumulator, or (power method) the last iterate, which has the
         // same element type on the FP64 and FP32 paths
@@ -330,6 +333,22 @@ static cudaError_t tile_phase(cpaa_graph *g, const TileJob &job, cudaStream_t st
     return cudaErrorInvalidValue;
 }
 
+// Deferred accumulation (StepLaunch::pend, defer): a column leaves the term
+// of an odd round k for round k + 1 unless k is its last, so the accumulator
+// is read and written in every other round.  k and rounds[b] are the rounds
+// of the columns; ck[b][j] their coefficients.
+void defer_terms(int k, const int *rounds, int W, const std::vector<std::vector<double>> &ck, StepLaunch &sl) {
+    sl.pend = sl.defer = 0;
+    for (int b = 0; b < W; ++b) {
+        if (k > rounds[b]) continue;
+        if ((k & 1) && k < rounds[b]) sl.defer |= 1u << b;
+        if (!(k & 1) && k >= 2) {
+            sl.pend |= 1u << b;
+            sl.ck_prev[b] = ck[b][k - 1];
+        }
+    }
+}
+
 // The M round launches of a tile on stream st.
 static cudaError_t launch_rounds(cpaa_graph *g, const TileJob &job, bool history_all_rounds, int maxM,
                                  cudaStream_t st) {
@@ -363,6 +382,9 @@ static cudaError_t launch_rounds(cpaa_graph *g, const TileJob &job, bool history
             }
             if (k == job.rounds[b] || (history_all_rounds && k <= job.rounds[b])) sl.reduce |= 1u << b;
         }
+        // every column's last round is known here
+        if (!job.power && !job.posteriori && defer_supported(job.precision, W))
+            defer_terms(k, job.rounds, W, ck, sl);
         if (job.posteriori) {
             // every round takes its sums; columns still within their
             // rigorous M test the a-posteriori rule after it
@@ -384,7 +406,8 @@ static cudaError_t launch_rounds(cpaa_graph *g, const TileJob &job, bool history
         if (interval) {
             sl.interval = 1;
             sl.ia = 1.0 / im.half;
-            sl.ib = im.mid / im.half;
+            sl.mb = -2.0 * im.mid / im.half;
+            sl.ivtab = w.ivtab;
         }
         sl.long_cnt = nullptr;
         sl.stream = st;
@@ -419,7 +442,8 @@ static cpaa_status round_graph(cpaa_graph *g, const TileJob &job, bool history_a
                                  (uint64_t)(uintptr_t)w.y0, (uint64_t)(uintptr_t)w.y1,
                                  (uint64_t)(uintptr_t)w.rho, (uint64_t)(uintptr_t)w.comp,
                                  (uint64_t)(uintptr_t)w.long_part, (uint64_t)(uintptr_t)w.red,
-                                 (uint64_t)(uintptr_t)w.ipart, (uint64_t)(uintptr_t)w.maxl1};
+                                 (uint64_t)(uintptr_t)w.ipart, (uint64_t)(uintptr_t)w.maxl1,
+                                 (uint64_t)(uintptr_t)w.ivtab};
     for (int b = 0; b < job.width; ++b) {
         uint64_t cb;
         std::memcpy(&cb, &job.c[b], sizeof cb);

@@ -69,6 +69,12 @@ struct StepParams {
     // vectors (new order)
     const A *deg;
     const A *inv_deg;  // 2 / d for Chebyshev rounds, 1 / d for power-method rounds
+    // the same by degree for the rows of short chunks, which read their
+    // degree as a 2-byte word: tab_inv[d] is inv_deg's value (ia 2 / d for the
+    // interval series), tab_deg[d] = d
+    const uint16_t *deg16;
+    const A *tab_inv;
+    const A *tab_deg;
     const S *y_src;  // [(n+1) x W]
     S *y_io;         // [(n+1) x W]
     R *rho;          // [n x W]
@@ -76,12 +82,15 @@ struct StepParams {
     double *ipart;   // item partial sums [(n_hub + num_chunks)][2][W] (reducing rounds)
     const unsigned *stop;  // columns stopped by the a-posteriori rule, or NULL
     A ck[W];
+    A ck_prev[W];     // coefficient of a term left from the last round
+    unsigned pend;    // columns adding last round's term c_{k-1} y_{k-1} now (read back from y_src)
+    unsigned defer;   // columns whose term this round is added in the next one
     unsigned active;
     unsigned reduce;
     unsigned first;  // columns in their first round (y_1 = D^-1 P y_0... scaled: s / d)
     int power;       // 1: power-method round y' = c s / d + q, ck[b] = c, q held in rho
     int interval;    // 1: the series on [lambda_lo, 1] (interval_iterate), with
-    A ia, ib;        //    ia = 1 / half and ib = mid / half
+    A ia, mb;        //    ia = 1 / half and mb = -2 mid / half
     // sparse frontier (frontier.cu), or front == NULL: items with no row in
     // front are skipped, unless *front_full or the covered entries exceed
     // front_limit (then this and every later round take every item)
@@ -188,16 +197,46 @@ __device__ __forceinline__ void gather_row(const typename Prec<P>::S *y, int j,
     for (int b = 0; b < W; ++b) x[b] = to_acc(v[b]);
 }
 
-// A row's own operands: the iterate it overwrites, the accumulator and its
-// compensation.
+// A row's own operands: the iterate it overwrites, its current one (read
+// when a deferred term is added or by the interval series), the accumulator
+// and its compensation.
 template <int P, int W>
 struct RowOps {
     typename Prec<P>::A y_old[W];
+    typename Prec<P>::A yp[W];
     typename Prec<P>::R rr[W];
     typename Prec<P>::R cmp[W];
 };
 
+// Whether a round kernel form takes deferred terms (defer_supported on the
+// host gives the same answer): the single-vector FP32, BF16 and DF64 forms.
+// Elsewhere the pending term's read and add cost more registers than its
+// bytes save (measured: the FP64 single vector 32 -> 40, FP32 tiles of two
+// 32 -> 40, FP64 tiles of 16 156 -> 251).
+template <int P, int W, bool I>
+__device__ __forceinline__ constexpr bool deferred_form() {
+    return W == 1 && P != CPAA_F64;
+}
+
+// Whether this round reads and writes the accumulator: a term is added now
+// (one left from the last round, or this round's own), or rho holds the power
+// method's q.  The same for every thread of the launch.
+template <int P, int W, bool I>
+__device__ __forceinline__ bool rho_touched(const StepParams<P, W> &p) {
+    if constexpr (!deferred_form<P, W, I>()) return p.power || p.active != 0u;
+    else return p.power || (p.pend | (p.active & ~p.defer)) != 0u;
+}
+
+// The row's stored y_{k-1} into o.yp.
 template <int P, int W>
+__device__ __forceinline__ void load_yp(const StepParams<P, W> &p, int64_t r, RowOps<P, W> &o) {
+    typename Prec<P>::S v[W];
+    load_row<typename Prec<P>::S, W>(p.y_src + r * W, v, false);
+#pragma unroll
+    for (int b = 0; b < W; ++b) o.yp[b] = to_acc(v[b]);
+}
+
+template <int P, int W, bool I>
 __device__ __forceinline__ void load_ops(const StepParams<P, W> &p, int64_t r, RowOps<P, W> &o) {
     using S = typename Prec<P>::S;
     using A = typename Prec<P>::A;
@@ -211,16 +250,38 @@ __device__ __forceinline__ void load_ops(const StepParams<P, W> &p, int64_t r, R
 #pragma unroll
         for (int b = 0; b < W; ++b) o.y_old[b] = to_acc(v[b]);
     }
-    load_row<R, W>(p.rho + r * W, o.rr, true);
-    if constexpr (Prec<P>::kKahan) load_row<R, W>(p.comp + r * W, o.cmp, true);
-    else {
+    // y_{k-1}: narrow tiles fetch their operands before the gather, so they
+    // read it in the epilogue (registers) and only bring it to L1 here
+    if (I || (deferred_form<P, W, I>() && p.pend)) {
+        if constexpr (W <= 4) asm volatile("prefetch.global.L1 [%0];" ::"l"(p.y_src + r * W));
+        else load_yp<P, W>(p, r, o);
+    }
+    if (rho_touched<P, W, I>(p)) {
+        load_row<R, W>(p.rho + r * W, o.rr, true);
+        if constexpr (Prec<P>::kKahan) load_row<R, W>(p.comp + r * W, o.cmp, true);
+        else {
 #pragma unroll
-        for (int b = 0; b < W; ++b) o.cmp[b] = R(0);
+            for (int b = 0; b < W; ++b) o.cmp[b] = R(0);
+        }
+    } else {  // nothing is added to rho this round
+#pragma unroll
+        for (int b = 0; b < W; ++b) o.rr[b] = o.cmp[b] = R(0);
     }
 }
 
+// The row's factor for the recurrence: inv_deg's value, times ia for the
+// interval series (the table path has it scaled already).
+template <int P, int W, bool I>
+__device__ __forceinline__ typename Prec<P>::A row_factor(const StepParams<P, W> &p, typename Prec<P>::A inv) {
+    if constexpr (I) return mul_rn(p.ia, inv);
+    else return inv;
+}
+
 // Row epilogue: new iterates and accumulation; yv receives the new iterates
-// (as stored) for the round's sums.
+// (as stored) for the round's sums.  inv is the row's factor (row_factor).
+// A term left from the last round is added first, from the stored y_{k-1}
+// (which is the value that round accumulated would have used), so rho takes
+// the same operations in the same order as without deferral.
 template <int P, int W, bool I>
 __device__ __forceinline__ void row_finish(const StepParams<P, W> &p, int64_t r,
                                            const typename Prec<P>::A (&s)[W],
@@ -241,28 +302,42 @@ __device__ __forceinline__ void row_finish(const StepParams<P, W> &p, int64_t r,
         store_row<S, W>(p.y_io + r * W, ys, false);
         return;
     }
-    if constexpr (I) {
-#pragma unroll
-        for (int b = 0; b < W; ++b) {
-            // the row's current iterate y_k[u], which the shifted recurrence reads
-            const A yc = to_acc(p.y_src[r * W + b]);
-            const A y = interval_iterate<P>(s[b], inv, yc, o.y_old[b], (p.first >> b) & 1u, p.ia, p.ib);
-            store_y(&ys[b], y);
-            if (active >> b & 1u) accumulate<P>(o.rr[b], o.cmp[b], p.ck[b], y);
-            yv[b] = y;
-        }
+    // o.yp: the row's own y_{k-1} as stored (a pending term's value, the
+    // interval series' y_cur; the plain form reads it here, only in rounds
+    // that add a pending term, to keep its registers)
+    constexpr bool kDefer = deferred_form<P, W, I>();
+    if constexpr (W <= 4) {
+        if (I || (kDefer && p.pend)) load_yp<P, W>(p, r, o);
+    }
+    const unsigned pend = kDefer ? p.pend : 0u;
+    const unsigned now = kDefer ? (active & ~p.defer) : active;
+    auto column = [&](int b, unsigned first) {
+        if (pend >> b & 1u) accumulate<P>(o.rr[b], o.cmp[b], p.ck_prev[b], o.yp[b]);
+        A y;
+        if constexpr (I) y = interval_iterate<P>(s[b], inv, o.yp[b], o.y_old[b], first, p.mb);
+        else y = new_iterate<P>(s[b], inv, o.y_old[b], first);
+        store_y(&ys[b], y);
+        if (now >> b & 1u) accumulate<P>(o.rr[b], o.cmp[b], p.ck[b], y);
+        yv[b] = y;
+    };
+    // every round but a column's first takes the plain update: for the single
+    // vector a branch on the launch's mask, so that the first round's form is
+    // not evaluated (and selected away) on every row of every round.  On
+    // GB300's FP64 pipe that evaluation was two multiplies a row: the branch
+    // took the FP64 lattice round from 0.270 to 0.211 ms.  Tiles keep one loop
+    // (the branch would cost them registers), and so does DF64, whose
+    // products run on the FP32 pipes (2% slower with it).
+    if (W == 1 && P != CPAA_DF64 && p.first == 0u) {
+        column(0, 0u);
     } else {
 #pragma unroll
-        for (int b = 0; b < W; ++b) {
-            const A y = new_iterate<P>(s[b], inv, o.y_old[b], (p.first >> b) & 1u);
-            store_y(&ys[b], y);
-            if (active >> b & 1u) accumulate<P>(o.rr[b], o.cmp[b], p.ck[b], y);
-            yv[b] = y;
-        }
+        for (int b = 0; b < W; ++b) column(b, (p.first >> b) & 1u);
     }
     store_row<S, W>(p.y_io + r * W, ys, false);
-    store_row<R, W>(p.rho + r * W, o.rr, true);
-    if constexpr (Prec<P>::kKahan) store_row<R, W>(p.comp + r * W, o.cmp, true);
+    if (rho_touched<P, W, I>(p)) {
+        store_row<R, W>(p.rho + r * W, o.rr, true);
+        if constexpr (Prec<P>::kKahan) store_row<R, W>(p.comp + r * W, o.cmp, true);
+    }
 }
 
 // A row's terms of the round's sums: T = d y and |T| (only in rounds that take
@@ -374,9 +449,9 @@ __device__ __forceinline__ void hub_tile(const StepParams<P, W> &p, int4 t, unsi
         cta_sum_w<A, W>(part, s_w);
         if (tid == 0) {
             RowOps<P, W> o;
-            load_ops<P, W>(p, h, o);
+            load_ops<P, W, I>(p, h, o);
             A yv[W], tT[W], tA[W];
-            row_finish<P, W, I>(p, h, part, p.inv_deg[h], o, yv, active);
+            row_finish<P, W, I>(p, h, part, row_factor<P, W, I>(p, p.inv_deg[h]), o, yv, active);
             if (p.reduce) {
                 row_terms<A, W>(yv, p.deg[h], tT, tA);
                 double *d = p.ipart + (int64_t)h * 2 * W;
@@ -536,8 +611,8 @@ __device__ __forceinline__ void long_chunk(const StepParams<P, W> &p, int4 dsc, 
         for (int b = 0; b < W; ++b) yv[b] = A(0);
         if (r < p.n) {
             RowOps<P, W> o;
-            load_ops<P, W>(p, r, o);
-            row_finish<P, W, I>(p, r, s, ld_once(p.inv_deg + r), o, yv, active);
+            load_ops<P, W, I>(p, r, o);
+            row_finish<P, W, I>(p, r, s, row_factor<P, W, I>(p, ld_once(p.inv_deg + r)), o, yv, active);
         }
         if (p.reduce) {
             A tT[W], tA[W];
@@ -564,12 +639,15 @@ __device__ __forceinline__ void short_chunk(const StepParams<P, W> &p, int4 dsc,
     // for narrow tiles the row's own operands are fetched before the gather
     // so that their latency overlaps it
     constexpr bool kEarly = W <= 4;
+    // the row's factors by its degree: a 2-byte word and the degree tables
+    // (cached), fetched before the gather like the other operands
     A inv = A(0), d = A(0);
     RowOps<P, W> o;
     if (live) {
-        inv = ld_once(p.inv_deg + r);
-        if (p.reduce) d = ld_once(p.deg + r);  // only the round's sums need d
-        if constexpr (kEarly) load_ops<P, W>(p, r, o);
+        const int dg = ld_once(p.deg16 + r);
+        inv = ld_ro(p.tab_inv + dg);
+        if (p.reduce) d = ld_ro(p.tab_deg + dg);  // only the round's sums need d
+        if constexpr (kEarly) load_ops<P, W, I>(p, r, o);
     }
     A acc[W];
     chunk_sum<P, W>(p, p.sell_col + off + kSellVec * lane, 0, groups, tail, acc);
@@ -577,7 +655,7 @@ __device__ __forceinline__ void short_chunk(const StepParams<P, W> &p, int4 dsc,
 #pragma unroll
     for (int b = 0; b < W; ++b) yv[b] = A(0);
     if (live) {
-        if constexpr (!kEarly) load_ops<P, W>(p, r, o);
+        if constexpr (!kEarly) load_ops<P, W, I>(p, r, o);
         row_finish<P, W, I>(p, r, acc, inv, o, yv, active);
     }
     if (p.reduce) {
@@ -596,7 +674,7 @@ __global__ void __launch_bounds__(kThreads) cheb_step_kernel(const StepParams<P,
     // columns stopped by the a-posteriori rule no longer accumulate; once
     // every column has stopped the remaining rounds do nothing
     const unsigned active = p.stop ? (p.active & ~*p.stop) : p.active;
-    if (p.stop && active == 0) return;
+    if (p.stop && active == 0 && p.pend == 0) return;
     // sparse frontier: every thread takes the same decision from the same two
     // words (the flag it may set is set only when the count already says so)
     bool filt = false;
@@ -645,7 +723,7 @@ __global__ void __launch_bounds__(kThreads) cheb_step_multi_kernel(const __grid_
         while (it >= mp.cta_off[gi + 1]) ++gi;
         const StepParams<P, W> &p = mp.g[gi];
         const unsigned active = p.stop ? (p.active & ~*p.stop) : p.active;
-        if (p.stop && active == 0) continue;
+        if (p.stop && active == 0 && p.pend == 0) continue;
         const int local = it - mp.cta_off[gi];
         if (local < p.num_hub_tiles) hub_tile<P, W, false>(p, p.hub_tiles[local], active);
         else long_chunk<P, W, false>(p, ld_stream4(&p.chunk_desc[local - p.num_hub_tiles].x), active);
@@ -656,7 +734,7 @@ __global__ void __launch_bounds__(kThreads) cheb_step_multi_kernel(const __grid_
         while (idx >= mp.warp_off[gi + 1]) ++gi;
         const StepParams<P, W> &p = mp.g[gi];
         const unsigned active = p.stop ? (p.active & ~*p.stop) : p.active;
-        if (p.stop && active == 0) continue;
+        if (p.stop && active == 0 && p.pend == 0) continue;
         short_chunk<P, W, false>(p, ld_stream4(&p.chunk_desc[p.num_long_chunks + idx - mp.warp_off[gi]].x), active);
     }
 }
@@ -770,30 +848,43 @@ static void fill_params(const StepLaunch &s, StepParams<P, W> &p) {
     p.num_long_chunks = g->num_long_chunks;
     p.n_hub = g->n_hub;
     p.n = g->n;
+    const A *tab;  // rows: d, 1 / d, 2 / d
     if constexpr (P == CPAA_F64) {
         p.deg = g->deg64;
         p.inv_deg = s.power ? g->inv_deg64 : g->inv2_deg64;
+        tab = g->tab64;
     } else if constexpr (P == CPAA_DF64) {
         p.deg = g->deg_df;
         p.inv_deg = s.power ? g->inv_deg_df : g->inv2_deg_df;
+        tab = g->tab_df;
     } else {
         p.deg = g->deg32;
         p.inv_deg = s.power ? g->inv_deg32 : g->inv2_deg32;
+        tab = g->tab32;
     }
+    // the interval series reads its own scaled table
+    p.deg16 = g->deg16;
+    p.tab_deg = tab;
+    p.tab_inv = s.interval ? static_cast<const A *>(s.ivtab) : tab + (size_t)(s.power ? 1 : 2) * g->tab_n;
     p.y_src = static_cast<const S *>(s.y_src);
     p.y_io = static_cast<S *>(s.y_io);
     p.rho = static_cast<R *>(s.rho);
     p.comp = static_cast<R *>(s.comp);
     p.ipart = s.ipart;
     p.stop = s.stop;
-    for (int b = 0; b < W; ++b) p.ck[b] = (A)s.ck[b];
+    for (int b = 0; b < W; ++b) {
+        p.ck[b] = (A)s.ck[b];
+        p.ck_prev[b] = (A)s.ck_prev[b];
+    }
+    p.pend = s.pend;
+    p.defer = s.defer;
     p.active = s.active;
     p.reduce = s.reduce;
     p.first = s.first;
     p.power = s.power;
     p.interval = s.interval;
     p.ia = (A)s.ia;
-    p.ib = (A)s.ib;
+    p.mb = (A)s.mb;
     p.front = s.front;
     p.front_full = s.front_full;
     p.front_entries = s.front_entries;
