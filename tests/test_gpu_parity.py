@@ -271,7 +271,7 @@ def test_batch_columns_equal_single(pkg, uploaded):
     seeds = ci.seed_vectors(g.n, B, seed=3)
     P = ci.seed_dense(g.n, seeds)
     cs = np.array([0.5, 0.85, 0.95, 0.85, 0.7])
-    for prec in (pkg.CPAA_F64, pkg.CPAA_F32, pkg.CPAA_DF64):
+    for prec in (pkg.CPAA_F64, pkg.CPAA_F32, pkg.CPAA_DF64, pkg.CPAA_BF16):
         Pd = torch.as_tensor(P).cuda()
         PI = torch.empty_like(Pd)
         infos = G.solve_batch(B, Pd, cs, 1e-7, PI, precision=prec)
@@ -280,6 +280,31 @@ def test_batch_columns_equal_single(pkg, uploaded):
             single, info = solve(pkg, G, P[b], cs[b], 1e-7, precision=prec)
             assert infos[b].rounds == info.rounds
             assert np.array_equal(PI[b].cpu().numpy(), single)
+
+
+@pytest.mark.parametrize("prec", ["F32", "BF16", "DF64"])
+def test_deferred_accumulation_every_round_count(pkg, uploaded, prec):
+    """The single-vector FP32, BF16 and DF64 solves add a term c_k y_k one
+    round late, from the stored y_k (deferred accumulation); tiles of two do
+    not.  For every round count from 1 to 9 (odd counts end on a term that may
+    not be deferred) the two agree bit for bit, and both match the oracle."""
+    P = getattr(pkg, "CPAA_" + prec)
+    tol = {"F32": 1e-6, "BF16": 5e-2, "DF64": 1e-12}[prec]
+    for gi in (12, 13, 14):
+        g, G = GRAPHS[gi], uploaded[gi]
+        rp, cx = g.numpy()
+        p = ci.seed_dense(g.n, ci.seed_vectors(g.n, 1, seed=21 + gi))[0]
+        Pd = torch.as_tensor(np.stack([p, p])).cuda()
+        for M in range(1, 10):
+            single, info = solve(pkg, G, p, 0.85, fixed_rounds=M, precision=P)
+            assert info.rounds == M
+            PI = torch.empty_like(Pd)
+            G.solve_batch(2, Pd, np.full(2, 0.85), 0.0, PI, precision=P, fixed_rounds=M, batch_width=2)
+            torch.cuda.synchronize()
+            assert np.array_equal(PI[0].cpu().numpy(), single), (gi, M)
+            assert np.array_equal(PI[1].cpu().numpy(), single), (gi, M)
+            ref = O.cpaa(rp, cx, p, 0.85, M)
+            assert np.abs(single - ref).sum() / np.abs(ref).sum() <= tol, (gi, M)
 
 
 def test_batch_on_fresh_graph(pkg):
