@@ -197,7 +197,8 @@ cpaa_status cpaa_graph_info(const cpaa_graph *g, int64_t *n, int64_t *nnz,
  * kept as CSR and cut into tiles of hub_tile entries, one CTA per tile; the
  * other rows, sorted by degree within windows of sort_window rows, form SELL
  * chunks of 32 rows (sell_entries counts their stored entries with padding),
- * of which long_chunks, those whose longest row exceeds long_chunk entries,
+ * of which long_chunks, those whose longest row exceeds long_chunk entries
+ * (or 65532, whichever is smaller: a warp's rows read a 2-byte degree),
  * get a CTA and the rest a warp.  tuned = 1 when CPAA_GRAPH_AUTOTUNE picked
  * the parameters after timing tune_candidates layouts. */
 typedef struct {
