@@ -320,15 +320,17 @@ __device__ __forceinline__ void row_finish(const StepParams<P, W> &p, int64_t r,
         if (now >> b & 1u) accumulate<P>(o.rr[b], o.cmp[b], p.ck[b], y);
         yv[b] = y;
     };
-    // every round but a column's first takes the plain update: for the single
-    // vector a branch on the launch's mask, so that the first round's form is
-    // not evaluated (and selected away) on every row of every round.  On
-    // GB300's FP64 pipe that evaluation was two multiplies a row: the branch
-    // took the FP64 lattice round from 0.270 to 0.211 ms.  Tiles keep one loop
-    // (the branch would cost them registers), and so does DF64, whose
-    // products run on the FP32 pipes (2% slower with it).
-    if (W == 1 && P != CPAA_DF64 && p.first == 0u) {
-        column(0, 0u);
+    // every round but a column's first takes the plain update: a branch on the
+    // launch's mask, so that the first round's form is not evaluated (and
+    // selected away) on every row of every round.  On GB300's FP64 pipe that
+    // evaluation was two multiplies a row and column: the branch took the FP64
+    // lattice round from 0.270 to 0.211 ms, and an FP64 batch of 8 on the
+    // lattice from 92.3 to 79.7 ms.  FP32 and BF16 tiles keep one loop (the
+    // branch would cost them registers), and so does DF64, whose products run
+    // on the FP32 pipes (2% slower with it).
+    if ((W == 1 && P != CPAA_DF64 && p.first == 0u) || (W > 1 && P == CPAA_F64 && p.first == 0u)) {
+#pragma unroll
+        for (int b = 0; b < W; ++b) column(b, 0u);
     } else {
 #pragma unroll
         for (int b = 0; b < W; ++b) column(b, (p.first >> b) & 1u);
