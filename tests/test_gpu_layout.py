@@ -118,3 +118,34 @@ def test_autotune_on_the_lattice(pkg):
     ref = O.cpaa(rp, cx, p, 0.85, info.rounds)
     assert np.abs(pi - ref).sum() <= 1e-12
     G.close()
+
+
+def test_row_longer_than_a_short_chunk_may_hold(pkg):
+    """A non-hub row of more than 65532 entries (hub threshold and long-chunk
+    threshold both above it) goes to a long chunk, because a warp's rows read a
+    2-byte degree; every format still matches the oracle, and the short chunks'
+    factor tables cover the degrees they meet."""
+    g = ci.star(70001)                       # centre of degree 70001, leaves of degree 1
+    rp, cx = g.numpy()
+    G = pkg.Graph(g.row_ptr.cuda(), g.col_idx.cuda(), n=g.n,
+                  layout={"hub_degree": 100000, "long_chunk": 1 << 20})
+    lay = G.layout()
+    assert lay["hub_rows"] == 0 and lay["long_chunks"] == 1, lay
+    p = np.zeros(g.n)
+    p[[0, 1, 5000, g.n - 1]] = 0.25
+    M = 15
+    ref = O.cpaa(rp, cx, p, 0.85, M)
+    # The centre's row is one long chunk: each of a CTA's 8 warps adds a slice
+    # of about 8750 of its entries in sequence.  DF64's significands hold about
+    # 48 bits, so that sum is about 1e-12 off in L1 here (measured 1.02e-12),
+    # and FP32's about 1e-5 (measured 1.2e-5): their bounds on this row are
+    # ten times those of the bench graphs, whose rows this long are hub rows
+    # summed by shuffle trees.
+    for prec, bound, rel in ((pkg.CPAA_F64, 1e-12, False), (pkg.CPAA_DF64, 1e-11, False),
+                             (pkg.CPAA_F32, 1e-4, True), (pkg.CPAA_BF16, 5e-2, True)):
+        pi, info = solve(pkg, G, p, 0.85, 0.0, precision=prec, fixed_rounds=M)
+        err = np.abs(pi - ref).sum()
+        if rel:
+            err /= np.abs(ref).sum()
+        assert err <= bound, (prec, err)
+    G.close()
