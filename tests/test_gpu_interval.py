@@ -113,7 +113,7 @@ def test_interval_batch_and_frontier(pkg, looped):
         seeds = ci.seed_vectors(g.n, 5, max_seeds=4, seed=9)
         P = ci.seed_dense(g.n, seeds)
         Pd = torch.as_tensor(P).cuda()
-        for prec in (pkg.CPAA_F64, pkg.CPAA_F32):
+        for prec in (pkg.CPAA_F64, pkg.CPAA_F32, pkg.CPAA_DF64, pkg.CPAA_BF16):
             PI = torch.empty_like(Pd)
             infos = G.solve_batch(5, Pd, np.array([0.5, 0.85, 0.95, 0.85, 0.7]), 1e-7, PI, precision=prec,
                                   batch_width=4, certify_interval=True)
