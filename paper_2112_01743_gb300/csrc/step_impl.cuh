@@ -814,18 +814,26 @@ static int resident_ctas() {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cheb_step_kernel<P, W, I>, kThreads, 0);
         // The kernel's shared arrays take a few KB per CTA.  Left to itself the
         // driver configured more of each SM's L1/shared array as shared memory
-        // than that: asking for a 10% carveout keeps the same resident CTAs and
-        // leaves the rest to L1 for the gathers (measured on two boxes: the FP64
-        // round on the 16.7M-vertex Chung-Lu graph 2.3-3.1% faster, DF64
-        // 2.1-2.7%, FP32 and the lattice unchanged).  Where it would cost
-        // resident CTAs (wide tiles, whose shared arrays are larger) the
-        // default stays.
-        if (per_sm > 0 &&
-            cudaFuncSetAttribute(cheb_step_kernel<P, W, I>, cudaFuncAttributePreferredSharedMemoryCarveout, 10) ==
-                cudaSuccess) {
-            int after = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&after, cheb_step_kernel<P, W, I>, kThreads, 0);
-            if (after < per_sm)
+        // than that: the smallest carveout (of 10, 15, ... 75%) that keeps the
+        // same resident CTAs leaves the rest to L1 for the gathers (measured:
+        // the FP64 round on the 16.7M-vertex Chung-Lu graph 2.3-3.1% faster
+        // at 10%, DF64 2.1-2.7%; FP32 batches of 8 on the 4M graph 2.4% at 15%,
+        // of 16 1%; FP32 single vectors and the lattice unchanged).  If none
+        // keeps them, the default stays.
+        if (per_sm > 0) {
+            bool kept = false;
+            for (int pct : {10, 15, 20, 25, 30, 40, 50, 60, 75}) {
+                if (cudaFuncSetAttribute(cheb_step_kernel<P, W, I>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         pct) != cudaSuccess)
+                    break;
+                int after = 0;
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&after, cheb_step_kernel<P, W, I>, kThreads, 0);
+                if (after >= per_sm) {
+                    kept = true;
+                    break;
+                }
+            }
+            if (!kept)
                 cudaFuncSetAttribute(cheb_step_kernel<P, W, I>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                      (int)cudaSharedmemCarveoutDefault);
         }
